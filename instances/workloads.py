@@ -1,0 +1,258 @@
+"""Seeded workload generators shaped like the paper's experiments.
+
+Every generator returns an :class:`instances.SOSProgram`.  Random coefficients
+come from ``numpy.random.default_rng(seed)`` and are drawn in graded
+lexicographic order of their support, so a (generator, seed) pair names one
+fixed problem.
+
+Workloads:
+
+* ``quartic_pop``      - unconstrained quartic POP  max g s.t. p - g SOS (eq. (9)),
+                          p = (sum x_i^2)^2 + sum_{|a|<=3} c_a x^a, c_a ~ N(0,1).
+* ``ball_pop``         - the same p on the unit ball through the order-2 Lasserre
+                          relaxation p - g = s0 + s1 (1 - |x|^2) (eq. (12)-(13)),
+                          with s1 handled as a weighted SOS block (Section VI).
+* ``paper_pop``        - the constrained quartic POP of eq. (46) (Tables I-II).
+* ``univariate_pop``   - n = 1, where nonnegative polynomials are SOS.
+* ``lyapunov_linear``  - quadratic V for x' = A x, cost trace(P) (closed form).
+* ``lyapunov_cubic``   - global Lyapunov search for x' = -x + cubic(x) with a
+                          degree-4 V (eq. (10) with an eps |x|^2 margin).
+* ``parametric_pop``   - p = p0 + sum_k theta_k q_k (learned warm-start family).
+"""
+
+from __future__ import annotations
+
+import itertools
+from typing import Dict, List, Sequence, Tuple
+
+import numpy as np
+
+from .program import Block, Constraint, SOSProgram
+
+Exp = Tuple[int, ...]
+Poly = Dict[Exp, float]
+
+
+# --------------------------------------------------------------------------
+# sparse polynomial helpers used only to *write down* input polynomials
+# --------------------------------------------------------------------------
+
+def _support(n: int, max_deg: int, min_deg: int = 0) -> List[Exp]:
+    """Exponents of degree min_deg..max_deg, graded, then x1 > x2 > ... lex.
+
+    Used only to fix the order in which random coefficients are drawn."""
+    out: List[Exp] = []
+    for deg in range(min_deg, max_deg + 1):
+        level = [e for e in itertools.product(range(deg + 1), repeat=n) if sum(e) == deg]
+        level.sort(reverse=True)
+        out.extend(level)
+    return out
+
+
+def _unit(n: int, i: int, k: int = 1) -> Exp:
+    e = [0] * n
+    e[i] = k
+    return tuple(e)
+
+
+def _zero(n: int) -> Exp:
+    return tuple([0] * n)
+
+
+def padd(*ps: Poly, scale: Sequence[float] | None = None) -> Poly:
+    out: Poly = {}
+    for idx, p in enumerate(ps):
+        s = 1.0 if scale is None else float(scale[idx])
+        for e, c in p.items():
+            out[e] = out.get(e, 0.0) + s * c
+    return {e: c for e, c in out.items() if c != 0.0}
+
+
+def pmul(p: Poly, q: Poly) -> Poly:
+    out: Poly = {}
+    for e1, c1 in p.items():
+        for e2, c2 in q.items():
+            e = tuple(a + b for a, b in zip(e1, e2))
+            out[e] = out.get(e, 0.0) + c1 * c2
+    return {e: c for e, c in out.items() if c != 0.0}
+
+
+def pdiff(p: Poly, i: int) -> Poly:
+    out: Poly = {}
+    for e, c in p.items():
+        if e[i] > 0:
+            f = list(e)
+            f[i] -= 1
+            out[tuple(f)] = out.get(tuple(f), 0.0) + c * e[i]
+    return out
+
+
+def sq_norm(n: int, scale: float = 1.0) -> Poly:
+    return {_unit(n, i, 2): scale for i in range(n)}
+
+
+def _random_low_part(n: int, rng: np.random.Generator, deg: int = 3) -> Poly:
+    sup = _support(n, deg)
+    coef = rng.standard_normal(len(sup))
+    return {e: float(c) for e, c in zip(sup, coef)}
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+
+def quartic_poly(n: int, seed: int) -> Poly:
+    """p = (sum x_i^2)^2 + sum_{|a|<=3} c_a x^a with c_a ~ N(0,1)."""
+    rng = np.random.default_rng(seed)
+    s = sq_norm(n)
+    return padd(pmul(s, s), _random_low_part(n, rng))
+
+
+def _pop_program(n: int, p: Poly, name: str, ball: bool) -> SOSProgram:
+    blocks = [Block(2)]
+    if ball:
+        blocks.append(Block(1, padd({_zero(n): 1.0}, sq_norm(n, -1.0))))
+    con = Constraint(degree=4, g0=p, g=[{_zero(n): 1.0}], blocks=blocks)
+    return SOSProgram(n=n, w=np.array([-1.0]), constraints=[con], name=name)
+
+
+def quartic_pop(n: int, seed: int = 0) -> SOSProgram:
+    """Unconstrained quartic POP: min -g s.t. p - g is SOS (eq. (9))."""
+    return _pop_program(n, quartic_poly(n, seed), f"quartic_pop(n={n},seed={seed})", ball=False)
+
+
+def ball_pop(n: int, seed: int = 0) -> SOSProgram:
+    """Quartic POP on the unit ball, order-2 Lasserre relaxation as a weighted
+    SOS constraint: p - g = s0 + s1 (1 - |x|^2), s0 deg 4, s1 deg 2."""
+    return _pop_program(n, quartic_poly(n, seed), f"ball_pop(n={n},seed={seed})", ball=True)
+
+
+def paper_pop_poly(n: int) -> Poly:
+    """Objective of eq. (46): sum_{i<j} (x_i x_j + x_i^2 x_j - x_j^3 - x_i^2 x_j^2)."""
+    p: Poly = {}
+    for j in range(n):
+        for i in range(j):
+            for e, c in (
+                (tuple(a + b for a, b in zip(_unit(n, i), _unit(n, j))), 1.0),
+                (tuple(a + b for a, b in zip(_unit(n, i, 2), _unit(n, j))), 1.0),
+                (_unit(n, j, 3), -1.0),
+                (tuple(a + b for a, b in zip(_unit(n, i, 2), _unit(n, j, 2))), -1.0),
+            ):
+                p[e] = p.get(e, 0.0) + c
+    return {e: c for e, c in p.items() if c != 0.0}
+
+
+def paper_pop(n: int) -> SOSProgram:
+    """Constrained POP of eq. (46) on the unit ball, order 2d = 4."""
+    return _pop_program(n, paper_pop_poly(n), f"paper_pop(n={n})", ball=True)
+
+
+def univariate_pop(degree: int, seed: int) -> SOSProgram:
+    """p(x) = x^degree + sum_{k<degree} c_k x^k, c_k ~ N(0,1); degree even."""
+    assert degree % 2 == 0
+    rng = np.random.default_rng(seed)
+    coef = rng.standard_normal(degree)
+    p: Poly = {(degree,): 1.0}
+    for k in range(degree):
+        p[(k,)] = float(coef[k])
+    con = Constraint(degree=degree, g0=p, g=[{(0,): 1.0}], blocks=[Block(degree // 2)])
+    return SOSProgram(n=1, w=np.array([-1.0]), constraints=[con], name=f"univariate(deg={degree},seed={seed})",
+                      meta={"p": p})
+
+
+def hurwitz_matrix(n: int, seed: int) -> np.ndarray:
+    """Random A with spectral abscissa <= -0.5 (shifted Gaussian matrix)."""
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((n, n)) / np.sqrt(n)
+    shift = np.max(np.linalg.eigvals(a).real) + 0.5
+    return a - shift * np.eye(n)
+
+
+def lyapunov_linear(n: int, seed: int, eps: float = 1e-3) -> SOSProgram:
+    """min trace(P) s.t. V - eps|x|^2 SOS and -grad V . (A x) - x^T x SOS,
+    V(x) = x^T P x.  Decision variables: P_ij, i <= j (t = n(n+1)/2).
+
+    The constraints read P - eps I >= 0 and -(A^T P + P A) - I >= 0, so the
+    optimum is the Lyapunov solution of A^T P + P A + I = 0 when it is
+    >= eps I."""
+    A = hurwitz_matrix(n, seed)
+    pairs = [(i, j) for j in range(n) for i in range(j + 1)]
+    # V = sum_{i<=j} P_ij m_ij(x) with m_ii = x_i^2, m_ij = 2 x_i x_j
+    mons: List[Poly] = []
+    for (i, j) in pairs:
+        e = tuple(a + b for a, b in zip(_unit(n, i), _unit(n, j)))
+        mons.append({e: 1.0 if i == j else 2.0})
+    fx = [{_unit(n, k): float(A[r, k]) for k in range(n) if A[r, k] != 0.0} for r in range(n)]
+    w = np.array([1.0 if i == j else 0.0 for (i, j) in pairs])
+    # s1 = V - eps|x|^2 = g0 - sum u_i g_i with g_i = -m_i
+    c1 = Constraint(degree=2, g0=sq_norm(n, -eps), g=[{e: -c for e, c in m.items()} for m in mons],
+                    blocks=[Block(1)])
+    # s2 = -grad V . f - |x|^2 = g0 - sum u_i g_i with g_i = grad m_i . f
+    g2 = []
+    for m in mons:
+        gi: Poly = {}
+        for r in range(n):
+            gi = padd(gi, pmul(pdiff(m, r), fx[r]))
+        g2.append(gi)
+    c2 = Constraint(degree=2, g0=sq_norm(n, -1.0), g=g2, blocks=[Block(1)])
+    return SOSProgram(n=n, w=w, constraints=[c1, c2], name=f"lyapunov_linear(n={n},seed={seed})",
+                      meta={"A": A, "pairs": pairs, "eps": eps})
+
+
+def lyapunov_cubic(n: int, seed: int, eps: float = 1e-3, sigma: float = 0.1) -> SOSProgram:
+    """Global Lyapunov search for x' = f(x) = -x + cubic(x).
+
+    Each component of f gets every cubic monomial with a N(0, sigma^2)
+    coefficient.  V = sum_i u_i m_i over the monomials of degree 2..4 and
+    feasibility (w = 0) of
+
+        V - eps |x|^2 SOS (degree 4, basis degree 2),
+        -grad V . f - eps |x|^2 SOS (degree 6, basis degree 3)."""
+    rng = np.random.default_rng(seed)
+    cubic = _support(n, 3, 3)
+    fx: List[Poly] = []
+    for r in range(n):
+        comp = {e: float(sigma * rng.standard_normal()) for e in cubic}
+        comp[_unit(n, r)] = comp.get(_unit(n, r), 0.0) - 1.0
+        fx.append(comp)
+    vmons = _support(n, 4, 2)
+    c1 = Constraint(degree=4, g0=sq_norm(n, -eps), g=[{m: -1.0} for m in vmons], blocks=[Block(2)])
+    g2 = []
+    for m in vmons:
+        gi: Poly = {}
+        for r in range(n):
+            gi = padd(gi, pmul(pdiff({m: 1.0}, r), fx[r]))
+        g2.append(gi)
+    c2 = Constraint(degree=6, g0=sq_norm(n, -eps), g=g2, blocks=[Block(3)])
+    return SOSProgram(n=n, w=np.zeros(len(vmons)), constraints=[c1, c2],
+                      name=f"lyapunov_cubic(n={n},seed={seed})", meta={"f": fx})
+
+
+def lyapunov_batch(count: int, seed: int = 0, n_min: int = 2, n_max: int = 6) -> List[SOSProgram]:
+    """``count`` cubic Lyapunov searches with n ~ U{n_min..n_max}."""
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(n_min, n_max + 1, size=count)
+    seeds = rng.integers(0, 2**31 - 1, size=count)
+    return [lyapunov_cubic(int(n), int(s)) for n, s in zip(ns, seeds)]
+
+
+class ParametricPOP:
+    """p(theta) = p0 + sum_{k=1..K} theta_k q_k on monomials of degree <= 3
+    (p0 also carries (sum x_i^2)^2 so every member is coercive)."""
+
+    def __init__(self, n: int = 10, K: int = 16, seed: int = 0):
+        self.n, self.K = n, K
+        self.p0 = quartic_poly(n, seed)
+        self.q = []
+        for k in range(1, K + 1):
+            self.q.append(_random_low_part(n, np.random.default_rng(seed + k)))
+
+    def poly(self, theta: np.ndarray) -> Poly:
+        return padd(self.p0, *self.q, scale=[1.0] + [float(x) for x in theta])
+
+    def program(self, theta: np.ndarray) -> SOSProgram:
+        return _pop_program(self.n, self.poly(theta), f"parametric_pop(n={self.n})", ball=False)
+
+    @staticmethod
+    def thetas(count: int, seed: int, K: int = 16) -> np.ndarray:
+        return np.random.default_rng(seed).uniform(-1.0, 1.0, size=(count, K))
