@@ -1,0 +1,208 @@
+/*
+ * libsos - HSDE ADMM for sum-of-squares programs on one GB300 GPU (sm_103a).
+ *
+ * Method: Zheng, Fantuzzi, Papachristodoulou, "Fast ADMM for sum-of-squares
+ * programs using partial orthogonality".  An SOS program in the standard form
+ * of eq. (7) (weighted blocks as in eq. (37)) is recast as the conic program
+ * of eq. (15) over K = R^t x S_+^{N_1} x ... and solved by the three-step ADMM
+ * of eq. (20) on its homogeneous self-dual embedding (eq. (18)-(19)).  The
+ * affine step uses the eliminations of eq. (23)-(27) and the diagonal-plus-
+ * low-rank structure of Prop. 1 / Prop. 3 (Woodbury, eq. (28)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All pointers in argument structs are HOST pointers owned by the caller;
+ *   sos_setup copies what it needs, so they may be freed after it returns.
+ * - The handle is owned by the library and released with sos_destroy.
+ * - Exponent arrays are row-major int32 [count x n_vars].
+ * - Packed Gram order ("svec"): for each block, the lower triangle column by
+ *   column (column j holds rows j..N-1); off-diagonal entries are scaled by
+ *   sqrt(2), so <svec X, svec Y> = trace(X Y).
+ * - Per instance the primal vector is xi = [u (t free variables); svec X_1;
+ *   svec X_2; ...] of length n_x, the dual vector y has length m (one entry
+ *   per matched monomial, constraints concatenated in order), and the HSDE
+ *   iterates are u = [xi; y; tau], v = [z; s; kappa] (eq. (19)).
+ * - Return codes: SOS_OK (0) or a negative SOS_ERR_*; the message of the last
+ *   failure on a handle is available from sos_last_error.  A failure during
+ *   sos_setup leaves *out NULL; its message is available from
+ *   sos_last_error(NULL).
+ * - Solver outcomes are reported in sos_result.status, not in return codes.
+ * - Every entry point is synchronous with respect to the host unless noted;
+ *   device work is issued on the stream given in sos_options.cuda_stream
+ *   (NULL: a stream the library creates).
+ */
+#ifndef LIBSOS_SOS_H
+#define LIBSOS_SOS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define SOS_OK 0
+#define SOS_ERR_INVALID_ARG (-1)   /* malformed input: bad sizes, a monomial that is not a row, ... */
+#define SOS_ERR_CUDA (-2)          /* a CUDA runtime call failed */
+#define SOS_ERR_FACTOR (-3)        /* the Woodbury core I + A_L^T P^-1 A_L is not SPD in FP64 */
+#define SOS_ERR_TIMEOUT (-4)       /* a bounded device-side wait expired; the context stays usable */
+#define SOS_ERR_UNSUPPORTED (-5)   /* option not available for this problem (e.g. block too large) */
+
+/* ---- solver status (sos_result.status) ---- */
+#define SOS_RUNNING 0
+#define SOS_SOLVED 1
+#define SOS_PRIMAL_INFEASIBLE 2
+#define SOS_DUAL_INFEASIBLE 3
+#define SOS_MAX_ITER 4
+#define SOS_NUMERICAL 5
+
+/* ---- precision forms (sos_options.precision) ---- */
+#define SOS_PREC_FP64 0  /* plain: FP64 iterates, FP64 PSD projections */
+#define SOS_PREC_FP32 1  /* FP32 iterates and projections; FP64 Woodbury, tau/kappa, residuals */
+
+typedef struct sos_handle sos_handle;
+
+/* One Gram block X_b of a constraint.  basis_exps lists the N monomials of
+ * its basis v (eq. (4) for the full basis).  With n_weight_terms == 0 the
+ * block contributes v^T X v (eq. (5)); otherwise it contributes
+ * p(x) v^T X v with p = sum_k weight_coef[k] x^weight_exps[k] (eq. (38)). */
+typedef struct {
+  int32_t N;
+  const int32_t* basis_exps;   /* [N x n_vars] */
+  int32_t n_weight_terms;
+  const int32_t* weight_exps;  /* [n_weight_terms x n_vars] */
+  const double* weight_coef;   /* [n_weight_terms] */
+} sos_block;
+
+/* One polynomial identity of eq. (7):
+ *   g_0(x) - sum_i u_i g_i(x) = sum_b (weighted) Gram forms of its blocks,
+ * matched coefficient-wise on the n_rows monomials row_exps (eq. (11)).
+ * term k adds term_coef[k] x^term_exps[k] to g_{term_poly[k]}
+ * (term_poly 0 = g_0 -> b, 1..t = g_i -> column i-1 of A_1). */
+typedef struct {
+  int32_t n_rows;
+  const int32_t* row_exps;     /* [n_rows x n_vars], distinct */
+  int64_t n_terms;
+  const int32_t* term_poly;    /* [n_terms] in 0..t */
+  const int32_t* term_exps;    /* [n_terms x n_vars] */
+  const double* term_coef;     /* [n_terms] */
+  int32_t n_blocks;
+  const sos_block* blocks;     /* [n_blocks] */
+} sos_constraint;
+
+/* min w^T u subject to the constraints (eq. (7), eq. (15)). */
+typedef struct {
+  int32_t n_vars;
+  int32_t t;
+  const double* w;                   /* [t] */
+  int32_t n_constraints;
+  const sos_constraint* constraints; /* [n_constraints] */
+} sos_program;
+
+typedef struct {
+  int32_t precision;      /* SOS_PREC_* */
+  int32_t k_check;        /* residual check period in iterations (>= 1) */
+  void* cuda_stream;      /* cudaStream_t to issue work on, or NULL */
+  int32_t reserved[8];    /* must be zero */
+} sos_options;
+
+/* Per-instance solve report.  x, y, s are optional caller-allocated HOST
+ * buffers (NULL to skip) receiving the normalised solution
+ * xi = u_xi / tau (n_x), y = u_y / tau (m) and the dual slack z = v_z / tau
+ * of eq. (17) (n_x).  Residuals follow the definitions documented with
+ * sos_solve. */
+typedef struct {
+  double* x;
+  double* y;
+  double* s;
+  double res_primal;
+  double res_dual;
+  double gap;
+  double obj_primal;   /* c^T xi */
+  double obj_dual;     /* b^T y */
+  double tau;
+  double kappa;
+  int32_t iters;
+  int32_t status;      /* SOS_* status */
+} sos_result;
+
+/* Builds the conic data of every program (coefficient matching eq. (11),
+ * index map of the indicator matrices eq. (8) and eq. (38)), splits the
+ * columns into the orthogonal part (plain Gram blocks, Prop. 1) and the
+ * low-rank part (free variables and weighted blocks), factors the FP64
+ * Woodbury core I + A_L^T P^-1 A_L (eq. (28)) once, precomputes M^-1 zeta
+ * (eq. (25)), copies everything to the device and sets the iterate to the
+ * cold start u = v = (0, 0, 1).  n_progs >= 1 instances are solved together
+ * (batched); each keeps its own data and status.
+ * Errors: SOS_ERR_INVALID_ARG (a monomial of g_i, of a block product or of a
+ * weight product that is not among the rows; non-positive sizes),
+ * SOS_ERR_FACTOR, SOS_ERR_CUDA, SOS_ERR_UNSUPPORTED. */
+int sos_setup(const sos_program* progs, int32_t n_progs, const sos_options* opts, sos_handle** out);
+
+/* Releases all device and host memory of the handle (NULL is a no-op). */
+void sos_destroy(sos_handle* h);
+
+/* Message of the last error on h (or of the last failed sos_setup when h is
+ * NULL).  The string stays valid until the next call on the same handle. */
+const char* sos_last_error(const sos_handle* h);
+
+/* Sizes of instance inst: dims = {n_x, m, t, t_eff, n_blocks, total Gram
+ * entries}, where t_eff = t + sum of packed sizes of weighted blocks is the
+ * order of the Woodbury core. */
+int sos_dims(const sos_handle* h, int32_t inst, int64_t dims[6]);
+
+/* Runs ADMM (eq. (20)) from the current iterate until every instance has
+ * terminated or max_iter iterations have run.  Every k_check iterations each
+ * running instance is checked (tau > 1e-12 (kappa + 1)):
+ *   res_primal = |A xi - b| / (1 + |b|),  res_dual = |A^T y + z - c| / (1 + |c|),
+ *   gap = |c^T xi - b^T y| / (1 + |c^T xi| + |b^T y|),
+ * SOLVED when all three are <= tol; PRIMAL_INFEASIBLE when b^T u_y > 0 and
+ * |A^T u_y + v_z| / b^T u_y <= tol; DUAL_INFEASIBLE when c^T u_xi < 0 and
+ * |A u_xi| / -c^T u_xi <= tol; NUMERICAL on a non-finite iterate.  A
+ * terminated instance is frozen (its iterate no longer changes).
+ * results: array of n_progs reports (may be NULL).  Returns SOS_OK or an
+ * error code (SOS_ERR_TIMEOUT if a bounded device wait expired). */
+int sos_solve(sos_handle* h, double tol, int32_t max_iter, sos_result* results);
+
+/* Runs exactly iters ADMM iterations on every running instance with no
+ * residual checks (the timing and parity entry point).  Asynchronous: returns
+ * after enqueueing the work on the handle's stream. */
+int sos_iterate(sos_handle* h, int32_t iters);
+
+/* Waits for the handle's stream and reports a device-side error flag
+ * (SOS_ERR_TIMEOUT) raised by any kernel since the last call. */
+int sos_sync(sos_handle* h);
+
+/* Copies the HSDE iterates of all instances (concatenated in instance order,
+ * each [n_x + m + 1]) to / from HOST buffers.  set_iterate also marks every
+ * instance as running (warm start, resume from a checkpoint). */
+int sos_get_iterate(sos_handle* h, double* u, double* v);
+int sos_set_iterate(sos_handle* h, const double* u, const double* v);
+
+/* Exponents of all monomials of degree <= degree in n_vars variables in the
+ * graded order of eq. (4) (x1 > x2 > ... within a degree).  Writes at most
+ * capacity rows to out (may be NULL) and the total count to *count. */
+int sos_monomials(int32_t n_vars, int32_t degree, int32_t* out, int64_t capacity, int64_t* count);
+
+/* Host-only view of the index map of ONE program (no GPU needed), for
+ * checking the setup: dims as in sos_dims; if the arrays are non-NULL,
+ * ent_row[n_x] receives for each packed entry the row of its single nonzero
+ * for a plain Gram entry (eq. (8)) or -1 for a low-rank entry (free variable
+ * or weighted block), p_diag[m] the diagonal of P = I + A_D A_D^T (Prop. 1),
+ * b[m] the coefficients of g_0, and *zeta_h the scalar zeta^T M^{-1} zeta of
+ * eq. (25).  Errors as sos_setup. */
+int sos_host_plan(const sos_program* prog, int64_t dims[6], int32_t* ent_row, double* p_diag, double* b,
+                  double* zeta_h);
+
+/* Profiling hooks (used by the benchmark to time single stages with events
+ * on the handle's stream).  sos_stream returns the cudaStream_t in use.
+ * sos_run_stage enqueues one stage of one iteration: 0 = affine step (all
+ * kernels up to the cone projection), 1 = PSD projection of small blocks,
+ * 2 = PSD projection of large blocks, 3 = one full iteration. */
+void* sos_stream(sos_handle* h);
+int sos_run_stage(sos_handle* h, int32_t stage);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBSOS_SOS_H */

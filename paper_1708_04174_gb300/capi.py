@@ -1,0 +1,273 @@
+"""ctypes binding of libsos (include/sos.h): argument marshalling only.
+
+Every step of the solver runs in the library (host setup in C++, iterations
+in CUDA kernels).  This module only turns an ``instances.SOSProgram``-like
+description into the C structs of the header and copies results out.  It
+never falls back to anything else: if ``libsos.so`` is missing or fails to
+load, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsos.so")
+
+SOS_OK = 0
+SOS_ERR_INVALID_ARG, SOS_ERR_CUDA, SOS_ERR_FACTOR, SOS_ERR_TIMEOUT, SOS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5
+RUNNING, SOLVED, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE, MAX_ITER, NUMERICAL = 0, 1, 2, 3, 4, 5
+PREC_FP64, PREC_FP32 = 0, 1
+
+_i32p = C.POINTER(C.c_int32)
+_f64p = C.POINTER(C.c_double)
+
+
+class sos_block(C.Structure):
+    _fields_ = [("N", C.c_int32), ("basis_exps", _i32p), ("n_weight_terms", C.c_int32),
+                ("weight_exps", _i32p), ("weight_coef", _f64p)]
+
+
+class sos_constraint(C.Structure):
+    _fields_ = [("n_rows", C.c_int32), ("row_exps", _i32p), ("n_terms", C.c_int64), ("term_poly", _i32p),
+                ("term_exps", _i32p), ("term_coef", _f64p), ("n_blocks", C.c_int32),
+                ("blocks", C.POINTER(sos_block))]
+
+
+class sos_program(C.Structure):
+    _fields_ = [("n_vars", C.c_int32), ("t", C.c_int32), ("w", _f64p), ("n_constraints", C.c_int32),
+                ("constraints", C.POINTER(sos_constraint))]
+
+
+class sos_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("k_check", C.c_int32), ("cuda_stream", C.c_void_p),
+                ("reserved", C.c_int32 * 8)]
+
+
+class sos_result(C.Structure):
+    _fields_ = [("x", _f64p), ("y", _f64p), ("s", _f64p), ("res_primal", C.c_double), ("res_dual", C.c_double),
+                ("gap", C.c_double), ("obj_primal", C.c_double), ("obj_dual", C.c_double), ("tau", C.c_double),
+                ("kappa", C.c_double), ("iters", C.c_int32), ("status", C.c_int32)]
+
+
+EXPORTS = {
+    "sos_setup": (C.c_int, [C.POINTER(sos_program), C.c_int32, C.POINTER(sos_options), C.POINTER(C.c_void_p)]),
+    "sos_destroy": (None, [C.c_void_p]),
+    "sos_last_error": (C.c_char_p, [C.c_void_p]),
+    "sos_dims": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
+    "sos_solve": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.POINTER(sos_result)]),
+    "sos_iterate": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sos_sync": (C.c_int, [C.c_void_p]),
+    "sos_get_iterate": (C.c_int, [C.c_void_p, _f64p, _f64p]),
+    "sos_set_iterate": (C.c_int, [C.c_void_p, _f64p, _f64p]),
+    "sos_monomials": (C.c_int, [C.c_int32, C.c_int32, _i32p, C.c_int64, C.POINTER(C.c_int64)]),
+    "sos_host_plan": (C.c_int, [C.POINTER(sos_program), C.POINTER(C.c_int64), _i32p, _f64p, _f64p, _f64p]),
+    "sos_stream": (C.c_void_p, [C.c_void_p]),
+    "sos_run_stage": (C.c_int, [C.c_void_p, C.c_int32]),
+}
+
+_lib = None
+
+
+def lib():
+    """Loads libsos.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libsos.so not found at {LIB_PATH}; build it with "
+                               "`python -m paper_1708_04174_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _check(rc: int, handle=None):
+    if rc != SOS_OK:
+        msg = lib().sos_last_error(handle)
+        raise RuntimeError(f"libsos error {rc}: {msg.decode() if msg else ''}")
+
+
+def monomials(n: int, degree: int) -> np.ndarray:
+    """Exponents of v_degree(x) in the graded order of eq. (4) (computed by libsos)."""
+    cnt = C.c_int64(0)
+    _check(lib().sos_monomials(n, degree, None, 0, C.byref(cnt)))
+    out = np.zeros((cnt.value, n), dtype=np.int32)
+    _check(lib().sos_monomials(n, degree, _ptr(out, C.c_int32), cnt.value, C.byref(cnt)))
+    return out
+
+
+class _Marshalled:
+    """C structs for a list of programs; keeps every array alive."""
+
+    def __init__(self, progs: Sequence):
+        self.keep: List = []
+        self.progs = (sos_program * len(progs))()
+        cache = {}
+
+        def mono(n, d):
+            if (n, d) not in cache:
+                cache[(n, d)] = monomials(n, d)
+            return cache[(n, d)]
+
+        for pi, pg in enumerate(progs):
+            n = pg.n
+            cons = (sos_constraint * len(pg.constraints))()
+            for ci, con in enumerate(pg.constraints):
+                rows = mono(n, con.degree)
+                polys = [con.g0] + list(con.g)
+                tp, te, tc = [], [], []
+                for k, poly in enumerate(polys):
+                    for e, cval in poly.items():
+                        tp.append(k)
+                        te.append(e)
+                        tc.append(cval)
+                tp = np.ascontiguousarray(tp, dtype=np.int32)
+                te = np.ascontiguousarray(np.array(te, dtype=np.int32).reshape(-1, n))
+                tc = np.ascontiguousarray(tc, dtype=np.float64)
+                blks = (sos_block * len(con.blocks))()
+                for bi, blk in enumerate(con.blocks):
+                    bas = mono(n, blk.basis_degree)
+                    blks[bi].N = bas.shape[0]
+                    blks[bi].basis_exps = _ptr(bas, C.c_int32)
+                    if blk.weight is not None:
+                        we = np.ascontiguousarray(np.array(list(blk.weight.keys()), dtype=np.int32).reshape(-1, n))
+                        wc = np.ascontiguousarray(list(blk.weight.values()), dtype=np.float64)
+                        blks[bi].n_weight_terms = len(wc)
+                        blks[bi].weight_exps = _ptr(we, C.c_int32)
+                        blks[bi].weight_coef = _ptr(wc, C.c_double)
+                        self.keep += [we, wc]
+                    else:
+                        blks[bi].n_weight_terms = 0
+                    self.keep.append(bas)
+                cons[ci].n_rows = rows.shape[0]
+                cons[ci].row_exps = _ptr(rows, C.c_int32)
+                cons[ci].n_terms = len(tp)
+                cons[ci].term_poly = _ptr(tp, C.c_int32)
+                cons[ci].term_exps = _ptr(te, C.c_int32)
+                cons[ci].term_coef = _ptr(tc, C.c_double)
+                cons[ci].n_blocks = len(con.blocks)
+                cons[ci].blocks = blks
+                self.keep += [rows, tp, te, tc, blks]
+            w = np.ascontiguousarray(pg.w, dtype=np.float64)
+            self.progs[pi].n_vars = n
+            self.progs[pi].t = len(w)
+            self.progs[pi].w = _ptr(w, C.c_double)
+            self.progs[pi].n_constraints = len(pg.constraints)
+            self.progs[pi].constraints = cons
+            self.keep += [w, cons]
+
+
+def host_plan(prog):
+    """Index map of one program as built by libsos's host setup (no GPU)."""
+    m = _Marshalled([prog])
+    dims = (C.c_int64 * 6)()
+    _check(lib().sos_host_plan(m.progs, dims, None, None, None, None))
+    nx, mm = dims[0], dims[1]
+    ent = np.zeros(nx, dtype=np.int32)
+    pd = np.zeros(mm)
+    b = np.zeros(mm)
+    zh = C.c_double(0)
+    _check(lib().sos_host_plan(m.progs, dims, _ptr(ent, C.c_int32), _ptr(pd, C.c_double), _ptr(b, C.c_double),
+                               C.byref(zh)))
+    return {"dims": tuple(dims), "ent_row": ent, "p_diag": pd, "b": b, "zeta_h": zh.value}
+
+
+class Solver:
+    """One libsos handle over a batch of SOS programs (instances)."""
+
+    def __init__(self, progs, precision: int = PREC_FP64, k_check: int = 10, stream=None):
+        if not isinstance(progs, (list, tuple)):
+            progs = [progs]
+        self.n_inst = len(progs)
+        m = _Marshalled(progs)
+        opts = sos_options()
+        opts.precision = precision
+        opts.k_check = k_check
+        opts.cuda_stream = C.c_void_p(stream) if stream else None
+        h = C.c_void_p()
+        _check(lib().sos_setup(m.progs, len(progs), C.byref(opts), C.byref(h)))
+        self.h = h
+        self.precision = precision
+        self.dims = [self._dims(i) for i in range(self.n_inst)]
+        self.total = sum(d[0] + d[1] + 1 for d in self.dims)
+
+    def _dims(self, i):
+        d = (C.c_int64 * 6)()
+        _check(lib().sos_dims(self.h, i, d), self.h)
+        return tuple(d)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sos_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def iterate(self, iters: int):
+        _check(lib().sos_iterate(self.h, iters), self.h)
+
+    def sync(self):
+        _check(lib().sos_sync(self.h), self.h)
+
+    @property
+    def stream(self) -> int:
+        return lib().sos_stream(self.h) or 0
+
+    def run_stage(self, stage: int):
+        _check(lib().sos_run_stage(self.h, stage), self.h)
+
+    def get_iterate(self):
+        u = np.zeros(self.total)
+        v = np.zeros(self.total)
+        _check(lib().sos_get_iterate(self.h, _ptr(u, C.c_double), _ptr(v, C.c_double)), self.h)
+        return u, v
+
+    def set_iterate(self, u: np.ndarray, v: np.ndarray):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        assert u.shape == (self.total,) and v.shape == (self.total,)
+        _check(lib().sos_set_iterate(self.h, _ptr(u, C.c_double), _ptr(v, C.c_double)), self.h)
+
+    def split(self, vec: np.ndarray):
+        """Per-instance (xi, y, tau) slices of a concatenated iterate."""
+        out, pos = [], 0
+        for d in self.dims:
+            nx, mm = d[0], d[1]
+            out.append((vec[pos:pos + nx], vec[pos + nx:pos + nx + mm], vec[pos + nx + mm]))
+            pos += nx + mm + 1
+        return out
+
+    def solve(self, tol: float, max_iter: int, want_solution: bool = True):
+        res = (sos_result * self.n_inst)()
+        bufs = []
+        for i, d in enumerate(self.dims):
+            if want_solution:
+                x, y, s = np.zeros(d[0]), np.zeros(d[1]), np.zeros(d[0])
+                res[i].x, res[i].y, res[i].s = _ptr(x, C.c_double), _ptr(y, C.c_double), _ptr(s, C.c_double)
+                bufs.append((x, y, s))
+            else:
+                bufs.append((None, None, None))
+        _check(lib().sos_solve(self.h, tol, max_iter, res), self.h)
+        out = []
+        for i in range(self.n_inst):
+            r = res[i]
+            out.append({"status": r.status, "iters": r.iters, "res_primal": r.res_primal, "res_dual": r.res_dual,
+                        "gap": r.gap, "obj_primal": r.obj_primal, "obj_dual": r.obj_dual, "tau": r.tau,
+                        "kappa": r.kappa, "x": bufs[i][0], "y": bufs[i][1], "s": bufs[i][2]})
+        return out

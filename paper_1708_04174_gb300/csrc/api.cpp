@@ -1,0 +1,694 @@
+// C-ABI of libsos: handle lifetime, device memory, the per-iteration CUDA
+// graph, the solve loop with residual checks, iterate I/O.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/sos.h"
+#include "kernels.h"
+#include "setup.h"
+
+using namespace sos;
+
+namespace {
+thread_local std::string g_setup_error;
+
+struct SmallClass {
+  int maxN;
+  int count;
+  int32_t* ids;  // device
+};
+
+template <typename T>
+struct LargeBlock {
+  int bid, N, grid;
+  LargeScratch<T> scratch;
+};
+}  // namespace
+
+struct sos_handle {
+  int32_t precision = SOS_PREC_FP64;
+  int32_t k_check = 10;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int32_t n_inst = 0;
+  int64_t NX = 0, M = 0;
+  int32_t TL = 0;
+  std::vector<InstInfo> inst;
+  std::vector<BlockDesc> blocks;
+  std::vector<void*> allocs;
+  DevPlan<double> d64;
+  DevPlan<float> d32;
+  LaunchShape shape;
+  std::vector<SmallClass> small;
+  std::vector<LargeBlock<double>> large64;
+  std::vector<LargeBlock<float>> large32;
+  int32_t* active = nullptr;  // device
+  std::vector<int32_t> active_h;
+  std::vector<int32_t> iters_h, status_h;
+  int64_t iter_count = 0;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_tried = false;
+  std::string err;
+};
+
+namespace {
+
+int set_err(sos_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return set_err(h, SOS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename V>
+int upload(sos_handle* h, const std::vector<V>& v, V** out) {
+  *out = nullptr;
+  size_t bytes = std::max<size_t>(1, v.size()) * sizeof(V);
+  void* p = nullptr;
+  CK(cudaMalloc(&p, bytes));
+  h->allocs.push_back(p);
+  if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice));
+  *out = static_cast<V*>(p);
+  return SOS_OK;
+}
+
+template <typename V>
+int alloc(sos_handle* h, size_t count, V** out) {
+  void* p = nullptr;
+  CK(cudaMalloc(&p, std::max<size_t>(1, count) * sizeof(V)));
+  CK(cudaMemset(p, 0, std::max<size_t>(1, count) * sizeof(V)));
+  h->allocs.push_back(p);
+  *out = static_cast<V*>(p);
+  return SOS_OK;
+}
+
+#define TRY(x)            \
+  do {                    \
+    int r_ = (x);         \
+    if (r_ != SOS_OK) return r_; \
+  } while (0)
+
+// Shared (type-independent) device arrays, filled once.
+struct Common {
+  const InstInfo* inst;
+  InstState* st;
+  InstResid* resid;
+  const BlockDesc* blocks;
+  const double *b, *pinv, *h2, *lr_val, *lrr_val, *lr_c, *lr_g, *linv;
+  const int32_t *row_inst, *row_ptr, *ent_row, *lr_ptr, *lr_row, *lrr_ptr, *lrr_col, *lr_inst;
+  const uint32_t* row_ent;
+  const int64_t* lr_ent;
+  double *tau, *kappa, *xP, *ylr, *zlr, *sig2, *ra, *atyl;
+  int32_t* err;
+};
+
+template <typename T>
+int make_devplan(sos_handle* h, const Common& c, int32_t max_teff, DevPlan<T>& p) {
+  p.n_inst = h->n_inst;
+  p.NX = h->NX;
+  p.M = h->M;
+  p.TL = h->TL;
+  p.max_teff = max_teff;
+  p.inst = c.inst;
+  p.st = c.st;
+  p.active = h->active;
+  p.resid = c.resid;
+  p.blocks = c.blocks;
+  p.b = c.b;
+  p.pinv = c.pinv;
+  p.h2 = c.h2;
+  p.row_inst = c.row_inst;
+  p.row_ptr = c.row_ptr;
+  p.row_ent = c.row_ent;
+  p.ent_row = c.ent_row;
+  p.lr_ptr = c.lr_ptr;
+  p.lr_row = c.lr_row;
+  p.lr_val = c.lr_val;
+  p.lrr_ptr = c.lrr_ptr;
+  p.lrr_col = c.lrr_col;
+  p.lrr_val = c.lrr_val;
+  p.lr_ent = c.lr_ent;
+  p.lr_inst = c.lr_inst;
+  p.lr_c = c.lr_c;
+  p.lr_g = c.lr_g;
+  p.linv = c.linv;
+  p.tau = c.tau;
+  p.kappa = c.kappa;
+  p.xP = c.xP;
+  p.ylr = c.ylr;
+  p.zlr = c.zlr;
+  p.sig2 = c.sig2;
+  p.ra = c.ra;
+  p.atyl = c.atyl;
+  p.err = c.err;
+  TRY(alloc(h, h->NX, &p.ux));
+  TRY(alloc(h, h->NX, &p.vx));
+  TRY(alloc(h, h->M, &p.uy));
+  TRY(alloc(h, h->M, &p.vy));
+  TRY(alloc(h, h->M, &p.uh2));
+  return SOS_OK;
+}
+
+template <typename T>
+int make_large(sos_handle* h, std::vector<LargeBlock<T>>& out, const std::vector<int>& bids) {
+  for (int bid : bids) {
+    LargeBlock<T> lb{};
+    lb.bid = bid;
+    lb.N = h->blocks[bid].N;
+    const size_t Np = lb.N + (lb.N & 1);
+    lb.grid = large_grid_size<T>(lb.N);
+    TRY(alloc(h, Np * Np, &lb.scratch.Wf));
+    TRY(alloc(h, Np * Np, &lb.scratch.B0));
+    TRY(alloc(h, Np * Np, &lb.scratch.V));
+    TRY(alloc(h, Np * Np, &lb.scratch.T1));
+    TRY(alloc(h, static_cast<size_t>(lb.grid), &lb.scratch.partial));
+    TRY(alloc(h, kMaxSweeps, &lb.scratch.flags));
+    TRY(alloc(h, 1, &lb.scratch.bar));
+    TRY(alloc(h, 1, &lb.scratch.sweeps_out));
+    TRY(alloc(h, 1, &lb.scratch.warm));
+    out.push_back(lb);
+  }
+  return SOS_OK;
+}
+
+template <typename T>
+cudaError_t enqueue_stage(sos_handle* h, const DevPlan<T>& p, std::vector<LargeBlock<T>>& large, int stage) {
+  cudaError_t e = cudaSuccess;
+  if (stage == 0 || stage == 3) {
+    e = launch_affine<T>(p, h->shape, h->stream);
+    if (e != cudaSuccess) return e;
+  }
+  if (stage == 1 || stage == 3)
+    for (auto& c : h->small) {
+      e = launch_psd_small<T>(p, c.ids, c.count, c.maxN, h->stream);
+      if (e != cudaSuccess) return e;
+    }
+  if (stage == 2 || stage == 3)
+    for (auto& lb : large) {
+      e = launch_psd_large<T>(p, lb.bid, lb.N, lb.scratch, lb.grid, h->stream);
+      if (e != cudaSuccess) return e;
+    }
+  return e;
+}
+
+cudaError_t enqueue_iteration(sos_handle* h) {
+  if (h->precision == SOS_PREC_FP64) return enqueue_stage<double>(h, h->d64, h->large64, 3);
+  return enqueue_stage<float>(h, h->d32, h->large32, 3);
+}
+
+void reset_warm(sos_handle* h) {
+  for (auto& lb : h->large64) cudaMemsetAsync(lb.scratch.warm, 0, sizeof(int32_t), h->stream);
+  for (auto& lb : h->large32) cudaMemsetAsync(lb.scratch.warm, 0, sizeof(int32_t), h->stream);
+}
+
+int check_err_word(sos_handle* h) {
+  int32_t e = 0;
+  CK(cudaMemcpyAsync(&e, h->d64.err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (e != 0) {
+    cudaMemsetAsync(h->d64.err, 0, sizeof(int32_t), h->stream);
+    return set_err(h, SOS_ERR_TIMEOUT, "a bounded device-side wait expired");
+  }
+  return SOS_OK;
+}
+
+int cold_start(sos_handle* h) {
+  std::vector<double> one(h->n_inst, 1.0);
+  CK(cudaMemcpyAsync(h->d64.tau, one.data(), sizeof(double) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d64.kappa, one.data(), sizeof(double) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
+  if (h->precision == SOS_PREC_FP64) {
+    CK(cudaMemsetAsync(h->d64.ux, 0, sizeof(double) * h->NX, h->stream));
+    CK(cudaMemsetAsync(h->d64.vx, 0, sizeof(double) * h->NX, h->stream));
+    CK(cudaMemsetAsync(h->d64.uy, 0, sizeof(double) * h->M, h->stream));
+    CK(cudaMemsetAsync(h->d64.vy, 0, sizeof(double) * h->M, h->stream));
+  } else {
+    CK(cudaMemsetAsync(h->d32.ux, 0, sizeof(float) * h->NX, h->stream));
+    CK(cudaMemsetAsync(h->d32.vx, 0, sizeof(float) * h->NX, h->stream));
+    CK(cudaMemsetAsync(h->d32.uy, 0, sizeof(float) * h->M, h->stream));
+    CK(cudaMemsetAsync(h->d32.vy, 0, sizeof(float) * h->M, h->stream));
+  }
+  std::fill(h->active_h.begin(), h->active_h.end(), 1);
+  CK(cudaMemcpyAsync(h->active, h->active_h.data(), sizeof(int32_t) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
+  std::fill(h->iters_h.begin(), h->iters_h.end(), 0);
+  std::fill(h->status_h.begin(), h->status_h.end(), SOS_RUNNING);
+  h->iter_count = 0;
+  reset_warm(h);
+  CK(cudaStreamSynchronize(h->stream));
+  return SOS_OK;
+}
+
+int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
+  HostPlan P;
+  std::string err;
+  int rc = build_plan(progs, n_progs, P, err);
+  if (rc != SOS_OK) return set_err(h, rc, err);
+  h->n_inst = P.n_inst;
+  h->NX = P.NX;
+  h->M = P.M;
+  h->TL = P.TL;
+  h->inst = P.inst;
+  h->blocks = P.blocks;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&h->shape.sms, cudaDevAttrMultiProcessorCount, dev));
+
+  Common c{};
+  InstInfo* inst;
+  TRY(upload(h, P.inst, &inst));
+  c.inst = inst;
+  InstState* st;
+  TRY(alloc(h, h->n_inst, &st));
+  c.st = st;
+  InstResid* resid;
+  TRY(alloc(h, h->n_inst, &resid));
+  c.resid = resid;
+  BlockDesc* bl;
+  TRY(upload(h, P.blocks, &bl));
+  c.blocks = bl;
+  double* dp;
+  TRY(upload(h, P.b, &dp));
+  c.b = dp;
+  TRY(upload(h, P.pinv, &dp));
+  c.pinv = dp;
+  TRY(upload(h, P.h2, &dp));
+  c.h2 = dp;
+  TRY(upload(h, P.lr_val, &dp));
+  c.lr_val = dp;
+  TRY(upload(h, P.lrr_val, &dp));
+  c.lrr_val = dp;
+  TRY(upload(h, P.lr_c, &dp));
+  c.lr_c = dp;
+  TRY(upload(h, P.lr_g, &dp));
+  c.lr_g = dp;
+  TRY(upload(h, P.linv, &dp));
+  c.linv = dp;
+  int32_t* ip;
+  TRY(upload(h, P.row_inst, &ip));
+  c.row_inst = ip;
+  TRY(upload(h, P.row_ptr, &ip));
+  c.row_ptr = ip;
+  TRY(upload(h, P.ent_row, &ip));
+  c.ent_row = ip;
+  TRY(upload(h, P.lr_ptr, &ip));
+  c.lr_ptr = ip;
+  TRY(upload(h, P.lr_row, &ip));
+  c.lr_row = ip;
+  TRY(upload(h, P.lrr_ptr, &ip));
+  c.lrr_ptr = ip;
+  TRY(upload(h, P.lrr_col, &ip));
+  c.lrr_col = ip;
+  TRY(upload(h, P.lr_inst, &ip));
+  c.lr_inst = ip;
+  uint32_t* up;
+  TRY(upload(h, P.row_ent, &up));
+  c.row_ent = up;
+  int64_t* lp;
+  TRY(upload(h, P.lr_ent, &lp));
+  c.lr_ent = lp;
+  TRY(alloc(h, h->n_inst, &c.tau));
+  TRY(alloc(h, h->n_inst, &c.kappa));
+  TRY(alloc(h, h->M, &c.xP));
+  TRY(alloc(h, h->TL, &c.ylr));
+  TRY(alloc(h, h->TL, &c.zlr));
+  TRY(alloc(h, h->M, &c.sig2));
+  TRY(alloc(h, h->M, &c.ra));
+  TRY(alloc(h, h->TL, &c.atyl));
+  TRY(alloc(h, 1, &c.err));
+  TRY(alloc(h, h->n_inst, &h->active));
+  h->active_h.assign(h->n_inst, 1);
+  h->iters_h.assign(h->n_inst, 0);
+  h->status_h.assign(h->n_inst, SOS_RUNNING);
+
+  int32_t max_teff = 0;
+  for (auto& in : P.inst) max_teff = std::max(max_teff, in.t_eff);
+
+  // projection classes: small blocks (shared-memory Jacobi) by size class, large blocks (grid Jacobi)
+  const bool fp64 = h->precision == SOS_PREC_FP64;
+  const int small_cap = psd_small_max_n(fp64);
+  const int caps[] = {16, 32, 48, 64, 96, 128, 160};
+  std::vector<std::vector<int32_t>> cls(7);
+  std::vector<int> large;
+  int max_small = 0;
+  for (int b = 0; b < static_cast<int>(P.blocks.size()); ++b) {
+    const int N = P.blocks[b].N;
+    if (N > small_cap) {
+      large.push_back(b);
+      continue;
+    }
+    for (int k = 0; k < 7; ++k)
+      if (N <= caps[k]) {
+        cls[k].push_back(b);
+        max_small = std::max(max_small, caps[k]);
+        break;
+      }
+  }
+  for (int k = 0; k < 7; ++k)
+    if (!cls[k].empty()) {
+      SmallClass sc{caps[k], static_cast<int>(cls[k].size()), nullptr};
+      TRY(upload(h, cls[k], &sc.ids));
+      h->small.push_back(sc);
+    }
+  if (fp64) {
+    TRY(make_devplan(h, c, max_teff, h->d64));
+    TRY(make_large(h, h->large64, large));
+    CK(prepare_kernels<double>(max_small, max_teff));
+  } else {
+    TRY(make_devplan(h, c, max_teff, h->d32));
+    TRY(make_large(h, h->large32, large));
+    CK(prepare_kernels<float>(max_small, max_teff));
+    // share the FP64-only pointers through d64 for the common helpers
+    h->d64.tau = c.tau;
+    h->d64.kappa = c.kappa;
+    h->d64.err = c.err;
+    h->d64.resid = c.resid;
+  }
+  h->d64.tau = c.tau;
+  h->d64.kappa = c.kappa;
+  h->d64.err = c.err;
+  h->d64.resid = c.resid;
+  return cold_start(h);
+}
+
+template <typename T>
+int copy_iterate_out(sos_handle* h, const DevPlan<T>& p, std::vector<double>& ux, std::vector<double>& vx,
+                     std::vector<double>& uy, std::vector<double>& vy, std::vector<double>& tau,
+                     std::vector<double>& kappa) {
+  std::vector<T> a(h->NX), b(h->NX), c(h->M), dd(h->M);
+  CK(cudaMemcpyAsync(a.data(), p.ux, sizeof(T) * h->NX, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(b.data(), p.vx, sizeof(T) * h->NX, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(c.data(), p.uy, sizeof(T) * h->M, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(dd.data(), p.vy, sizeof(T) * h->M, cudaMemcpyDeviceToHost, h->stream));
+  tau.resize(h->n_inst);
+  kappa.resize(h->n_inst);
+  CK(cudaMemcpyAsync(tau.data(), h->d64.tau, sizeof(double) * h->n_inst, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(kappa.data(), h->d64.kappa, sizeof(double) * h->n_inst, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  ux.assign(a.begin(), a.end());
+  vx.assign(b.begin(), b.end());
+  uy.assign(c.begin(), c.end());
+  vy.assign(dd.begin(), dd.end());
+  return SOS_OK;
+}
+
+int get_all(sos_handle* h, std::vector<double>& ux, std::vector<double>& vx, std::vector<double>& uy,
+            std::vector<double>& vy, std::vector<double>& tau, std::vector<double>& kappa) {
+  if (h->precision == SOS_PREC_FP64) return copy_iterate_out(h, h->d64, ux, vx, uy, vy, tau, kappa);
+  return copy_iterate_out(h, h->d32, ux, vx, uy, vy, tau, kappa);
+}
+
+template <typename T>
+int copy_iterate_in(sos_handle* h, const DevPlan<T>& p, const double* u, const double* v) {
+  std::vector<T> a(h->NX), b(h->NX), c(h->M), dd(h->M);
+  std::vector<double> tau(h->n_inst), kappa(h->n_inst);
+  int64_t pos = 0;
+  for (int i = 0; i < h->n_inst; ++i) {
+    const InstInfo& in = h->inst[i];
+    for (int k = 0; k < in.nx; ++k) {
+      a[in.x_off + k] = static_cast<T>(u[pos + k]);
+      b[in.x_off + k] = static_cast<T>(v[pos + k]);
+    }
+    pos += in.nx;
+    for (int k = 0; k < in.m; ++k) {
+      c[in.y_off + k] = static_cast<T>(u[pos + k]);
+      dd[in.y_off + k] = static_cast<T>(v[pos + k]);
+    }
+    pos += in.m;
+    tau[i] = u[pos];
+    kappa[i] = v[pos];
+    pos += 1;
+  }
+  CK(cudaMemcpyAsync(p.ux, a.data(), sizeof(T) * h->NX, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(p.vx, b.data(), sizeof(T) * h->NX, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(p.uy, c.data(), sizeof(T) * h->M, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(p.vy, dd.data(), sizeof(T) * h->M, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d64.tau, tau.data(), sizeof(double) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d64.kappa, kappa.data(), sizeof(double) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SOS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sos_setup(const sos_program* progs, int32_t n_progs, const sos_options* opts, sos_handle** out) {
+  if (!out) return SOS_ERR_INVALID_ARG;
+  *out = nullptr;
+  auto h = std::make_unique<sos_handle>();
+  if (opts) {
+    if (opts->precision != SOS_PREC_FP64 && opts->precision != SOS_PREC_FP32) {
+      g_setup_error = "unknown precision";
+      return SOS_ERR_INVALID_ARG;
+    }
+    h->precision = opts->precision;
+    h->k_check = opts->k_check > 0 ? opts->k_check : 10;
+    h->stream = static_cast<cudaStream_t>(opts->cuda_stream);
+  }
+  if (!h->stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      g_setup_error = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+      return SOS_ERR_CUDA;
+    }
+    h->own_stream = true;
+  }
+  int rc = build(h.get(), progs, n_progs);
+  if (rc != SOS_OK) {
+    g_setup_error = h->err;
+    sos_destroy(h.release());
+    return rc;
+  }
+  *out = h.release();
+  return SOS_OK;
+}
+
+void sos_destroy(sos_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+const char* sos_last_error(const sos_handle* h) { return h ? h->err.c_str() : g_setup_error.c_str(); }
+
+int sos_dims(const sos_handle* h, int32_t inst, int64_t dims[6]) {
+  if (!h || !dims || inst < 0 || inst >= h->n_inst) return SOS_ERR_INVALID_ARG;
+  const InstInfo& in = h->inst[inst];
+  dims[0] = in.nx;
+  dims[1] = in.m;
+  dims[2] = in.t;
+  dims[3] = in.t_eff;
+  int64_t nb = 0, ent = 0;
+  for (auto& b : h->blocks)
+    if (b.inst == inst) {
+      ++nb;
+      ent += static_cast<int64_t>(b.N) * (b.N + 1) / 2;
+    }
+  dims[4] = nb;
+  dims[5] = ent;
+  return SOS_OK;
+}
+
+int sos_iterate(sos_handle* h, int32_t iters) {
+  if (!h || iters < 0) return SOS_ERR_INVALID_ARG;
+  if (!h->graph_tried) {
+    h->graph_tried = true;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaError_t e = enqueue_iteration(h);
+      cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+      if (e == cudaSuccess && e2 == cudaSuccess && g) {
+        if (cudaGraphInstantiate(&h->graph, g, 0) != cudaSuccess) h->graph = nullptr;
+      }
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();  // clear a failed capture
+  }
+  for (int k = 0; k < iters; ++k) {
+    cudaError_t e = h->graph ? cudaGraphLaunch(h->graph, h->stream) : enqueue_iteration(h);
+    if (e != cudaSuccess) return set_err(h, SOS_ERR_CUDA, std::string("iteration launch: ") + cudaGetErrorString(e));
+  }
+  h->iter_count += iters;
+  for (int i = 0; i < h->n_inst; ++i)
+    if (h->active_h[i]) h->iters_h[i] += iters;
+  return SOS_OK;
+}
+
+int sos_sync(sos_handle* h) {
+  if (!h) return SOS_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  return check_err_word(h);
+}
+
+int sos_solve(sos_handle* h, double tol, int32_t max_iter, sos_result* results) {
+  if (!h || max_iter < 0 || !(tol > 0)) return SOS_ERR_INVALID_ARG;
+  std::vector<InstResid> R(h->n_inst);
+  std::vector<double> rp(h->n_inst, NAN), rd(h->n_inst, NAN), gp(h->n_inst, NAN), po(h->n_inst, NAN),
+      dobj(h->n_inst, NAN);
+  int32_t done = 0;
+  for (int i = 0; i < h->n_inst; ++i) done += h->active_h[i] ? 0 : 1;
+  int32_t it = 0;
+  while (it < max_iter && done < h->n_inst) {
+    const int32_t k = std::min(h->k_check, max_iter - it);
+    int rc = sos_iterate(h, k);
+    if (rc != SOS_OK) return rc;
+    it += k;
+    cudaError_t e = h->precision == SOS_PREC_FP64 ? launch_residuals<double>(h->d64, h->shape, h->stream)
+                                                  : launch_residuals<float>(h->d32, h->shape, h->stream);
+    if (e != cudaSuccess) return set_err(h, SOS_ERR_CUDA, std::string("residuals: ") + cudaGetErrorString(e));
+    CK(cudaMemcpyAsync(R.data(), h->d64.resid, sizeof(InstResid) * h->n_inst, cudaMemcpyDeviceToHost, h->stream));
+    rc = check_err_word(h);  // synchronises
+    if (rc != SOS_OK) return rc;
+    bool changed = false;
+    for (int i = 0; i < h->n_inst; ++i) {
+      if (!h->active_h[i]) continue;
+      const InstInfo& in = h->inst[i];
+      const InstResid& r = R[i];
+      int st = SOS_RUNNING;
+      double res = std::numeric_limits<double>::infinity();
+      if (r.tau > 1e-12 * (r.kappa + 1.0)) {
+        rp[i] = std::sqrt(r.pr2) / r.tau / (1.0 + in.norm_b);
+        rd[i] = std::sqrt(r.dr2) / r.tau / (1.0 + in.norm_c);
+        po[i] = r.cx / r.tau;
+        dobj[i] = r.by / r.tau;
+        gp[i] = std::fabs(po[i] - dobj[i]) / (1.0 + std::fabs(po[i]) + std::fabs(dobj[i]));
+        res = std::max(rp[i], std::max(rd[i], gp[i]));
+      }
+      const double pinf = r.by > 0 ? std::sqrt(r.aty2) / r.by : std::numeric_limits<double>::infinity();
+      const double dinf = r.cx < 0 ? std::sqrt(r.ax2) / (-r.cx) : std::numeric_limits<double>::infinity();
+      if (r.nonfinite > 0 || !std::isfinite(r.tau) || !std::isfinite(r.kappa))
+        st = SOS_NUMERICAL;
+      else if (res <= tol)
+        st = SOS_SOLVED;
+      else if (pinf <= tol)
+        st = SOS_PRIMAL_INFEASIBLE;
+      else if (dinf <= tol)
+        st = SOS_DUAL_INFEASIBLE;
+      if (st != SOS_RUNNING) {
+        h->status_h[i] = st;
+        h->active_h[i] = 0;
+        ++done;
+        changed = true;
+      }
+    }
+    if (changed)
+      CK(cudaMemcpyAsync(h->active, h->active_h.data(), sizeof(int32_t) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
+  }
+  if (!results) return SOS_OK;
+  std::vector<double> ux, vx, uy, vy, tau, kappa;
+  TRY(get_all(h, ux, vx, uy, vy, tau, kappa));
+  for (int i = 0; i < h->n_inst; ++i) {
+    sos_result& out = results[i];
+    const InstInfo& in = h->inst[i];
+    out.status = h->status_h[i] == SOS_RUNNING ? SOS_MAX_ITER : h->status_h[i];
+    out.iters = h->iters_h[i];
+    out.res_primal = rp[i];
+    out.res_dual = rd[i];
+    out.gap = gp[i];
+    out.obj_primal = po[i];
+    out.obj_dual = dobj[i];
+    out.tau = tau[i];
+    out.kappa = kappa[i];
+    const double it = tau[i] > 0 ? 1.0 / tau[i] : 0.0;
+    if (out.x)
+      for (int k = 0; k < in.nx; ++k) out.x[k] = ux[in.x_off + k] * it;
+    if (out.s)
+      for (int k = 0; k < in.nx; ++k) out.s[k] = vx[in.x_off + k] * it;
+    if (out.y)
+      for (int k = 0; k < in.m; ++k) out.y[k] = uy[in.y_off + k] * it;
+  }
+  return SOS_OK;
+}
+
+int sos_get_iterate(sos_handle* h, double* u, double* v) {
+  if (!h || !u || !v) return SOS_ERR_INVALID_ARG;
+  std::vector<double> ux, vx, uy, vy, tau, kappa;
+  TRY(get_all(h, ux, vx, uy, vy, tau, kappa));
+  int64_t pos = 0;
+  for (int i = 0; i < h->n_inst; ++i) {
+    const InstInfo& in = h->inst[i];
+    std::memcpy(u + pos, ux.data() + in.x_off, sizeof(double) * in.nx);
+    std::memcpy(v + pos, vx.data() + in.x_off, sizeof(double) * in.nx);
+    pos += in.nx;
+    std::memcpy(u + pos, uy.data() + in.y_off, sizeof(double) * in.m);
+    std::memcpy(v + pos, vy.data() + in.y_off, sizeof(double) * in.m);
+    pos += in.m;
+    u[pos] = tau[i];
+    v[pos] = kappa[i];
+    pos += 1;
+  }
+  return SOS_OK;
+}
+
+int sos_set_iterate(sos_handle* h, const double* u, const double* v) {
+  if (!h || !u || !v) return SOS_ERR_INVALID_ARG;
+  int rc = h->precision == SOS_PREC_FP64 ? copy_iterate_in(h, h->d64, u, v) : copy_iterate_in(h, h->d32, u, v);
+  if (rc != SOS_OK) return rc;
+  std::fill(h->active_h.begin(), h->active_h.end(), 1);
+  std::fill(h->iters_h.begin(), h->iters_h.end(), 0);
+  std::fill(h->status_h.begin(), h->status_h.end(), SOS_RUNNING);
+  CK(cudaMemcpyAsync(h->active, h->active_h.data(), sizeof(int32_t) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
+  reset_warm(h);
+  CK(cudaStreamSynchronize(h->stream));
+  return SOS_OK;
+}
+
+int sos_monomials(int32_t n_vars, int32_t degree, int32_t* out, int64_t capacity, int64_t* count) {
+  if (n_vars < 1 || degree < 0 || !count || capacity < 0) return SOS_ERR_INVALID_ARG;
+  *count = enumerate_monomials(n_vars, degree, out, capacity);
+  return SOS_OK;
+}
+
+int sos_host_plan(const sos_program* prog, int64_t dims[6], int32_t* ent_row, double* p_diag, double* b,
+                  double* zeta_h) {
+  if (!prog || !dims) return SOS_ERR_INVALID_ARG;
+  HostPlan P;
+  std::string err;
+  const int rc = build_plan(prog, 1, P, err);
+  if (rc != SOS_OK) {
+    g_setup_error = err;
+    return rc;
+  }
+  const InstInfo& in = P.inst[0];
+  dims[0] = in.nx;
+  dims[1] = in.m;
+  dims[2] = in.t;
+  dims[3] = in.t_eff;
+  dims[4] = static_cast<int64_t>(P.blocks.size());
+  int64_t ent = 0;
+  for (auto& bk : P.blocks) ent += static_cast<int64_t>(bk.N) * (bk.N + 1) / 2;
+  dims[5] = ent;
+  if (ent_row)
+    for (int64_t e = 0; e < in.nx; ++e) ent_row[e] = P.ent_row[e] >= 0 ? (P.ent_row[e] & ~kEntOffBit) : -1;
+  if (p_diag)
+    for (int64_t r = 0; r < in.m; ++r) p_diag[r] = 1.0 / P.pinv[r];
+  if (b)
+    for (int64_t r = 0; r < in.m; ++r) b[r] = P.b[r];
+  if (zeta_h) *zeta_h = in.zeta_h;
+  return SOS_OK;
+}
+
+void* sos_stream(sos_handle* h) { return h ? static_cast<void*>(h->stream) : nullptr; }
+
+int sos_run_stage(sos_handle* h, int32_t stage) {
+  if (!h || stage < 0 || stage > 3) return SOS_ERR_INVALID_ARG;
+  cudaError_t e = h->precision == SOS_PREC_FP64 ? enqueue_stage<double>(h, h->d64, h->large64, stage)
+                                                : enqueue_stage<float>(h, h->d32, h->large32, stage);
+  if (e != cudaSuccess) return set_err(h, SOS_ERR_CUDA, std::string("stage launch: ") + cudaGetErrorString(e));
+  return SOS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,848 @@
+// CUDA kernels of libsos for sm_103a (GB300).
+//
+// One ADMM iteration (eq. (20)) on a batch of instances is:
+//
+//   k_rows_r      r = w2hat - A w1hat, x = P^{-1} r           (eq. (27b), Appendix)
+//   k_lr_y        y = A_L^T x                                  (Appendix)
+//   k_woodbury    z = (L L^T)^{-1} y with the cached factor     (eq. (28))
+//   k_rows_sigma2 sigma_2 = x - P^{-1} A_L z                    (Appendix)
+//   k_inst_scalar Sherman-Morrison scalar, u_hat_3, tau/kappa,
+//                 free variables                                (eq. (24b), (25), (20b-c))
+//   k_rows_y      u_hat_2 = sigma_2 - s h_2; y-part of (20b-c)
+//   k_psd_*       Gram blocks: W = u_hat_1 - v, u = P_S+(W),
+//                 v = u - W                                     (eq. (20b-c))
+//
+// Identities used to avoid extra passes (exact in exact arithmetic):
+//   A_L^T sigma_2 = z            (since (I + A_L^T P^{-1} A_L) z = A_L^T P^{-1} r)
+//   u_hat_1 = w1hat - s c + A^T u_hat_2, and for a plain Gram entry
+//   W_e = u_hat_1,e - v_e = u_e + a_e u_hat_2[row(e)].
+#include <cfloat>
+#include <cstdio>
+
+#include "kernels.h"
+
+namespace sos {
+namespace {
+
+constexpr long long kSpinLimitCycles = 4000000000ll;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum; result valid in every thread.
+__device__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (w == 0) {
+    double x = (l < nw) ? sh[l] : 0.0;
+    x = warp_sum(x);
+    if (l == 0) sh[32] = x;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+template <typename T>
+__device__ __forceinline__ double d(T x) {
+  return static_cast<double>(x);
+}
+
+// ---------------------------------------------------------------------------
+// affine step
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_rows_r(DevPlan<T> p) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t a = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; a < p.M; a += stride) {
+    const int i = p.row_inst[a];
+    if (!p.active[i]) continue;
+    const double om3 = p.tau[i] + p.kappa[i];
+    double acc = d(p.uy[a]) + d(p.vy[a]) + p.b[a] * om3;  // w2hat
+    const int k1 = p.row_ptr[a + 1];
+    for (int k = p.row_ptr[a]; k < k1; ++k) {
+      const uint32_t v = p.row_ent[k];
+      const uint32_t e = v & ~kOffDiagBit;
+      const double w = d(p.ux[e]) + d(p.vx[e]);
+      acc -= (v & kOffDiagBit) ? kSqrt2 * w : w;
+    }
+    const int l1 = p.lrr_ptr[a + 1];
+    for (int k = p.lrr_ptr[a]; k < l1; ++k) {
+      const int j = p.lrr_col[k];
+      const int64_t e = p.lr_ent[j];
+      acc -= p.lrr_val[k] * (d(p.ux[e]) + d(p.vx[e]) - p.lr_c[j] * om3);
+    }
+    p.xP[a] = acc * p.pinv[a];
+  }
+}
+
+template <typename T>
+__global__ void k_lr_y(DevPlan<T> p) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int j = warp; j < p.TL; j += nwarps) {
+    if (!p.active[p.lr_inst[j]]) continue;
+    double acc = 0.0;
+    const int k1 = p.lr_ptr[j + 1];
+    for (int k = p.lr_ptr[j] + lane; k < k1; k += 32) acc += p.lr_val[k] * p.xP[p.lr_row[k]];
+    acc = warp_sum(acc);
+    if (lane == 0) p.ylr[j] = acc;
+  }
+}
+
+// z = L^{-T} L^{-1} y per instance (one CTA per instance).
+template <typename T>
+__global__ void k_woodbury(DevPlan<T> p) {
+  extern __shared__ double sh[];
+  const int i = blockIdx.x;
+  if (!p.active[i]) return;
+  const InstInfo in = p.inst[i];
+  const int te = in.t_eff;
+  if (te == 0) return;
+  double* y = sh;
+  double* q = sh + te;
+  const double* Li = p.linv + in.linv_off;
+  for (int k = threadIdx.x; k < te; k += blockDim.x) y[k] = p.ylr[in.lr_off + k];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < te; r += nw) {  // q = L^{-1} y, one warp per row
+    double acc = 0.0;
+    for (int k = lane; k <= r; k += 32) acc += Li[static_cast<int64_t>(r) * te + k] * y[k];
+    acc = warp_sum(acc);
+    if (lane == 0) q[r] = acc;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < te + 31; j += blockDim.x) {  // z = L^{-T} q, one thread per column
+    const int r0 = j & ~31;
+    double acc = 0.0;
+    for (int r = r0; r < te; ++r)
+      if (j < te && r >= j) acc += Li[static_cast<int64_t>(r) * te + j] * q[r];
+    if (j < te) p.zlr[in.lr_off + j] = acc;
+  }
+}
+
+template <typename T>
+__global__ void k_rows_sigma2(DevPlan<T> p) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t a = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; a < p.M; a += stride) {
+    if (!p.active[p.row_inst[a]]) continue;
+    double acc = 0.0;
+    const int l1 = p.lrr_ptr[a + 1];
+    for (int k = p.lrr_ptr[a]; k < l1; ++k) acc += p.lrr_val[k] * p.zlr[p.lrr_col[k]];
+    p.sig2[a] = p.xP[a] - acc * p.pinv[a];
+  }
+}
+
+// Per instance: b^T sigma_2, c^T sigma_1, Sherman-Morrison coefficient,
+// u_hat_3, the tau/kappa update and the free variables.
+template <typename T>
+__global__ void k_inst_scalar(DevPlan<T> p) {
+  __shared__ double sh[40];
+  const int i = blockIdx.x;
+  if (!p.active[i]) return;
+  const InstInfo in = p.inst[i];
+  const double tau = p.tau[i], kappa = p.kappa[i];
+  const double om3 = tau + kappa;
+  double bs = 0.0;
+  for (int a = threadIdx.x; a < in.m; a += blockDim.x) bs += p.b[in.y_off + a] * p.sig2[in.y_off + a];
+  const double bsig2 = block_sum(bs, sh);
+  double cs = 0.0;
+  for (int j = threadIdx.x; j < in.t; j += blockDim.x) {
+    const int jl = in.lr_off + j;
+    const double w = p.lr_c[jl];
+    const double w1 = d(p.ux[in.x_off + j]) + d(p.vx[in.x_off + j]) - w * om3;
+    cs += w * (w1 + p.zlr[jl]);  // c^T sigma_1, sigma_1 = w1hat + A^T sigma_2 = w1hat + z
+  }
+  const double csig1 = block_sum(cs, sh);
+  const double zs = csig1 - bsig2;                 // zeta^T sigma
+  const double s = zs / (1.0 + in.zeta_h);         // eq. (25)
+  const double uh3 = om3 + zs - s * in.zeta_h;     // eq. (24b): w3 + c^T u1 - b^T u2
+  for (int j = threadIdx.x; j < in.t; j += blockDim.x) {
+    const int jl = in.lr_off + j;
+    const double w = p.lr_c[jl];
+    const int64_t e = in.x_off + j;
+    const double wv = d(p.ux[e]) - w * (om3 + s) + p.zlr[jl] - s * p.lr_g[jl];
+    p.ux[e] = static_cast<T>(wv);  // free: projection is the identity
+    p.vx[e] = static_cast<T>(0);   // dual of a free variable is 0
+  }
+  if (threadIdx.x == 0) {
+    const double tn = fmax(uh3 - kappa, 0.0);
+    p.tau[i] = tn;
+    p.kappa[i] = kappa - uh3 + tn;
+    p.st[i].s = s;
+    p.st[i].omega3 = om3;
+    p.st[i].cs1 = csig1;
+  }
+}
+
+template <typename T>
+__global__ void k_rows_y(DevPlan<T> p) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t a = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; a < p.M; a += stride) {
+    const int i = p.row_inst[a];
+    if (!p.active[i]) continue;
+    const double uh2 = p.sig2[a] - p.st[i].s * p.h2[a];
+    const double vy = d(p.vy[a]);
+    const double un = uh2 - vy;
+    p.uy[a] = static_cast<T>(un);
+    p.vy[a] = static_cast<T>((vy - uh2) + un);
+    p.uh2[a] = static_cast<T>(uh2);
+  }
+}
+
+// Input of the PSD projection for packed entry e of block bd:
+//   plain:    W_e = u_e + a_e u_hat_2[row(e)]
+//   weighted: W_e = u_e + z_j - s g_j      (j = low-rank column of e)
+template <typename T>
+__device__ __forceinline__ T proj_input(const DevPlan<T>& p, const BlockDesc& bd, int64_t k, bool off, double s) {
+  const int64_t e = bd.x_off + k;
+  if (bd.kind == kPlain) {
+    const int row = p.ent_row[e] & ~kEntOffBit;
+    const T a = off ? static_cast<T>(kSqrt2) : static_cast<T>(1);
+    return p.ux[e] + a * p.uh2[row];
+  }
+  const int j = bd.lr_first + static_cast<int>(k);
+  return static_cast<T>(d(p.ux[e]) + p.zlr[j] - s * p.lr_g[j]);
+}
+
+__device__ __forceinline__ int64_t packed_index(int i, int j, int N) {  // i >= j
+  return static_cast<int64_t>(j) * N - static_cast<int64_t>(j) * (j - 1) / 2 + (i - j);
+}
+
+// Round-robin (circle method) pairing: pair k of round r, for Np even.
+__device__ __forceinline__ void rr_pair(int k, int r, int Np, int& a, int& b) {
+  const int m1 = Np - 1;
+  a = (k == 0) ? 0 : 1 + (k - 1 + r) % m1;
+  b = 1 + (Np - 2 - k + r) % m1;
+  if (a > b) {
+    const int t = a;
+    a = b;
+    b = t;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T rsqrt2() {
+  return static_cast<T>(0.70710678118654752440);
+}
+
+template <typename T>
+__device__ __forceinline__ T teps();
+template <>
+__device__ __forceinline__ double teps<double>() {
+  return DBL_EPSILON;
+}
+template <>
+__device__ __forceinline__ float teps<float>() {
+  return FLT_EPSILON;
+}
+
+// Rutishauser's rotation zeroing a_pq: a'_pp = a_pp - t a_pq, a'_qq = a_qq + t a_pq.
+template <typename T>
+__device__ __forceinline__ void jacobi_rot(T app, T aqq, T apq, T& c, T& s, T& t) {
+  const T theta = (aqq - app) / (static_cast<T>(2) * apq);
+  const T at = fabs(theta);
+  T tt;
+  if (at > static_cast<T>(1e150) && sizeof(T) == 8)
+    tt = static_cast<T>(0.5) / theta;
+  else if (at > static_cast<T>(1e18) && sizeof(T) == 4)
+    tt = static_cast<T>(0.5) / theta;
+  else
+    tt = static_cast<T>(1) / (at + sqrt(theta * theta + static_cast<T>(1)));
+  if (theta < 0) tt = -tt;
+  c = static_cast<T>(1) / sqrt(tt * tt + static_cast<T>(1));
+  s = tt * c;
+  t = tt;
+}
+
+// ---------------------------------------------------------------------------
+// PSD projection, small blocks: one CTA per block, cyclic Jacobi in shared
+// memory with the round-robin parallel ordering.  Each round applies Np/2
+// disjoint rotations as 2x2-block updates of A = J^T A J and column updates
+// V = V J.  A sweep without any rotation above eps |W|_F ends the solve.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* ids) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[40];
+  __shared__ int rotated;
+  const BlockDesc bd = p.blocks[ids[blockIdx.x]];
+  if (!p.active[bd.inst]) return;
+  const double s_sm = p.st[bd.inst].s;
+  const int N = bd.N, Np = N + (N & 1), ld = Np + 1, H = Np / 2;
+  T* A = reinterpret_cast<T*>(smraw);
+  T* V = A + Np * ld;
+  T* rc = V + Np * ld;
+  T* rs = rc + H;
+  T* rt = rs + H;
+  T* lam = rt + H;
+  int* rp = reinterpret_cast<int*>(lam + Np);
+  int* rq = rp + H;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  double nrm = 0.0;
+  for (int q = tid; q < Np * Np; q += nt) {
+    const int i = q / Np, j = q - i * Np;
+    V[i * ld + j] = (i == j) ? static_cast<T>(1) : static_cast<T>(0);
+    if (i >= N || j >= N) {
+      A[i * ld + j] = static_cast<T>(0);
+      continue;
+    }
+    if (i < j) continue;
+    const T w = proj_input(p, bd, packed_index(i, j, N), i != j, s_sm);
+    nrm += d(w) * d(w);
+    const T a = (i == j) ? w : w * rsqrt2<T>();
+    A[i * ld + j] = a;
+    A[j * ld + i] = a;
+  }
+  const T thr = static_cast<T>(sqrt(block_sum(nrm, red))) * teps<T>();
+
+  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    __syncthreads();  // every thread has read the previous sweep's flag
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < Np - 1; ++r) {
+      for (int k = tid; k < H; k += nt) {
+        int a, b;
+        rr_pair(k, r, Np, a, b);
+        T c = 1, s = 0, t = 0;
+        if (b < N) {
+          const T apq = A[a * ld + b];
+          if (fabs(apq) > thr) {
+            jacobi_rot(A[a * ld + a], A[b * ld + b], apq, c, s, t);
+            rotated = 1;
+          }
+        }
+        rp[k] = a;
+        rq[k] = b;
+        rc[k] = c;
+        rs[k] = s;
+        rt[k] = t;
+      }
+      __syncthreads();
+      const int nblk = H * H;
+      for (int task = tid; task < nblk + N * H; task += nt) {
+        if (task < nblk) {
+          const int k1 = task / H, k2 = task - k1 * H;
+          if (k1 > k2) continue;
+          const int p1 = rp[k1], q1 = rq[k1], p2 = rp[k2], q2 = rq[k2];
+          const T c1 = rc[k1], s1 = rs[k1];
+          if (k1 == k2) {
+            if (s1 != static_cast<T>(0)) {
+              const T apq = A[p1 * ld + q1], t1 = rt[k1];
+              A[p1 * ld + p1] -= t1 * apq;
+              A[q1 * ld + q1] += t1 * apq;
+              A[p1 * ld + q1] = static_cast<T>(0);
+              A[q1 * ld + p1] = static_cast<T>(0);
+            }
+            continue;
+          }
+          const T c2 = rc[k2], s2 = rs[k2];
+          if (s1 == static_cast<T>(0) && s2 == static_cast<T>(0)) continue;
+          const T x11 = A[p1 * ld + p2], x12 = A[p1 * ld + q2], x21 = A[q1 * ld + p2], x22 = A[q1 * ld + q2];
+          const T y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
+          const T y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
+          const T z11 = c2 * y11 - s2 * y12, z12 = s2 * y11 + c2 * y12;
+          const T z21 = c2 * y21 - s2 * y22, z22 = s2 * y21 + c2 * y22;
+          A[p1 * ld + p2] = z11;
+          A[p1 * ld + q2] = z12;
+          A[q1 * ld + p2] = z21;
+          A[q1 * ld + q2] = z22;
+          A[p2 * ld + p1] = z11;
+          A[q2 * ld + p1] = z12;
+          A[p2 * ld + q1] = z21;
+          A[q2 * ld + q1] = z22;
+        } else {
+          const int t2 = task - nblk;
+          const int row = t2 / H, k = t2 - row * H;
+          const T s = rs[k];
+          if (s == static_cast<T>(0)) continue;
+          const T c = rc[k];
+          const int pp = rp[k], qq = rq[k];
+          const T vp = V[row * ld + pp], vq = V[row * ld + qq];
+          V[row * ld + pp] = c * vp - s * vq;
+          V[row * ld + qq] = s * vp + c * vq;
+        }
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+  }
+
+  // P_S+(W) = V max(Lambda, 0) V^T; v = u - W
+  for (int k = tid; k < N; k += nt) lam[k] = fmax(A[k * ld + k], static_cast<T>(0));
+  __syncthreads();
+  for (int q = tid; q < N * N; q += nt) {
+    const int i = q / N, j = q - i * N;
+    if (i < j) continue;
+    T u = 0;
+    for (int k = 0; k < N; ++k) u += V[i * ld + k] * lam[k] * V[j * ld + k];
+    const int64_t kk = packed_index(i, j, N);
+    const T w = proj_input(p, bd, kk, i != j, s_sm);
+    if (i != j) u *= static_cast<T>(kSqrt2);
+    p.ux[bd.x_off + kk] = u;
+    p.vx[bd.x_off + kk] = u - w;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// PSD projection, large blocks: one cooperative grid per block.  Same Jacobi
+// as above with the matrix in global memory (L2 resident), warm-started
+// from the previous iteration's eigenvectors V: B = V^T W V, then sweeps on
+// B (double buffered; each round's rotations are recomputed by every task
+// from the current buffer), then U = V max(diag B, 0) V^T.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* ptr) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ptr) : "memory");
+  return v;
+}
+
+// Grid-wide barrier on a zero-initialised counter.  Bounded spin: on expiry
+// (or when another CTA already raised the error word) every CTA returns false.
+__device__ bool grid_barrier(unsigned* bar, unsigned target, int32_t* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int good = 1;
+    const long long t0 = clock64();
+    while (ld_acquire_u32(bar) < target) {
+      if (*reinterpret_cast<volatile int32_t*>(err) != 0) {
+        good = 0;
+        break;
+      }
+      if (clock64() - t0 > kSpinLimitCycles) {
+        atomicExch(err, 1);
+        good = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldg_cg(const T* ptr) {
+  return __ldcg(ptr);
+}
+
+// C tile (16x16, 256 threads) of one of:
+//   mode 0: C = A B           mode 1: C = A^T B        (A, B: Np x Np, ld Np)
+template <typename T>
+__device__ T tile_mm(const T* A, const T* B, int Np, int ti, int tj, int mode, T* sA, T* sB) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i = ti * 16 + ty, j = tj * 16 + tx;
+  T acc = 0;
+  for (int k0 = 0; k0 < Np; k0 += 16) {
+    {
+      const int r = ty, k = tx;  // element (r, k) of the A tile and (k=ty, c=tx) of the B tile
+      const int gi = ti * 16 + r, gk = k0 + k;
+      T av = 0;
+      if (gi < Np && gk < Np) av = (mode == 0) ? ldg_cg(A + static_cast<int64_t>(gi) * Np + gk)
+                                               : ldg_cg(A + static_cast<int64_t>(gk) * Np + gi);
+      sA[r * 17 + k] = av;
+      const int bk = k0 + ty, bj = tj * 16 + tx;
+      sB[ty * 17 + tx] = (bk < Np && bj < Np) ? ldg_cg(B + static_cast<int64_t>(bk) * Np + bj) : static_cast<T>(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc += sA[ty * 17 + k] * sB[k * 17 + tx];
+    __syncthreads();
+  }
+  (void)i;
+  (void)j;
+  return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeScratch<T> L) {
+  __shared__ double red[40];
+  __shared__ T sA[16 * 17], sB[16 * 17];
+  const BlockDesc bd = p.blocks[bid];
+  if (!p.active[bd.inst]) return;
+  const double s_sm = p.st[bd.inst].s;
+  const int N = bd.N, Np = N + (N & 1), H = Np / 2;
+  const int64_t gt = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t gs = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  unsigned gen = 0;
+  const unsigned G = gridDim.x;
+  int32_t* err = p.err;
+  const int warm_count = __ldcg(L.warm);
+  const bool warm = warm_count > 0 && warm_count < 256;
+  T* Wf = L.Wf;
+  T* V = L.V;
+
+  // load W (full symmetric, svec unscaled), norm, V = I when cold
+  double nrm = 0.0;
+  for (int64_t q = gt; q < static_cast<int64_t>(Np) * Np; q += gs) {
+    const int i = static_cast<int>(q / Np), j = static_cast<int>(q - static_cast<int64_t>(i) * Np);
+    if (!warm) V[q] = (i == j) ? static_cast<T>(1) : static_cast<T>(0);
+    if (i >= N || j >= N) {
+      Wf[q] = static_cast<T>(0);
+      continue;
+    }
+    const int ii = i >= j ? i : j, jj = i >= j ? j : i;
+    const T w = proj_input(p, bd, packed_index(ii, jj, N), ii != jj, s_sm);
+    if (i >= j) nrm += d(w) * d(w);
+    Wf[q] = (i == j) ? w : w * rsqrt2<T>();
+  }
+  const double part = block_sum(nrm, red);
+  if (threadIdx.x == 0) L.partial[blockIdx.x] = part;
+  if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+  double tot = 0.0;
+  for (unsigned c = 0; c < G; ++c) tot += __ldcg(L.partial + c);
+  const T thr = static_cast<T>(sqrt(tot)) * teps<T>();
+
+  const int nt = (Np + 15) / 16;
+  T* cur = Wf;
+  T* nxt = L.B0;
+  if (warm) {
+    for (int tile = blockIdx.x; tile < nt * nt; tile += G) {  // T1 = W V
+      const int ti = tile / nt, tj = tile - ti * nt;
+      const T v = tile_mm(Wf, V, Np, ti, tj, 0, sA, sB);
+      const int i = ti * 16 + (threadIdx.x >> 4), j = tj * 16 + (threadIdx.x & 15);
+      if (i < Np && j < Np) L.T1[static_cast<int64_t>(i) * Np + j] = v;
+    }
+    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    for (int tile = blockIdx.x; tile < nt * nt; tile += G) {  // B = V^T T1 (lower tiles, mirrored)
+      const int ti = tile / nt, tj = tile - ti * nt;
+      if (ti < tj) continue;
+      const T v = tile_mm(V, L.T1, Np, ti, tj, 1, sA, sB);
+      const int i = ti * 16 + (threadIdx.x >> 4), j = tj * 16 + (threadIdx.x & 15);
+      if (i < Np && j < Np && i >= j) {
+        Wf[static_cast<int64_t>(i) * Np + j] = v;
+        Wf[static_cast<int64_t>(j) * Np + i] = v;
+      }
+    }
+    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+  }
+
+  int sweeps = 0;
+  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    for (int r = 0; r < Np - 1; ++r) {
+      const int64_t nblk = static_cast<int64_t>(H) * H;
+      for (int64_t task = gt; task < nblk + static_cast<int64_t>(N) * H; task += gs) {
+        if (task < nblk) {
+          const int k1 = static_cast<int>(task / H), k2 = static_cast<int>(task - static_cast<int64_t>(k1) * H);
+          if (k1 > k2) continue;
+          int p1, q1, p2, q2;
+          rr_pair(k1, r, Np, p1, q1);
+          rr_pair(k2, r, Np, p2, q2);
+          T c1 = 1, s1 = 0, t1 = 0, c2 = 1, s2 = 0, t2 = 0;
+          const T a1 = ldg_cg(cur + static_cast<int64_t>(p1) * Np + q1);
+          if (q1 < N && fabs(a1) > thr)
+            jacobi_rot(ldg_cg(cur + static_cast<int64_t>(p1) * Np + p1), ldg_cg(cur + static_cast<int64_t>(q1) * Np + q1),
+                       a1, c1, s1, t1);
+          if (k1 == k2) {
+            const T app = ldg_cg(cur + static_cast<int64_t>(p1) * Np + p1);
+            const T aqq = ldg_cg(cur + static_cast<int64_t>(q1) * Np + q1);
+            if (s1 != static_cast<T>(0)) {
+              nxt[static_cast<int64_t>(p1) * Np + p1] = app - t1 * a1;
+              nxt[static_cast<int64_t>(q1) * Np + q1] = aqq + t1 * a1;
+              nxt[static_cast<int64_t>(p1) * Np + q1] = static_cast<T>(0);
+              nxt[static_cast<int64_t>(q1) * Np + p1] = static_cast<T>(0);
+              L.flags[sweep] = 1;
+            } else {
+              nxt[static_cast<int64_t>(p1) * Np + p1] = app;
+              nxt[static_cast<int64_t>(q1) * Np + q1] = aqq;
+              nxt[static_cast<int64_t>(p1) * Np + q1] = a1;
+              nxt[static_cast<int64_t>(q1) * Np + p1] = a1;
+            }
+            continue;
+          }
+          const T a2 = ldg_cg(cur + static_cast<int64_t>(p2) * Np + q2);
+          if (q2 < N && fabs(a2) > thr)
+            jacobi_rot(ldg_cg(cur + static_cast<int64_t>(p2) * Np + p2), ldg_cg(cur + static_cast<int64_t>(q2) * Np + q2),
+                       a2, c2, s2, t2);
+          const T x11 = ldg_cg(cur + static_cast<int64_t>(p1) * Np + p2);
+          const T x12 = ldg_cg(cur + static_cast<int64_t>(p1) * Np + q2);
+          const T x21 = ldg_cg(cur + static_cast<int64_t>(q1) * Np + p2);
+          const T x22 = ldg_cg(cur + static_cast<int64_t>(q1) * Np + q2);
+          const T y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
+          const T y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
+          const T z11 = c2 * y11 - s2 * y12, z12 = s2 * y11 + c2 * y12;
+          const T z21 = c2 * y21 - s2 * y22, z22 = s2 * y21 + c2 * y22;
+          nxt[static_cast<int64_t>(p1) * Np + p2] = z11;
+          nxt[static_cast<int64_t>(p1) * Np + q2] = z12;
+          nxt[static_cast<int64_t>(q1) * Np + p2] = z21;
+          nxt[static_cast<int64_t>(q1) * Np + q2] = z22;
+          nxt[static_cast<int64_t>(p2) * Np + p1] = z11;
+          nxt[static_cast<int64_t>(q2) * Np + p1] = z12;
+          nxt[static_cast<int64_t>(p2) * Np + q1] = z21;
+          nxt[static_cast<int64_t>(q2) * Np + q1] = z22;
+        } else {
+          const int64_t t2i = task - nblk;
+          const int row = static_cast<int>(t2i / H), k = static_cast<int>(t2i - static_cast<int64_t>(row) * H);
+          int pp, qq;
+          rr_pair(k, r, Np, pp, qq);
+          if (qq >= N) continue;
+          const T apq = ldg_cg(cur + static_cast<int64_t>(pp) * Np + qq);
+          if (!(fabs(apq) > thr)) continue;
+          T c, s, t;
+          jacobi_rot(ldg_cg(cur + static_cast<int64_t>(pp) * Np + pp), ldg_cg(cur + static_cast<int64_t>(qq) * Np + qq), apq,
+                     c, s, t);
+          T* vr = V + static_cast<int64_t>(row) * Np;
+          const T vp = ldg_cg(vr + pp), vq = ldg_cg(vr + qq);
+          vr[pp] = c * vp - s * vq;
+          vr[qq] = s * vp + c * vq;
+        }
+      }
+      if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+      T* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+    }
+    sweeps = sweep + 1;
+    const int any = __ldcg(L.flags + sweep);
+    if (!any) break;
+  }
+
+  // U = V max(diag B, 0) V^T on lower tiles; write u and v = u - W
+  const int ntl = (N + 15) / 16;
+  for (int tile = blockIdx.x; tile < ntl * ntl; tile += G) {
+    const int ti = tile / ntl, tj = tile - ti * ntl;
+    if (ti < tj) continue;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i = ti * 16 + ty, j = tj * 16 + tx;
+    T acc = 0;
+    for (int k0 = 0; k0 < N; k0 += 16) {
+      const int gk = k0 + tx;
+      const int ri = ti * 16 + ty, rj = tj * 16 + ty;
+      T lk = 0;
+      if (gk < N) lk = fmax(ldg_cg(cur + static_cast<int64_t>(gk) * Np + gk), static_cast<T>(0));
+      sA[ty * 17 + tx] = (ri < N && gk < N) ? ldg_cg(V + static_cast<int64_t>(ri) * Np + gk) * lk : static_cast<T>(0);
+      sB[ty * 17 + tx] = (rj < N && gk < N) ? ldg_cg(V + static_cast<int64_t>(rj) * Np + gk) : static_cast<T>(0);
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc += sA[ty * 17 + k] * sB[tx * 17 + k];
+      __syncthreads();
+    }
+    if (i < N && j < N && i >= j) {
+      const int64_t kk = packed_index(i, j, N);
+      const T w = proj_input(p, bd, kk, i != j, s_sm);
+      const T u = (i != j) ? acc * static_cast<T>(kSqrt2) : acc;
+      p.ux[bd.x_off + kk] = u;
+      p.vx[bd.x_off + kk] = u - w;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *L.sweeps_out = sweeps;
+    *L.warm = warm ? warm_count + 1 : 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// residuals (every k_check iterations)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_res_rows(DevPlan<T> p) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t a = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; a < p.M; a += stride) {
+    if (!p.active[p.row_inst[a]]) continue;
+    double acc = 0.0;
+    const int k1 = p.row_ptr[a + 1];
+    for (int k = p.row_ptr[a]; k < k1; ++k) {
+      const uint32_t v = p.row_ent[k];
+      const double x = d(p.ux[v & ~kOffDiagBit]);
+      acc += (v & kOffDiagBit) ? kSqrt2 * x : x;
+    }
+    const int l1 = p.lrr_ptr[a + 1];
+    for (int k = p.lrr_ptr[a]; k < l1; ++k) acc += p.lrr_val[k] * d(p.ux[p.lr_ent[p.lrr_col[k]]]);
+    p.ra[a] = acc;  // (A u_xi)_a
+  }
+}
+
+template <typename T>
+__global__ void k_res_lr(DevPlan<T> p) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int j = warp; j < p.TL; j += nwarps) {
+    if (!p.active[p.lr_inst[j]]) continue;
+    double acc = 0.0;
+    const int k1 = p.lr_ptr[j + 1];
+    for (int k = p.lr_ptr[j] + lane; k < k1; k += 32) acc += p.lr_val[k] * d(p.uy[p.lr_row[k]]);
+    acc = warp_sum(acc);
+    if (lane == 0) p.atyl[j] = acc;  // (A_L^T u_y)_j
+  }
+}
+
+template <typename T>
+__global__ void k_res_inst(DevPlan<T> p) {
+  __shared__ double sh[40];
+  const int i = blockIdx.x;
+  if (!p.active[i]) return;
+  const InstInfo in = p.inst[i];
+  const double tau = p.tau[i];
+  double pr = 0, ax = 0, by = 0, bad = 0;
+  for (int a = threadIdx.x; a < in.m; a += blockDim.x) {
+    const int64_t g = in.y_off + a;
+    const double axv = p.ra[g];
+    const double r = axv - p.b[g] * tau;
+    pr += r * r;
+    ax += axv * axv;
+    const double uy = d(p.uy[g]);
+    by += p.b[g] * uy;
+    if (!isfinite(uy) || !isfinite(axv)) bad += 1.0;
+  }
+  double dr = 0, aty = 0, cx = 0;
+  for (int k = threadIdx.x; k < in.nx; k += blockDim.x) {
+    const int64_t e = in.x_off + k;
+    const int er = p.ent_row[e];
+    double at, c = 0.0;
+    if (er >= 0) {  // plain Gram entry: one nonzero a_e (1 or sqrt 2) at its row
+      const double u = d(p.uy[er & ~kEntOffBit]);
+      at = (er & kEntOffBit) ? kSqrt2 * u : u;
+    } else {  // low-rank column j
+      const int j = -er - 1;
+      at = p.atyl[j];
+      c = p.lr_c[j];
+    }
+    const double vz = d(p.vx[e]);
+    const double ux = d(p.ux[e]);
+    if (!isfinite(vz) || !isfinite(ux)) bad += 1.0;
+    const double q = at + vz;
+    dr += (q - c * tau) * (q - c * tau);
+    aty += q * q;
+    cx += c * ux;
+  }
+  const double spr = block_sum(pr, sh), sax = block_sum(ax, sh), sby = block_sum(by, sh);
+  const double sdr = block_sum(dr, sh), saty = block_sum(aty, sh), scx = block_sum(cx, sh);
+  const double sbad = block_sum(bad, sh);
+  if (threadIdx.x == 0) {
+    InstResid R;
+    R.tau = tau;
+    R.kappa = p.kappa[i];
+    R.pr2 = spr;
+    R.ax2 = sax;
+    R.by = sby;
+    R.dr2 = sdr;
+    R.aty2 = saty;
+    R.cx = scx;
+    R.nonfinite = sbad;
+    p.resid[i] = R;
+  }
+}
+
+int grid_for(int64_t n, int threads, int sms) {
+  int64_t g = (n + threads - 1) / threads;
+  const int64_t cap = static_cast<int64_t>(sms) * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_affine(const DevPlan<T>& p, const LaunchShape& ls, cudaStream_t s) {
+  const int rt = ls.row_threads;
+  k_rows_r<T><<<grid_for(p.M, rt, ls.sms), rt, 0, s>>>(p);
+  if (p.TL > 0) {
+    k_lr_y<T><<<grid_for(static_cast<int64_t>(p.TL) * 32, 256, ls.sms), 256, 0, s>>>(p);
+    const size_t wsm = sizeof(double) * 2 * static_cast<size_t>(p.max_teff > 0 ? p.max_teff : 1);
+    k_woodbury<T><<<p.n_inst, 256, wsm, s>>>(p);
+  }
+  k_rows_sigma2<T><<<grid_for(p.M, rt, ls.sms), rt, 0, s>>>(p);
+  k_inst_scalar<T><<<p.n_inst, ls.inst_threads, 0, s>>>(p);
+  k_rows_y<T><<<grid_for(p.M, rt, ls.sms), rt, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+size_t psd_small_smem_bytes(int maxN, bool fp64) {
+  const int Np = maxN + (maxN & 1), ld = Np + 1, H = Np / 2;
+  const size_t es = fp64 ? 8 : 4;
+  return es * (2 * static_cast<size_t>(Np) * ld + 3 * H + Np) + sizeof(int) * 2 * H;
+}
+
+int psd_small_max_n(bool fp64) { return fp64 ? 96 : 160; }
+
+template <typename T>
+cudaError_t launch_psd_small(const DevPlan<T>& p, const int32_t* ids, int count, int maxN, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const size_t sm = psd_small_smem_bytes(maxN, sizeof(T) == 8);
+  k_psd_small<T><<<count, 256, sm, s>>>(p, ids);
+  return cudaGetLastError();
+}
+
+template <typename T>
+int large_grid_size(int N) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_psd_large<T>, 256, 0);
+  if (per < 1) per = 1;
+  int g = sms * (per > 2 ? 2 : per);
+  (void)N;
+  return g;
+}
+
+template <typename T>
+cudaError_t launch_psd_large(const DevPlan<T>& p, int bid, int N, const LargeScratch<T>& ls, int grid, cudaStream_t s) {
+  (void)N;
+  cudaError_t e = cudaMemsetAsync(ls.bar, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(ls.flags, 0, sizeof(int32_t) * kMaxSweeps, s);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_psd_large<T>, p, bid, ls);
+}
+
+template <typename T>
+cudaError_t launch_residuals(const DevPlan<T>& p, const LaunchShape& ls, cudaStream_t s) {
+  k_res_rows<T><<<grid_for(p.M, ls.row_threads, ls.sms), ls.row_threads, 0, s>>>(p);
+  if (p.TL > 0) k_res_lr<T><<<grid_for(static_cast<int64_t>(p.TL) * 32, 256, ls.sms), 256, 0, s>>>(p);
+  k_res_inst<T><<<p.n_inst, 512, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t prepare_kernels(int max_small_n, int max_teff) {
+  cudaError_t e = cudaSuccess;
+  if (max_small_n > 0) {
+    const size_t sm = psd_small_smem_bytes(max_small_n, sizeof(T) == 8);
+    e = cudaFuncSetAttribute(k_psd_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+    if (e != cudaSuccess) return e;
+  }
+  const size_t wsm = sizeof(double) * 2 * static_cast<size_t>(max_teff > 0 ? max_teff : 1);
+  if (wsm > 48 * 1024) e = cudaFuncSetAttribute(k_woodbury<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(wsm));
+  return e;
+}
+
+#define SOS_INSTANTIATE(T)                                                                                \
+  template cudaError_t launch_affine<T>(const DevPlan<T>&, const LaunchShape&, cudaStream_t);             \
+  template cudaError_t launch_psd_small<T>(const DevPlan<T>&, const int32_t*, int, int, cudaStream_t);    \
+  template cudaError_t launch_psd_large<T>(const DevPlan<T>&, int, int, const LargeScratch<T>&, int,      \
+                                           cudaStream_t);                                                 \
+  template int large_grid_size<T>(int);                                                                   \
+  template cudaError_t prepare_kernels<T>(int, int);                                                      \
+  template cudaError_t launch_residuals<T>(const DevPlan<T>&, const LaunchShape&, cudaStream_t);
+
+SOS_INSTANTIATE(double)
+SOS_INSTANTIATE(float)
+
+}  // namespace sos

@@ -1,0 +1,100 @@
+// Device kernels of libsos and their launch wrappers (host-callable).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sos_plan.h"
+
+namespace sos {
+
+// Device pointers of one problem set; T is the iterate type (double for the
+// plain FP64 form, float for the FP32 form).  Woodbury data, tau/kappa and
+// every reduction stay in FP64.
+template <typename T>
+struct DevPlan {
+  int32_t n_inst = 0;
+  int64_t NX = 0, M = 0;
+  int32_t TL = 0;
+  int32_t max_teff = 0;
+  const InstInfo* inst = nullptr;
+  InstState* st = nullptr;
+  const int32_t* active = nullptr;  // 1 while the instance iterates
+  InstResid* resid = nullptr;
+  const BlockDesc* blocks = nullptr;
+  const double* b = nullptr;
+  const double* pinv = nullptr;
+  const double* h2 = nullptr;
+  const int32_t* row_inst = nullptr;
+  const int32_t* row_ptr = nullptr;
+  const uint32_t* row_ent = nullptr;
+  const int32_t* ent_row = nullptr;   // plain: row | kEntOffBit if off-diagonal; low-rank: -(column + 1)
+  const int32_t* lr_ptr = nullptr;
+  const int32_t* lr_row = nullptr;
+  const double* lr_val = nullptr;
+  const int32_t* lrr_ptr = nullptr;
+  const int32_t* lrr_col = nullptr;
+  const double* lrr_val = nullptr;
+  const int64_t* lr_ent = nullptr;
+  const int32_t* lr_inst = nullptr;
+  const double* lr_c = nullptr;
+  const double* lr_g = nullptr;
+  const double* linv = nullptr;
+  // iterates
+  T* ux = nullptr;
+  T* vx = nullptr;
+  T* uy = nullptr;
+  T* vy = nullptr;
+  double* tau = nullptr;
+  double* kappa = nullptr;
+  // per-iteration work
+  double* xP = nullptr;    // P^{-1} r (M)
+  double* ylr = nullptr;   // A_L^T P^{-1} r (TL)
+  double* zlr = nullptr;   // core^{-1} ylr (TL)
+  double* sig2 = nullptr;  // sigma_2 (M)
+  T* uh2 = nullptr;        // u_hat_2 (M)
+  double* ra = nullptr;    // residual work (M)
+  double* atyl = nullptr;  // residual work (TL)
+  int32_t* err = nullptr;  // device error word (nonzero: a bounded wait expired)
+};
+
+// Scratch of the large-block (cooperative) projection, one per large block.
+template <typename T>
+struct LargeScratch {
+  T* Wf = nullptr;   // Np x Np symmetric input
+  T* B0 = nullptr;   // Jacobi working matrix (double buffered)
+  T* B1 = nullptr;
+  T* V = nullptr;    // eigenvectors, kept across iterations (warm start)
+  T* T1 = nullptr;   // GEMM temporary
+  double* partial = nullptr;   // per-CTA partial sums
+  int32_t* flags = nullptr;    // per-sweep rotation flags [kMaxSweeps]
+  uint32_t* bar = nullptr;     // grid barrier counter (zeroed before each launch)
+  int32_t* sweeps_out = nullptr;  // number of sweeps of the last launch
+  int32_t* warm = nullptr;     // 1 if V holds the previous eigenvectors
+};
+
+constexpr int kMaxSweeps = 40;
+
+struct LaunchShape {
+  int sms = 152;
+  int row_threads = 256;
+  int inst_threads = 256;
+};
+
+template <typename T>
+cudaError_t launch_affine(const DevPlan<T>& p, const LaunchShape& ls, cudaStream_t s);
+template <typename T>
+cudaError_t launch_psd_small(const DevPlan<T>& p, const int32_t* ids, int count, int maxN, cudaStream_t s);
+template <typename T>
+cudaError_t launch_psd_large(const DevPlan<T>& p, int bid, int N, const LargeScratch<T>& ls, int grid,
+                             cudaStream_t s);
+template <typename T>
+int large_grid_size(int N);
+template <typename T>
+cudaError_t prepare_kernels(int max_small_n, int max_teff);
+template <typename T>
+cudaError_t launch_residuals(const DevPlan<T>& p, const LaunchShape& ls, cudaStream_t s);
+size_t psd_small_smem_bytes(int maxN, bool fp64);
+int psd_small_max_n(bool fp64);
+
+}  // namespace sos

@@ -1,0 +1,479 @@
+// Host-side setup of libsos: coefficient matching, index map, column classes,
+// Woodbury core factorisation and Sherman-Morrison data.
+//
+// Paper references: coefficient matching eq. (11)-(12); indicator matrices
+// B_alpha eq. (8) (a Gram entry (i, j) belongs to row beta_i + beta_j);
+// weighted blocks eq. (38)-(40) (row beta_i + beta_j + delta for every term of
+// the weight); Prop. 1 / Prop. 3 (plain Gram columns are orthogonal, so
+// P = I + A_D A_D^T is diagonal); eq. (28) and the Appendix (Woodbury with a
+// cached Cholesky factor of I + A_L^T P^{-1} A_L); eq. (25) (h = M^{-1} zeta).
+#include "setup.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <thread>
+
+namespace sos {
+namespace {
+
+// ---------------------------------------------------------------------------
+// exponent-vector hash table (open addressing, FNV-1a over the int32 digits)
+// ---------------------------------------------------------------------------
+class ExpTable {
+ public:
+  ExpTable(int n_vars, const int32_t* exps, int32_t count) : n_(n_vars), exps_(exps), count_(count) {
+    size_t cap = 16;
+    while (cap < 2 * static_cast<size_t>(count) + 1) cap <<= 1;
+    slots_.assign(cap, -1);
+    mask_ = cap - 1;
+  }
+  // Inserts all rows; returns false on a duplicate.
+  bool build() {
+    for (int32_t r = 0; r < count_; ++r) {
+      const int32_t* e = exps_ + static_cast<int64_t>(r) * n_;
+      size_t s = hash(e) & mask_;
+      while (slots_[s] >= 0) {
+        if (equal(e, exps_ + static_cast<int64_t>(slots_[s]) * n_)) return false;
+        s = (s + 1) & mask_;
+      }
+      slots_[s] = r;
+    }
+    return true;
+  }
+  int32_t find(const int32_t* e) const {
+    size_t s = hash(e) & mask_;
+    while (slots_[s] >= 0) {
+      if (equal(e, exps_ + static_cast<int64_t>(slots_[s]) * n_)) return slots_[s];
+      s = (s + 1) & mask_;
+    }
+    return -1;
+  }
+
+ private:
+  size_t hash(const int32_t* e) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int i = 0; i < n_; ++i) {
+      uint32_t v = static_cast<uint32_t>(e[i]);
+      for (int k = 0; k < 4; ++k) {
+        h ^= (v >> (8 * k)) & 0xffu;
+        h *= 1099511628211ull;
+      }
+    }
+    return static_cast<size_t>(h ^ (h >> 29));
+  }
+  bool equal(const int32_t* a, const int32_t* b) const { return std::memcmp(a, b, sizeof(int32_t) * n_) == 0; }
+  int n_;
+  const int32_t* exps_;
+  int32_t count_;
+  std::vector<int32_t> slots_;
+  size_t mask_;
+};
+
+struct LocalBlock {
+  int64_t x_off;
+  int32_t N, kind, lr_first;
+};
+
+// One instance, all indices local to it.
+struct Local {
+  int32_t nx = 0, m = 0, t = 0, t_eff = 0;
+  std::vector<double> b, P, h2, g, linv, lr_c;
+  std::vector<int32_t> ent_row;                 // nx
+  std::vector<std::vector<std::pair<int32_t, double>>> cols;  // low-rank columns (row, value)
+  std::vector<int32_t> lr_ent;
+  std::vector<std::vector<uint32_t>> row_plain; // per row: entries | offdiag bit
+  std::vector<LocalBlock> blocks;
+  double zeta_h = 0, norm_b = 0, norm_c = 0;
+  int code = SOS_OK;
+  std::string err;
+};
+
+int fail(Local& L, int code, const std::string& msg) {
+  L.code = code;
+  L.err = msg;
+  return code;
+}
+
+// Dense FP64 Cholesky C = L L^T (row-major, lower), in place.  false if not SPD.
+bool cholesky(std::vector<double>& C, int n) {
+  for (int j = 0; j < n; ++j) {
+    double d = C[static_cast<size_t>(j) * n + j];
+    for (int k = 0; k < j; ++k) d -= C[static_cast<size_t>(j) * n + k] * C[static_cast<size_t>(j) * n + k];
+    if (!(d > 0.0) || !std::isfinite(d)) return false;
+    d = std::sqrt(d);
+    C[static_cast<size_t>(j) * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double s = C[static_cast<size_t>(i) * n + j];
+      for (int k = 0; k < j; ++k) s -= C[static_cast<size_t>(i) * n + k] * C[static_cast<size_t>(j) * n + k];
+      C[static_cast<size_t>(i) * n + j] = s / d;
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) C[static_cast<size_t>(i) * n + j] = 0.0;
+  return true;
+}
+
+// Inverse of a lower-triangular matrix (row-major), FP64.
+std::vector<double> tri_inverse(const std::vector<double>& Lm, int n) {
+  std::vector<double> X(static_cast<size_t>(n) * n, 0.0);
+  for (int j = 0; j < n; ++j) {  // column j of L^{-1}: solve L x = e_j
+    X[static_cast<size_t>(j) * n + j] = 1.0 / Lm[static_cast<size_t>(j) * n + j];
+    for (int i = j + 1; i < n; ++i) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s += Lm[static_cast<size_t>(i) * n + k] * X[static_cast<size_t>(k) * n + j];
+      X[static_cast<size_t>(i) * n + j] = -s / Lm[static_cast<size_t>(i) * n + i];
+    }
+  }
+  return X;
+}
+
+int build_instance(const sos_program& pg, Local& L) {
+  const int nv = pg.n_vars;
+  if (nv < 1) return fail(L, SOS_ERR_INVALID_ARG, "n_vars must be >= 1");
+  if (pg.t < 0 || (pg.t > 0 && !pg.w)) return fail(L, SOS_ERR_INVALID_ARG, "t < 0 or w missing");
+  if (pg.n_constraints < 1 || !pg.constraints) return fail(L, SOS_ERR_INVALID_ARG, "no constraints");
+  L.t = pg.t;
+
+  // rows of every constraint, concatenated
+  std::vector<int32_t> row_base(pg.n_constraints);
+  std::vector<ExpTable> tables;
+  tables.reserve(pg.n_constraints);
+  int32_t m = 0;
+  for (int j = 0; j < pg.n_constraints; ++j) {
+    const sos_constraint& c = pg.constraints[j];
+    if (c.n_rows < 1 || !c.row_exps) return fail(L, SOS_ERR_INVALID_ARG, "constraint without rows");
+    row_base[j] = m;
+    m += c.n_rows;
+    tables.emplace_back(nv, c.row_exps, c.n_rows);
+    if (!tables.back().build()) return fail(L, SOS_ERR_INVALID_ARG, "duplicate row monomial");
+  }
+  L.m = m;
+  L.b.assign(m, 0.0);
+  L.row_plain.assign(m, {});
+
+  // packed x layout: free u, then every block of every constraint
+  int64_t nx = pg.t;
+  for (int j = 0; j < pg.n_constraints; ++j)
+    for (int k = 0; k < pg.constraints[j].n_blocks; ++k) {
+      const sos_block& bk = pg.constraints[j].blocks[k];
+      if (bk.N < 1 || !bk.basis_exps) return fail(L, SOS_ERR_INVALID_ARG, "block with N < 1");
+      nx += static_cast<int64_t>(bk.N) * (bk.N + 1) / 2;
+    }
+  if (nx > (1ll << 30)) return fail(L, SOS_ERR_UNSUPPORTED, "instance too large");
+  L.nx = static_cast<int32_t>(nx);
+  L.ent_row.assign(L.nx, -1);
+
+  // free columns (A_1) and b, coefficient matching eq. (11)
+  std::vector<std::map<int32_t, double>> freecols(pg.t);
+  for (int j = 0; j < pg.n_constraints; ++j) {
+    const sos_constraint& c = pg.constraints[j];
+    for (int64_t k = 0; k < c.n_terms; ++k) {
+      int32_t p = c.term_poly[k];
+      if (p < 0 || p > pg.t) return fail(L, SOS_ERR_INVALID_ARG, "term_poly out of range");
+      int32_t r = tables[j].find(c.term_exps + k * nv);
+      if (r < 0) return fail(L, SOS_ERR_INVALID_ARG, "a term of g_i is not among the constraint's rows");
+      r += row_base[j];
+      if (p == 0)
+        L.b[r] += c.term_coef[k];
+      else
+        freecols[p - 1][r] += c.term_coef[k];
+    }
+  }
+  for (int i = 0; i < pg.t; ++i) {
+    std::vector<std::pair<int32_t, double>> col;
+    for (auto& kv : freecols[i])
+      if (kv.second != 0.0) col.push_back(kv);
+    L.cols.push_back(std::move(col));
+    L.lr_ent.push_back(i);
+    L.lr_c.push_back(pg.w[i]);
+  }
+
+  // Gram blocks: index map of eq. (8) / eq. (38)
+  std::vector<int32_t> sum(nv);
+  int64_t xo = pg.t;
+  for (int j = 0; j < pg.n_constraints; ++j) {
+    const sos_constraint& c = pg.constraints[j];
+    for (int k = 0; k < c.n_blocks; ++k) {
+      const sos_block& bk = c.blocks[k];
+      const int N = bk.N;
+      const bool weighted = bk.n_weight_terms > 0;
+      LocalBlock lb{xo, N, weighted ? kWeighted : kPlain, weighted ? static_cast<int32_t>(L.cols.size()) : -1};
+      L.blocks.push_back(lb);
+      int64_t e = xo;
+      for (int jj = 0; jj < N; ++jj) {
+        const int32_t* bj = bk.basis_exps + static_cast<int64_t>(jj) * nv;
+        for (int ii = jj; ii < N; ++ii, ++e) {
+          const int32_t* bi = bk.basis_exps + static_cast<int64_t>(ii) * nv;
+          for (int q = 0; q < nv; ++q) sum[q] = bi[q] + bj[q];
+          const bool off = ii != jj;
+          if (!weighted) {
+            int32_t r = tables[j].find(sum.data());
+            if (r < 0) return fail(L, SOS_ERR_INVALID_ARG, "a Gram product monomial is not among the rows");
+            r += row_base[j];
+            L.ent_row[e] = r | (off ? kEntOffBit : 0);
+            L.row_plain[r].push_back(static_cast<uint32_t>(e) | (off ? kOffDiagBit : 0u));
+          } else {
+            std::vector<std::pair<int32_t, double>> col;
+            std::vector<int32_t> s2(nv);
+            for (int w = 0; w < bk.n_weight_terms; ++w) {
+              const int32_t* d = bk.weight_exps + static_cast<int64_t>(w) * nv;
+              for (int q = 0; q < nv; ++q) s2[q] = sum[q] + d[q];
+              int32_t r = tables[j].find(s2.data());
+              if (r < 0) return fail(L, SOS_ERR_INVALID_ARG, "a weighted Gram product monomial is not among the rows");
+              col.emplace_back(r + row_base[j], bk.weight_coef[w] * (off ? kSqrt2 : 1.0));
+            }
+            std::sort(col.begin(), col.end());
+            std::vector<std::pair<int32_t, double>> merged;
+            for (auto& p : col) {
+              if (!merged.empty() && merged.back().first == p.first)
+                merged.back().second += p.second;
+              else
+                merged.push_back(p);
+            }
+            L.cols.push_back(std::move(merged));
+            L.lr_ent.push_back(static_cast<int32_t>(e));
+            L.lr_c.push_back(0.0);
+          }
+        }
+      }
+      xo = e;
+    }
+  }
+  const int te = static_cast<int>(L.cols.size());
+  L.t_eff = te;
+
+  // P = I + A_D A_D^T, diagonal by Prop. 1 (svec: 1 per diagonal, 2 per off-diagonal entry)
+  L.P.assign(m, 1.0);
+  for (int32_t r = 0; r < m; ++r)
+    for (uint32_t v : L.row_plain[r]) L.P[r] += (v & kOffDiagBit) ? 2.0 : 1.0;
+
+  // low-rank rows
+  std::vector<std::vector<std::pair<int32_t, double>>> lrrows(m);
+  for (int jc = 0; jc < te; ++jc)
+    for (auto& p : L.cols[jc]) lrrows[p.first].emplace_back(jc, p.second);
+
+  // Woodbury core I + A_L^T P^{-1} A_L (eq. (28)) and its FP64 Cholesky factor
+  std::vector<double> C(static_cast<size_t>(te) * te, 0.0);
+  for (int i = 0; i < te; ++i) C[static_cast<size_t>(i) * te + i] = 1.0;
+  for (int32_t r = 0; r < m; ++r) {
+    const double pi = 1.0 / L.P[r];
+    const auto& row = lrrows[r];
+    for (size_t a = 0; a < row.size(); ++a) {
+      const double va = row[a].second * pi;
+      double* Ci = &C[static_cast<size_t>(row[a].first) * te];
+      for (size_t c2 = 0; c2 < row.size(); ++c2) Ci[row[c2].first] += va * row[c2].second;
+    }
+  }
+  std::vector<double> Lf = C;
+  if (!cholesky(Lf, te)) return fail(L, SOS_ERR_FACTOR, "Woodbury core is not positive definite");
+  L.linv = tri_inverse(Lf, te);
+
+  // h = M^{-1} zeta, zeta = [c; -b] (eq. (25)), via eq. (27) with the Cholesky factor
+  //   r = -b - A c ; sigma2 = (P + A_L A_L^T)^{-1} r ; sigma1 = c + A^T sigma2
+  std::vector<double> r(m);
+  for (int32_t i = 0; i < m; ++i) r[i] = -L.b[i];
+  for (int i = 0; i < pg.t; ++i)
+    for (auto& p : L.cols[i]) r[p.first] -= p.second * pg.w[i];
+  std::vector<double> xw(m), y(te, 0.0), z(te, 0.0);
+  for (int32_t i = 0; i < m; ++i) xw[i] = r[i] / L.P[i];
+  for (int jc = 0; jc < te; ++jc)
+    for (auto& p : L.cols[jc]) y[jc] += p.second * xw[p.first];
+  for (int i = 0; i < te; ++i) {  // forward substitution L q = y
+    double s = y[i];
+    for (int k = 0; k < i; ++k) s -= Lf[static_cast<size_t>(i) * te + k] * z[k];
+    z[i] = s / Lf[static_cast<size_t>(i) * te + i];
+  }
+  for (int i = te - 1; i >= 0; --i) {  // back substitution L^T z = q
+    double s = z[i];
+    for (int k = i + 1; k < te; ++k) s -= Lf[static_cast<size_t>(k) * te + i] * z[k];
+    z[i] = s / Lf[static_cast<size_t>(i) * te + i];
+  }
+  L.h2.assign(m, 0.0);
+  for (int32_t i = 0; i < m; ++i) {
+    double acc = 0.0;
+    for (auto& p : lrrows[i]) acc += p.second * z[p.first];
+    L.h2[i] = xw[i] - acc / L.P[i];
+  }
+  // g = A_L^T h_2 (equals z up to rounding; recomputed from h_2 directly)
+  L.g.assign(te, 0.0);
+  for (int jc = 0; jc < te; ++jc)
+    for (auto& p : L.cols[jc]) L.g[jc] += p.second * L.h2[p.first];
+  double ch1 = 0.0, bh2 = 0.0, nb = 0.0, nc = 0.0;
+  for (int i = 0; i < pg.t; ++i) {
+    ch1 += pg.w[i] * (pg.w[i] + L.g[i]);  // h_1 = c + A^T h_2 on the free columns
+    nc += pg.w[i] * pg.w[i];
+  }
+  for (int32_t i = 0; i < m; ++i) {
+    bh2 += L.b[i] * L.h2[i];
+    nb += L.b[i] * L.b[i];
+  }
+  L.zeta_h = ch1 - bh2;
+  L.norm_b = std::sqrt(nb);
+  L.norm_c = std::sqrt(nc);
+  if (!(1.0 + L.zeta_h > 0.0)) return fail(L, SOS_ERR_FACTOR, "1 + zeta^T h is not positive");
+  return SOS_OK;
+}
+
+}  // namespace
+
+int64_t enumerate_monomials(int32_t n_vars, int32_t degree, int32_t* out, int64_t capacity) {
+  // graded; inside a degree, x1-major descending (eq. (4))
+  int64_t count = 0;
+  std::vector<int32_t> e(n_vars);
+  for (int32_t deg = 0; deg <= degree; ++deg) {
+    // first exponent of the level: (deg, 0, ..., 0)
+    std::fill(e.begin(), e.end(), 0);
+    e[0] = deg;
+    while (true) {
+      if (out && count < capacity) std::memcpy(out + count * n_vars, e.data(), sizeof(int32_t) * n_vars);
+      ++count;
+      // next in descending lex order among compositions of deg
+      int k = n_vars - 2;
+      while (k >= 0 && e[k] == 0) --k;
+      if (k < 0) break;
+      e[k] -= 1;
+      int32_t rest = 0;
+      for (int q = k + 1; q < n_vars; ++q) rest += e[q];
+      for (int q = k + 1; q < n_vars; ++q) e[q] = 0;
+      e[k + 1] = rest + 1;
+    }
+  }
+  return count;
+}
+
+int build_plan(const sos_program* progs, int32_t n_progs, HostPlan& P, std::string& err) {
+  if (!progs || n_progs < 1) {
+    err = "need at least one program";
+    return SOS_ERR_INVALID_ARG;
+  }
+  std::vector<Local> loc(n_progs);
+  unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (n_progs < 4) nth = 1;
+  std::vector<std::thread> pool;
+  for (unsigned w = 0; w < nth; ++w)
+    pool.emplace_back([&, w]() {
+      for (int32_t i = static_cast<int32_t>(w); i < n_progs; i += static_cast<int32_t>(nth)) build_instance(progs[i], loc[i]);
+    });
+  for (auto& th : pool) th.join();
+  for (int32_t i = 0; i < n_progs; ++i)
+    if (loc[i].code != SOS_OK) {
+      err = "instance " + std::to_string(i) + ": " + loc[i].err;
+      return loc[i].code;
+    }
+
+  // merge with global offsets
+  P.n_inst = n_progs;
+  int64_t NX = 0, M = 0, nnzD = 0, nnzL = 0, nlinv = 0;
+  int64_t TL = 0;
+  for (auto& L : loc) {
+    NX += L.nx;
+    M += L.m;
+    TL += L.t_eff;
+    nlinv += static_cast<int64_t>(L.t_eff) * L.t_eff;
+    for (auto& r : L.row_plain) nnzD += static_cast<int64_t>(r.size());
+    for (auto& c : L.cols) nnzL += static_cast<int64_t>(c.size());
+  }
+  if (NX >= (1ll << 31) || M >= (1ll << 30) || TL >= (1ll << 31) || nnzL >= (1ll << 31) || nnzD >= (1ll << 31)) {
+    err = "problem set too large for 32-bit indices";
+    return SOS_ERR_UNSUPPORTED;
+  }
+  P.NX = NX;
+  P.M = M;
+  P.TL = static_cast<int32_t>(TL);
+  P.n_linv = nlinv;
+  P.b.reserve(M);
+  P.pinv.reserve(M);
+  P.h2.reserve(M);
+  P.row_inst.reserve(M);
+  P.row_ptr.reserve(M + 1);
+  P.row_ent.reserve(nnzD);
+  P.ent_row.reserve(NX);
+  P.lr_ptr.reserve(TL + 1);
+  P.lr_row.reserve(nnzL);
+  P.lr_val.reserve(nnzL);
+  P.linv.reserve(nlinv);
+  P.row_ptr.push_back(0);
+  P.lr_ptr.push_back(0);
+  int64_t xoff = 0, yoff = 0, loff = 0;
+  int32_t lroff = 0;
+  for (int32_t i = 0; i < n_progs; ++i) {
+    Local& L = loc[i];
+    InstInfo in{};
+    in.x_off = xoff;
+    in.y_off = yoff;
+    in.nx = L.nx;
+    in.m = L.m;
+    in.t = L.t;
+    in.t_eff = L.t_eff;
+    in.lr_off = lroff;
+    in.linv_off = loff;
+    in.zeta_h = L.zeta_h;
+    in.norm_b = L.norm_b;
+    in.norm_c = L.norm_c;
+    P.inst.push_back(in);
+    P.x_inst_start.push_back(xoff);
+    for (int32_t r = 0; r < L.m; ++r) {
+      P.b.push_back(L.b[r]);
+      P.pinv.push_back(1.0 / L.P[r]);
+      P.h2.push_back(L.h2[r]);
+      P.row_inst.push_back(i);
+      for (uint32_t v : L.row_plain[r]) {
+        uint32_t e = (v & ~kOffDiagBit) + static_cast<uint32_t>(xoff);
+        P.row_ent.push_back(e | (v & kOffDiagBit));
+      }
+      P.row_ptr.push_back(static_cast<int32_t>(P.row_ent.size()));
+    }
+    for (int32_t e = 0; e < L.nx; ++e) {
+      const int32_t er = L.ent_row[e];
+      P.ent_row.push_back(er >= 0 ? static_cast<int32_t>(((er & ~kEntOffBit) + yoff) | (er & kEntOffBit)) : -1);
+    }
+    for (int jc = 0; jc < L.t_eff; ++jc) {
+      P.ent_row[xoff + L.lr_ent[jc]] = -(lroff + jc + 1);
+      for (auto& p : L.cols[jc]) {
+        P.lr_row.push_back(static_cast<int32_t>(p.first + yoff));
+        P.lr_val.push_back(p.second);
+      }
+      P.lr_ptr.push_back(static_cast<int32_t>(P.lr_row.size()));
+      P.lr_ent.push_back(L.lr_ent[jc] + xoff);
+      P.lr_inst.push_back(i);
+      P.lr_c.push_back(L.lr_c[jc]);
+      P.lr_g.push_back(L.g[jc]);
+    }
+    P.linv.insert(P.linv.end(), L.linv.begin(), L.linv.end());
+    for (auto& lb : L.blocks) {
+      BlockDesc bd{};
+      bd.x_off = lb.x_off + xoff;
+      bd.v_off = -1;
+      bd.N = lb.N;
+      bd.inst = i;
+      bd.kind = lb.kind;
+      bd.lr_first = lb.kind == kWeighted ? lb.lr_first + lroff : -1;
+      P.blocks.push_back(bd);
+    }
+    xoff += L.nx;
+    yoff += L.m;
+    loff += static_cast<int64_t>(L.t_eff) * L.t_eff;
+    lroff += L.t_eff;
+    L = Local();  // release
+  }
+  P.x_inst_start.push_back(xoff);
+  // CSR of A_L by rows (global)
+  P.lrr_ptr.assign(M + 1, 0);
+  for (int64_t k = 0; k < static_cast<int64_t>(P.lr_row.size()); ++k) P.lrr_ptr[P.lr_row[k] + 1]++;
+  for (int64_t r = 0; r < M; ++r) P.lrr_ptr[r + 1] += P.lrr_ptr[r];
+  P.lrr_col.assign(P.lr_row.size(), 0);
+  P.lrr_val.assign(P.lr_row.size(), 0.0);
+  std::vector<int32_t> fillp(P.lrr_ptr.begin(), P.lrr_ptr.end() - 1);
+  for (int32_t jc = 0; jc < P.TL; ++jc)
+    for (int32_t k = P.lr_ptr[jc]; k < P.lr_ptr[jc + 1]; ++k) {
+      int32_t r = P.lr_row[k];
+      P.lrr_col[fillp[r]] = jc;
+      P.lrr_val[fillp[r]] = P.lr_val[k];
+      fillp[r]++;
+    }
+  return SOS_OK;
+}
+
+}  // namespace sos

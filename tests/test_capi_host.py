@@ -1,0 +1,93 @@
+"""CPU tests of libsos's host side: the library loads and exports every symbol
+of include/sos.h, its monomial enumeration follows eq. (4), and its host
+setup (index map of eq. (8)/(38), P of Prop. 1, b, zeta^T h of eq. (25)) is
+bit-exact against the oracle's independent construction.  No GPU needed."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from instances import workloads as W
+from oracle import admm, basis, conic
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1708_04174_gb300 import build, capi as c
+
+    if not os.path.exists(c.LIB_PATH):
+        build.build()
+    c.lib()
+    return c
+
+
+def test_exports_match_header(capi):
+    hdr = open(os.path.join(ROOT, "include", "sos.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|void\*|void|const char\*)\s+(sos_\w+)\s*\(", hdr, re.M))
+    assert declared, "no declarations parsed"
+    for name in declared:
+        assert hasattr(capi.lib(), name), name
+    assert declared == set(capi.EXPORTS), declared ^ set(capi.EXPORTS)
+
+
+@pytest.mark.parametrize("n,d", [(1, 5), (2, 3), (3, 2), (6, 2), (5, 3), (30, 2)])
+def test_monomials_match_oracle(capi, n, d):
+    assert np.array_equal(capi.monomials(n, d), np.array(basis.monomials(n, d), dtype=np.int32))
+
+
+PROGS = [
+    lambda: W.quartic_pop(3, 0),
+    lambda: W.quartic_pop(6, 0),
+    lambda: W.ball_pop(2, 1),
+    lambda: W.ball_pop(4, 2),
+    lambda: W.lyapunov_cubic(2, 5),
+    lambda: W.lyapunov_cubic(3, 7),
+    lambda: W.lyapunov_linear(3, 0),
+    lambda: W.paper_pop(5),
+    lambda: W.univariate_pop(6, 2),
+]
+
+
+@pytest.mark.parametrize("make", PROGS)
+def test_index_map_bit_exact(capi, make):
+    prog = make()
+    hp = capi.host_plan(prog)
+    cd = conic.build(prog)
+    hs = admm.HSDE(cd)
+    nx, m, t, teff, nb, nent = hp["dims"]
+    assert (m, t, nb) == (cd.m, cd.t, len(cd.blocks))
+    assert nx == conic.packed_length(cd) and nent == nx - t
+    assert teff == cd.t + sum(b.N * (b.N + 1) // 2 for b in cd.blocks if b.weighted)
+    # oracle: row of each plain Gram entry (column i + j N of vec X has one nonzero)
+    A = cd.A.tocsc()
+    want = [-1] * cd.t
+    for blk in cd.blocks:
+        for j in range(blk.N):
+            for i in range(j, blk.N):
+                if blk.weighted:
+                    want.append(-1)
+                else:
+                    col = A[:, blk.offset + i + j * blk.N]
+                    assert col.nnz == 1
+                    want.append(int(col.indices[0]))
+    assert np.array_equal(hp["ent_row"], np.array(want, dtype=np.int32))
+    assert np.array_equal(hp["p_diag"], hs.P)  # 1 + n_alpha, exact small integers
+    assert np.array_equal(hp["b"], cd.b)
+    assert abs(hp["zeta_h"] - hs.zeta @ hs.h) <= 1e-12 * max(1.0, abs(hs.zeta @ hs.h))
+
+
+def test_setup_rejects_bad_input(capi):
+    from instances.program import Block, Constraint, SOSProgram
+
+    # g_1 has a monomial of degree 5 that is not among the degree-4 rows
+    bad = SOSProgram(n=1, w=np.array([1.0]), constraints=[Constraint(4, {(0,): 1.0}, [{(5,): 1.0}], [Block(2)])])
+    with pytest.raises(RuntimeError, match="not among"):
+        capi.host_plan(bad)
+    # a Gram block whose products exceed the rows
+    bad = SOSProgram(n=1, w=np.array([1.0]), constraints=[Constraint(2, {(0,): 1.0}, [{(0,): 1.0}], [Block(2)])])
+    with pytest.raises(RuntimeError, match="not among"):
+        capi.host_plan(bad)

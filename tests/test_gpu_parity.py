@@ -1,0 +1,135 @@
+"""GPU parity: libsos (CUDA, through the C-ABI) against the FP64 CPU oracle on
+the same seeded programs.
+
+* plain FP64 form: the HSDE iterates after a fixed number of ADMM iterations
+  agree within 1e-9 relative (max-norm, per vector);
+* converged objectives agree within 1e-6 relative; statuses agree;
+* FP32 form: iterates and objectives within the error that FP32 projections
+  allow (bounds stated in each test).
+"""
+
+import numpy as np
+import pytest
+
+from instances import workloads as W
+from oracle import admm, conic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1708_04174_gb300 import build, capi as c
+
+    import os
+
+    if not os.path.exists(c.LIB_PATH):
+        build.build()
+    return c
+
+
+def oracle_packed(prog, iters):
+    cd = conic.build(prog)
+    hs = admm.HSDE(cd)
+    u, v = hs.run(iters)
+    uo = np.concatenate([conic.vec_to_packed(cd, u[:cd.nx]), u[cd.nx:]])
+    vo = np.concatenate([conic.vec_to_packed(cd, v[:cd.nx]), v[cd.nx:]])
+    return uo, vo
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+CASES = [
+    ("quartic_n3", lambda: W.quartic_pop(3, 0), 60),
+    ("config0_quartic_n6", lambda: W.quartic_pop(6, 0), 200),
+    ("univariate_odd_N", lambda: W.univariate_pop(4, 1), 80),
+    ("ball_n2_weighted", lambda: W.ball_pop(2, 1), 80),
+    ("ball_n5_weighted", lambda: W.ball_pop(5, 0), 60),
+    ("lyapunov_cubic_n2", lambda: W.lyapunov_cubic(2, 5), 60),
+    ("lyapunov_cubic_n3", lambda: W.lyapunov_cubic(3, 1), 40),
+    ("lyapunov_linear_n4", lambda: W.lyapunov_linear(4, 3), 60),
+    ("eq46_n6", lambda: W.paper_pop(6), 60),
+]
+
+
+@pytest.mark.parametrize("name,make,iters", CASES, ids=[c[0] for c in CASES])
+def test_fp64_iterates_match_oracle(capi, name, make, iters):
+    prog = make()
+    uo, vo = oracle_packed(prog, iters)
+    s = capi.Solver(prog, precision=capi.PREC_FP64)
+    s.iterate(iters)
+    s.sync()
+    ug, vg = s.get_iterate()
+    s.close()
+    assert rel(ug, uo) < 1e-9, rel(ug, uo)
+    assert rel(vg, vo) < 1e-9, rel(vg, vo)
+
+
+def test_fp64_batch_matches_oracle_per_instance(capi):
+    progs = [W.quartic_pop(3, 0), W.ball_pop(2, 1), W.lyapunov_cubic(2, 5), W.univariate_pop(6, 3),
+             W.lyapunov_cubic(3, 2)]
+    iters = 50
+    s = capi.Solver(progs, precision=capi.PREC_FP64)
+    s.iterate(iters)
+    s.sync()
+    ug, vg = s.get_iterate()
+    for (xg, yg, tg), (zg, sg, kg), prog in zip(s.split(ug), s.split(vg), progs):
+        uo, vo = oracle_packed(prog, iters)
+        assert rel(np.concatenate([xg, yg, [tg]]), uo) < 1e-9
+        assert rel(np.concatenate([zg, sg, [kg]]), vo) < 1e-9
+    s.close()
+
+
+def test_fp64_large_block_config1(capi):
+    """Constrained quartic POP n = 20 (Gram 231 + weighted 21, m = 10626):
+    the large-block (grid Jacobi) path with a ragged tile tail."""
+    prog = W.ball_pop(20, 0)
+    iters = 12
+    uo, vo = oracle_packed(prog, iters)
+    s = capi.Solver(prog, precision=capi.PREC_FP64)
+    s.iterate(iters)
+    s.sync()
+    ug, vg = s.get_iterate()
+    s.close()
+    assert rel(ug, uo) < 1e-9, rel(ug, uo)
+    assert rel(vg, vo) < 1e-9, rel(vg, vo)
+
+
+def test_fp64_solve_objective_and_status(capi):
+    prog = W.quartic_pop(6, 0)
+    cd = conic.build(prog)
+    ro = admm.solve(cd, 1e-8, 50000, k_check=10)
+    s = capi.Solver(prog, precision=capi.PREC_FP64, k_check=10)
+    r = s.solve(1e-8, 50000)[0]
+    s.close()
+    assert r["status"] == capi.SOLVED and ro.status == admm.SOLVED
+    assert abs(r["obj_primal"] - ro.res["pobj"]) <= 1e-6 * abs(ro.res["pobj"])
+    assert r["iters"] == ro.iters  # same iterates, same checks
+
+
+def test_infeasibility_statuses(capi):
+    from instances.program import Block, Constraint, SOSProgram
+
+    pinf = SOSProgram(n=1, w=np.array([0.0]),
+                      constraints=[Constraint(2, {(0,): -1.0}, [{(2,): 1.0}], [Block(1)])])
+    dinf = SOSProgram(n=1, w=np.array([1.0]),
+                      constraints=[Constraint(2, {(2,): 1.0}, [{(2,): 1.0}], [Block(1)])])
+    s = capi.Solver([pinf, dinf], precision=capi.PREC_FP64, k_check=1)
+    r = s.solve(1e-6, 5000)
+    s.close()
+    assert r[0]["status"] == capi.PRIMAL_INFEASIBLE
+    assert r[1]["status"] == capi.DUAL_INFEASIBLE
+
+
+def test_fp32_form_error_vs_oracle(capi):
+    prog = W.quartic_pop(6, 0)
+    cd = conic.build(prog)
+    ro = admm.solve(cd, 1e-6, 50000, k_check=10)
+    s = capi.Solver(prog, precision=capi.PREC_FP32, k_check=10)
+    r = s.solve(1e-4, 50000)[0]
+    s.close()
+    assert r["status"] == capi.SOLVED
+    err = abs(r["obj_primal"] - ro.res["pobj"]) / abs(ro.res["pobj"])
+    assert err < 1e-3, err
