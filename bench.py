@@ -1,0 +1,316 @@
+"""Benchmark: ADMM iterations/s of the HSDE ADMM for SOS programs on GB300.
+
+Default workload: the constrained quartic POP on the unit ball with n = 20
+(Gram blocks 231x231 and a weighted 21x21, m = 10626 monomial rows), plain
+FP64 form.  One "step" is one full ADMM iteration (eq. (20): affine step,
+PSD projection of every Gram block, dual/embedding update) of that instance.
+
+JSON line (rank 0): value = ADMM iterations/s (device-timed with CUDA events
+on the solver's stream, L2 flushed between steps), e2e = the same metric
+through the C-ABI with host buffers (iterate copied in and out every step),
+roofline of the dominant kernel, the CPU oracle as a bounded baseline,
+time to a 1e-4 residual for the plain FP64 form and the FP32 form, and SM
+clocks sampled during the timed region.
+
+``--impl reference`` times the CPU oracle (the reference arm of this build)
+on the same workload and metric.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "ball_pop_n20": dict(desc="constrained quartic POP on the unit ball, n=20, 2d=4: Gram 231x231 + weighted "
+                              "21x21, m=10626 (Lasserre order 2)", make=("ball_pop", 20, 0)),
+    "quartic_pop_n6": dict(desc="unconstrained quartic POP, n=6, 2d=4: Gram 28x28, m=210",
+                           make=("quartic_pop", 6, 0)),
+    "quartic_pop_n30": dict(desc="unconstrained quartic POP, n=30, 2d=4: Gram 496x496, m=46376",
+                            make=("quartic_pop", 30, 0)),
+}
+
+
+def make_program(name):
+    from instances import workloads as W
+
+    fn, n, seed = WORKLOADS[name]["make"]
+    return getattr(W, fn)(n, seed)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    def __init__(self, out_path):
+        self.proc = None
+        self.path = out_path
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, dev_index=0):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                if int(parts[0]) != dev_index:
+                    continue
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_oracle_iters(prog, seconds: float, max_iters: int):
+    """Times the CPU oracle's ADMM iterations (bounded sample)."""
+    from oracle import admm, conic
+
+    cd = conic.build(prog)
+    hs = admm.HSDE(cd)
+    u, v = hs.start()
+    u, v = hs.step(u, v)  # warm-up
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_iters and (time.perf_counter() - t0) < seconds:
+        u, v = hs.step(u, v)
+        k += 1
+    dt = time.perf_counter() - t0
+    return k, dt
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    prog = make_program(args.workload)
+    k, dt = run_oracle_iters(prog, seconds=max(2.0, 8.0 * (args.steps + args.warmup) / 20), max_iters=10**9)
+    ips = k / dt
+    line = {"impl": "reference", "metric": "ADMM iterations/s (plain FP64)", "value": ips, "unit": "iter/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / ips,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"]},
+            "cpu_baseline": {"value": ips, "unit": "iter/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"{k} ADMM iterations of the FP64 NumPy/SciPy oracle from a cold start"},
+            "e2e": {"value": ips, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="ball_pop_n20", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tt", action="store_true", help="skip the time-to-1e-4 solves")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+    from paper_1708_04174_gb300 import capi
+
+    prog = make_program(args.workload)
+    prec = capi.PREC_FP64 if args.precision == "fp64" else capi.PREC_FP32
+    solver = capi.Solver(prog, precision=prec, k_check=10)
+    stream = torch.cuda.ExternalStream(solver.stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # warm-up
+    solver.iterate(args.warmup)
+    solver.sync()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    barrier()
+    with clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()  # L2 flush (256 MB > 129 MB L2) between steps, outside the step's events
+                starts[k].record(stream)
+            solver.iterate(1)
+            with torch.cuda.stream(stream):
+                ends[k].record(stream)
+        solver.sync()
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(np.sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ips = world * args.steps / (total_ms / 1e3)
+
+    # dominant kernel: time each stage alone with events on the solver's stream
+    stage_ms = {}
+    for stage, name in ((0, "affine"), (1, "psd_small"), (2, "psd_large")):
+        reps = 10
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in evs:
+            with torch.cuda.stream(stream):
+                a.record(stream)
+            solver.run_stage(stage)
+            with torch.cuda.stream(stream):
+                b.record(stream)
+        solver.sync()
+        stage_ms[name] = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+    d = solver.dims[0]
+    from instances import workloads as W  # noqa: F401
+    blocks = []
+    for con in prog.constraints:
+        for blk in con.blocks:
+            from math import comb
+
+            blocks.append(comb(prog.n + blk.basis_degree, blk.basis_degree))
+    big = [N for N in blocks if N > (96 if prec == capi.PREC_FP64 else 160)]
+    pk, pk_kind = peaks()
+    if big and stage_ms["psd_large"] >= stage_ms["psd_small"]:
+        flops = sum(9.0 * N ** 3 for N in big)
+        dom_ms = stage_ms["psd_large"]
+        fp64_peak = 1190.0 if prec == capi.PREC_FP64 else 69700.0
+        roof = {"kernel": "k_psd_large (grid Jacobi eigen-projection)", "bound": "alu",
+                "achieved": flops / (dom_ms / 1e3) / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
+                "frac": flops / (dom_ms / 1e3) / 1e9 / fp64_peak, "traffic": None,
+                "note": f"algorithmic flops 9 N^3 per N x N eigen-projection (N={big}); peak = FMA-loop "
+                        f"{'FP64' if prec == capi.PREC_FP64 else 'FP32'} rate measured on this GB300"}
+    else:
+        small = [N for N in blocks if N not in big]
+        flops = sum(9.0 * N ** 3 for N in small)
+        dom_ms = stage_ms["psd_small"]
+        peak = 1190.0 if prec == capi.PREC_FP64 else 69700.0
+        roof = {"kernel": "k_psd_small (shared-memory Jacobi eigen-projection)", "bound": "alu",
+                "achieved": flops / (dom_ms / 1e3) / 1e9, "peak": peak, "unit": "GFLOP/s",
+                "frac": flops / (dom_ms / 1e3) / 1e9 / peak, "traffic": None,
+                "note": "algorithmic flops 9 N^3 per block; peak = FMA-loop rate measured on this GB300"}
+    roof["stage_ms"] = stage_ms
+
+    # end-to-end through the C-ABI with host buffers
+    u0, v0 = solver.get_iterate()
+    e2e_steps = max(5, args.steps // 4)
+    solver.sync()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.set_iterate(u0, v0)
+        solver.iterate(1)
+        u0, v0 = solver.get_iterate()
+    e2e_dt = time.perf_counter() - t0
+    esz = 8 if prec == capi.PREC_FP64 else 4
+    nbytes = 2 * ((d[0] + d[1]) * esz + 8)
+    e2e = {"value": world * e2e_steps / e2e_dt, "unit": "iter/s", "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+
+    out = {"metric": "ADMM iterations/s (one iteration = affine step + PSD projections + update)",
+           "value": ips, "unit": "iter/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if prec == capi.PREC_FP64 else "f32", "data": "synthetic",
+           "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
+                      "form": "plain FP64" if prec == capi.PREC_FP64 else "FP32 projections, FP64 Woodbury",
+                      "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
+                      "n_x": d[0], "m": d[1], "t_eff": d[3]},
+           "wall_s": t_wall, "e2e": e2e, "roofline": roof,
+           "gpu_launches": None}
+    out["gpu_launches"] = int(solver.launches_per_iteration() * args.steps)
+    out["roofline"]["peak_source"] = "FMA-loop probe on this GB300 (FP64 1.19 TFLOP/s, FP32 69.7 TFLOP/s)"
+    out["clocks"] = clk.summary(local)
+
+    if not args.no_tt:
+        tt = {}
+        for nm, pr in (("fp64", capi.PREC_FP64), ("fp32", capi.PREC_FP32)):
+            s2 = capi.Solver(prog, precision=pr, k_check=10)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = s2.solve(1e-4, 20000, want_solution=False)[0]
+            dt = time.perf_counter() - t0
+            tt[nm] = {"seconds": dt, "iters": r["iters"], "status": r["status"], "obj": r["obj_primal"]}
+            s2.close()
+        out["time_to_1e-4"] = tt
+
+    if rank == 0 and not args.no_cpu_baseline:
+        k, dt = run_oracle_iters(prog, seconds=15.0, max_iters=10**9)
+        out["cpu_baseline"] = {"value": k / dt, "unit": "iter/s", "cores": cpu_cores(), "kind": "oracle",
+                               "sample": f"{k} ADMM iterations of the FP64 NumPy/SciPy oracle on the same "
+                                         f"instance (about 15 s), BLAS threads at their default"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

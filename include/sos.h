@@ -194,6 +194,26 @@ int sos_monomials(int32_t n_vars, int32_t degree, int32_t* out, int64_t capacity
 int sos_host_plan(const sos_program* prog, int64_t dims[6], int32_t* ent_row, double* p_diag, double* b,
                   double* zeta_h);
 
+/* Projection onto the PSD cone of ONE symmetric N x N matrix (the Gram-block
+ * part of the cone projection of eq. (20b)): out = svec(P_S+(smat(in))),
+ * P_S+(X) = V max(Lambda, 0) V^T.  in, out: DEVICE pointers to N(N+1)/2
+ * doubles in the packed order above (they must not overlap).  The work runs
+ * on stream (a cudaStream_t; NULL = legacy default stream) and the call
+ * returns when it has finished.  The call allocates its scratch (about
+ * 5 N^2 doubles for N > 96, less below) with cudaMalloc and frees it before
+ * returning.  Errors: SOS_ERR_INVALID_ARG (N < 1 or NULL pointers),
+ * SOS_ERR_CUDA, SOS_ERR_TIMEOUT; the message is in sos_last_error(NULL). */
+int sos_psd_project(const double* in, double* out, int32_t N, void* stream);
+
+/* Diagnostics (synchronises the handle's stream): out[0] = iterations run
+ * since setup, out[1] = number of Gram blocks, out[2] = largest number of
+ * Jacobi sweeps any block needed in the last projection, out[3] = total
+ * sweeps over all blocks in the last projection. */
+int sos_stats(sos_handle* h, int64_t out[4]);
+
+/* Number of CUDA kernels one ADMM iteration launches for this handle. */
+int sos_launches_per_iteration(const sos_handle* h);
+
 /* Profiling hooks (used by the benchmark to time single stages with events
  * on the handle's stream).  sos_stream returns the cudaStream_t in use.
  * sos_run_stage enqueues one stage of one iteration: 0 = affine step (all

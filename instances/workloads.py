@@ -22,7 +22,6 @@ Workloads:
 
 from __future__ import annotations
 
-import itertools
 from typing import Dict, List, Sequence, Tuple
 
 import numpy as np
@@ -37,15 +36,24 @@ Poly = Dict[Exp, float]
 # sparse polynomial helpers used only to *write down* input polynomials
 # --------------------------------------------------------------------------
 
+def _compositions_desc(total: int, parts: int):
+    """All exponent tuples of length ``parts`` summing to ``total``, in
+    decreasing lexicographic order."""
+    if parts == 1:
+        yield (total,)
+        return
+    for first in range(total, -1, -1):
+        for rest in _compositions_desc(total - first, parts - 1):
+            yield (first,) + rest
+
+
 def _support(n: int, max_deg: int, min_deg: int = 0) -> List[Exp]:
     """Exponents of degree min_deg..max_deg, graded, then x1 > x2 > ... lex.
 
     Used only to fix the order in which random coefficients are drawn."""
     out: List[Exp] = []
     for deg in range(min_deg, max_deg + 1):
-        level = [e for e in itertools.product(range(deg + 1), repeat=n) if sum(e) == deg]
-        level.sort(reverse=True)
-        out.extend(level)
+        out.extend(_compositions_desc(deg, n))
     return out
 
 

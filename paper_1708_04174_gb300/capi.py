@@ -67,6 +67,9 @@ EXPORTS = {
     "sos_monomials": (C.c_int, [C.c_int32, C.c_int32, _i32p, C.c_int64, C.POINTER(C.c_int64)]),
     "sos_host_plan": (C.c_int, [C.POINTER(sos_program), C.POINTER(C.c_int64), _i32p, _f64p, _f64p, _f64p]),
     "sos_stream": (C.c_void_p, [C.c_void_p]),
+    "sos_launches_per_iteration": (C.c_int, [C.c_void_p]),
+    "sos_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "sos_psd_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sos_run_stage": (C.c_int, [C.c_void_p, C.c_int32]),
 }
 
@@ -169,6 +172,11 @@ class _Marshalled:
             self.keep += [w, cons]
 
 
+def psd_project(in_ptr: int, out_ptr: int, N: int, stream: int = 0):
+    """PSD projection of one packed symmetric matrix; device pointers."""
+    _check(lib().sos_psd_project(C.c_void_p(in_ptr), C.c_void_p(out_ptr), N, C.c_void_p(stream) if stream else None))
+
+
 def host_plan(prog):
     """Index map of one program as built by libsos's host setup (no GPU)."""
     m = _Marshalled([prog])
@@ -228,6 +236,14 @@ class Solver:
     @property
     def stream(self) -> int:
         return lib().sos_stream(self.h) or 0
+
+    def stats(self) -> dict:
+        out = (C.c_int64 * 4)()
+        _check(lib().sos_stats(self.h, out), self.h)
+        return {"iterations": out[0], "blocks": out[1], "max_sweeps": out[2], "total_sweeps": out[3]}
+
+    def launches_per_iteration(self) -> int:
+        return int(lib().sos_launches_per_iteration(self.h))
 
     def run_stage(self, stage: int):
         _check(lib().sos_run_stage(self.h, stage), self.h)

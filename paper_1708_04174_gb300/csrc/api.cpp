@@ -53,6 +53,7 @@ struct sos_handle {
   std::vector<int32_t> active_h;
   std::vector<int32_t> iters_h, status_h;
   int64_t iter_count = 0;
+  int32_t* blk_sweeps = nullptr;  // device
   cudaGraphExec_t graph = nullptr;
   bool graph_tried = false;
   std::string err;
@@ -111,6 +112,7 @@ struct Common {
   const int64_t* lr_ent;
   double *tau, *kappa, *xP, *ylr, *zlr, *sig2, *ra, *atyl;
   int32_t* err;
+  int32_t* blk_sweeps;
 };
 
 template <typename T>
@@ -152,6 +154,7 @@ int make_devplan(sos_handle* h, const Common& c, int32_t max_teff, DevPlan<T>& p
   p.ra = c.ra;
   p.atyl = c.atyl;
   p.err = c.err;
+  p.blk_sweeps = c.blk_sweeps;
   TRY(alloc(h, h->NX, &p.ux));
   TRY(alloc(h, h->NX, &p.vx));
   TRY(alloc(h, h->M, &p.uy));
@@ -174,7 +177,7 @@ int make_large(sos_handle* h, std::vector<LargeBlock<T>>& out, const std::vector
     TRY(alloc(h, Np * Np, &lb.scratch.T1));
     TRY(alloc(h, static_cast<size_t>(lb.grid), &lb.scratch.partial));
     TRY(alloc(h, kMaxSweeps, &lb.scratch.flags));
-    TRY(alloc(h, 1, &lb.scratch.bar));
+    TRY(alloc(h, 2, &lb.scratch.bar));
     TRY(alloc(h, 1, &lb.scratch.sweeps_out));
     TRY(alloc(h, 1, &lb.scratch.warm));
     out.push_back(lb);
@@ -325,6 +328,8 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   TRY(alloc(h, h->M, &c.ra));
   TRY(alloc(h, h->TL, &c.atyl));
   TRY(alloc(h, 1, &c.err));
+  TRY(alloc(h, P.blocks.size(), &c.blk_sweeps));
+  h->blk_sweeps = c.blk_sweeps;
   TRY(alloc(h, h->n_inst, &h->active));
   h->active_h.assign(h->n_inst, 1);
   h->iters_h.assign(h->n_inst, 0);
@@ -641,7 +646,6 @@ int sos_set_iterate(sos_handle* h, const double* u, const double* v) {
   std::fill(h->iters_h.begin(), h->iters_h.end(), 0);
   std::fill(h->status_h.begin(), h->status_h.end(), SOS_RUNNING);
   CK(cudaMemcpyAsync(h->active, h->active_h.data(), sizeof(int32_t) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
-  reset_warm(h);
   CK(cudaStreamSynchronize(h->stream));
   return SOS_OK;
 }
@@ -679,6 +683,107 @@ int sos_host_plan(const sos_program* prog, int64_t dims[6], int32_t* ent_row, do
     for (int64_t r = 0; r < in.m; ++r) b[r] = P.b[r];
   if (zeta_h) *zeta_h = in.zeta_h;
   return SOS_OK;
+}
+
+int sos_psd_project(const double* in, double* out, int32_t N, void* stream) {
+  if (!in || !out || N < 1) return SOS_ERR_INVALID_ARG;
+  sos_handle tmp;  // owns the scratch allocations of this call
+  sos_handle* h = &tmp;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t len = static_cast<int64_t>(N) * (N + 1) / 2;
+  h->stream = s;
+  auto release = [&]() {
+    cudaStreamSynchronize(s);
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+  };
+  const bool small = N <= psd_small_max_n(true);
+  BlockDesc bd{};
+  bd.x_off = 0;
+  bd.v_off = -1;
+  bd.N = N;
+  bd.inst = 0;
+  bd.kind = kRaw;
+  bd.lr_first = -1;
+  h->blocks.assign(1, bd);
+  h->n_inst = 1;
+  h->NX = len;
+  DevPlan<double> p;
+  int rc = SOS_OK;
+  do {
+    BlockDesc* dbd;
+    if ((rc = upload(h, h->blocks, &dbd)) != SOS_OK) break;
+    std::vector<int32_t> one(1, 1), zero_id(1, 0);
+    int32_t *act, *ids, *sw, *err;
+    if ((rc = upload(h, one, &act)) != SOS_OK) break;
+    if ((rc = upload(h, zero_id, &ids)) != SOS_OK) break;
+    if ((rc = alloc(h, 1, &sw)) != SOS_OK) break;
+    if ((rc = alloc(h, 1, &err)) != SOS_OK) break;
+    InstState* st;
+    if ((rc = alloc(h, 1, &st)) != SOS_OK) break;
+    double* v;
+    if ((rc = alloc(h, len, &v)) != SOS_OK) break;
+    p.n_inst = 1;
+    p.NX = len;
+    p.blocks = dbd;
+    p.active = act;
+    p.st = st;
+    p.blk_sweeps = sw;
+    p.err = err;
+    p.ux = out;
+    p.vx = v;
+    if (cudaMemcpyAsync(out, in, sizeof(double) * len, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      rc = set_err(h, SOS_ERR_CUDA, "copy of the input failed");
+      break;
+    }
+    cudaError_t e;
+    if (small) {
+      const int cap = N <= 16 ? 16 : N <= 32 ? 32 : N <= 48 ? 48 : N <= 64 ? 64 : 96;
+      e = prepare_kernels<double>(cap, 0);
+      if (e == cudaSuccess) e = launch_psd_small<double>(p, ids, 1, cap, s);
+    } else {
+      std::vector<LargeBlock<double>> lb;
+      if ((rc = make_large(h, lb, std::vector<int>(1, 0))) != SOS_OK) break;
+      e = launch_psd_large<double>(p, 0, N, lb[0].scratch, lb[0].grid, s);
+    }
+    if (e != cudaSuccess) {
+      rc = set_err(h, SOS_ERR_CUDA, std::string("projection launch: ") + cudaGetErrorString(e));
+      break;
+    }
+    int32_t ew = 0;
+    if (cudaMemcpyAsync(&ew, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = set_err(h, SOS_ERR_CUDA, "projection failed");
+      break;
+    }
+    if (ew != 0) rc = set_err(h, SOS_ERR_TIMEOUT, "a bounded device-side wait expired");
+  } while (false);
+  if (rc != SOS_OK) g_setup_error = h->err;
+  release();
+  return rc;
+}
+
+int sos_stats(sos_handle* h, int64_t out[4]) {
+  if (!h || !out) return SOS_ERR_INVALID_ARG;
+  std::vector<int32_t> sw(h->blocks.size());
+  if (!sw.empty())
+    CK(cudaMemcpyAsync(sw.data(), h->blk_sweeps, sizeof(int32_t) * sw.size(), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  out[0] = h->iter_count;
+  out[1] = static_cast<int64_t>(sw.size());
+  out[2] = 0;
+  out[3] = 0;
+  for (int32_t s : sw) {
+    out[2] = std::max<int64_t>(out[2], s);
+    out[3] += s;
+  }
+  return SOS_OK;
+}
+
+int sos_launches_per_iteration(const sos_handle* h) {
+  if (!h) return SOS_ERR_INVALID_ARG;
+  const int affine = h->TL > 0 ? 6 : 4;
+  return affine + static_cast<int>(h->small.size()) + static_cast<int>(h->large64.size() + h->large32.size());
 }
 
 void* sos_stream(sos_handle* h) { return h ? static_cast<void*>(h->stream) : nullptr; }

@@ -204,6 +204,7 @@ __global__ void k_rows_y(DevPlan<T> p) {
 template <typename T>
 __device__ __forceinline__ T proj_input(const DevPlan<T>& p, const BlockDesc& bd, int64_t k, bool off, double s) {
   const int64_t e = bd.x_off + k;
+  if (bd.kind == kRaw) return p.ux[e];
   if (bd.kind == kPlain) {
     const int row = p.ent_row[e] & ~kEntOffBit;
     const T a = off ? static_cast<T>(kSqrt2) : static_cast<T>(1);
@@ -273,7 +274,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* ids) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[40];
-  __shared__ int rotated;
+  __shared__ int last_rot;  // index of the last round that had a rotation
   const BlockDesc bd = p.blocks[ids[blockIdx.x]];
   if (!p.active[bd.inst]) return;
   const double s_sm = p.st[bd.inst].s;
@@ -287,6 +288,7 @@ __global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* 
   int* rp = reinterpret_cast<int*>(lam + Np);
   int* rq = rp + H;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) last_rot = -1;  // block_sum below orders this before any use
 
   double nrm = 0.0;
   for (int q = tid; q < Np * Np; q += nt) {
@@ -305,11 +307,12 @@ __global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* 
   }
   const T thr = static_cast<T>(sqrt(block_sum(nrm, red))) * teps<T>();
 
+  int sweeps_done = 0;
+  int round_id = 0;
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-    __syncthreads();  // every thread has read the previous sweep's flag
-    if (tid == 0) rotated = 0;
-    __syncthreads();
-    for (int r = 0; r < Np - 1; ++r) {
+    bool rotated = false;
+    sweeps_done = sweep + 1;
+    for (int r = 0; r < Np - 1; ++r, ++round_id) {
       for (int k = tid; k < H; k += nt) {
         int a, b;
         rr_pair(k, r, Np, a, b);
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* 
           const T apq = A[a * ld + b];
           if (fabs(apq) > thr) {
             jacobi_rot(A[a * ld + a], A[b * ld + b], apq, c, s, t);
-            rotated = 1;
+            last_rot = round_id;
           }
         }
         rp[k] = a;
@@ -328,6 +331,8 @@ __global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* 
         rt[k] = t;
       }
       __syncthreads();
+      if (last_rot != round_id) continue;  // no rotation this round (uniform)
+      rotated = true;
       const int nblk = H * H;
       for (int task = tid; task < nblk + N * H; task += nt) {
         if (task < nblk) {
@@ -378,6 +383,7 @@ __global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* 
   }
 
   // P_S+(W) = V max(Lambda, 0) V^T; v = u - W
+  if (tid == 0) p.blk_sweeps[ids[blockIdx.x]] = sweeps_done;
   for (int k = tid; k < N; k += nt) lam[k] = fmax(A[k * ld + k], static_cast<T>(0));
   __syncthreads();
   for (int q = tid; q < N * N; q += nt) {
@@ -407,27 +413,39 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* ptr) {
   return v;
 }
 
-// Grid-wide barrier on a zero-initialised counter.  Bounded spin: on expiry
+__device__ __forceinline__ void st_release_u32(unsigned* ptr, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(ptr), "r"(v) : "memory");
+}
+
+// Grid-wide barrier.  bar[0] counts arrivals (zeroed before the launch),
+// bar[1] holds the last released generation; the CTA that completes a
+// generation releases it, the others poll bar[1].  Bounded spin: on expiry
 // (or when another CTA already raised the error word) every CTA returns false.
 __device__ bool grid_barrier(unsigned* bar, unsigned target, int32_t* err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
+    const unsigned G = gridDim.x;
+    const unsigned gen = target / G;
     __threadfence();
-    atomicAdd(bar, 1u);
+    const unsigned old = atomicAdd(bar, 1u);
     int good = 1;
-    const long long t0 = clock64();
-    while (ld_acquire_u32(bar) < target) {
-      if (*reinterpret_cast<volatile int32_t*>(err) != 0) {
-        good = 0;
-        break;
+    if (old == target - 1) {
+      __threadfence();  // order the other CTAs' arrivals before the release
+      st_release_u32(bar + 1, gen);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire_u32(bar + 1) < gen) {
+        if (*reinterpret_cast<volatile int32_t*>(err) != 0) {
+          good = 0;
+          break;
+        }
+        if (clock64() - t0 > kSpinLimitCycles) {
+          atomicExch(err, 1);
+          good = 0;
+          break;
+        }
       }
-      if (clock64() - t0 > kSpinLimitCycles) {
-        atomicExch(err, 1);
-        good = 0;
-        break;
-      }
-      __nanosleep(32);
     }
     __threadfence();
     ok = good;
@@ -471,10 +489,13 @@ __device__ T tile_mm(const T* A, const T* B, int Np, int ti, int tj, int mode, T
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeScratch<T> L) {
+  extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double red[40];
   __shared__ T sA[16 * 17], sB[16 * 17];
+  __shared__ int any_rot;
   const BlockDesc bd = p.blocks[bid];
   if (!p.active[bd.inst]) return;
+  if (threadIdx.x == 0) any_rot = -1;  // the load phase's block_sum orders this before any use
   const double s_sm = p.st[bd.inst].s;
   const int N = bd.N, Np = N + (N & 1), H = Np / 2;
   const int64_t gt = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -510,7 +531,6 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
 
   const int nt = (Np + 15) / 16;
   T* cur = Wf;
-  T* nxt = L.B0;
   if (warm) {
     for (int tile = blockIdx.x; tile < nt * nt; tile += G) {  // T1 = W V
       const int ti = tile / nt, tj = tile - ti * nt;
@@ -532,31 +552,61 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
     if (!grid_barrier(L.bar, (++gen) * G, err)) return;
   }
 
+  // Jacobi sweeps, double buffered (cur -> nxt).  Every CTA computes all
+  // rotations of a round into shared memory from cur, so all CTAs take the
+  // same decisions: a round without rotations writes nothing and is skipped
+  // without a barrier, and the sweep loop ends everywhere at once.  Reads of
+  // cur never race with writes, which only go to nxt.
+  T* nxt = L.B0;
+  T* rc = reinterpret_cast<T*>(dsm);
+  T* rs = rc + H;
+  T* rt = rs + H;
+  int* rp = reinterpret_cast<int*>(rt + H);
+  int* rq = rp + H;
   int sweeps = 0;
+  int round_id = 0;
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-    for (int r = 0; r < Np - 1; ++r) {
+    bool sweep_rot = false;
+    sweeps = sweep + 1;
+    for (int r = 0; r < Np - 1; ++r, ++round_id) {
+      for (int k = threadIdx.x; k < H; k += blockDim.x) {
+        int a, b;
+        rr_pair(k, r, Np, a, b);
+        T c = 1, s = 0, t = 0;
+        if (b < N) {
+          const T apq = ldg_cg(cur + static_cast<int64_t>(a) * Np + b);
+          if (fabs(apq) > thr) {
+            jacobi_rot(ldg_cg(cur + static_cast<int64_t>(a) * Np + a), ldg_cg(cur + static_cast<int64_t>(b) * Np + b), apq,
+                       c, s, t);
+            any_rot = round_id;
+          }
+        }
+        rp[k] = a;
+        rq[k] = b;
+        rc[k] = c;
+        rs[k] = s;
+        rt[k] = t;
+      }
+      __syncthreads();
+      if (any_rot != round_id) continue;  // same decision in every CTA
+      sweep_rot = true;
       const int64_t nblk = static_cast<int64_t>(H) * H;
       for (int64_t task = gt; task < nblk + static_cast<int64_t>(N) * H; task += gs) {
         if (task < nblk) {
           const int k1 = static_cast<int>(task / H), k2 = static_cast<int>(task - static_cast<int64_t>(k1) * H);
           if (k1 > k2) continue;
-          int p1, q1, p2, q2;
-          rr_pair(k1, r, Np, p1, q1);
-          rr_pair(k2, r, Np, p2, q2);
-          T c1 = 1, s1 = 0, t1 = 0, c2 = 1, s2 = 0, t2 = 0;
-          const T a1 = ldg_cg(cur + static_cast<int64_t>(p1) * Np + q1);
-          if (q1 < N && fabs(a1) > thr)
-            jacobi_rot(ldg_cg(cur + static_cast<int64_t>(p1) * Np + p1), ldg_cg(cur + static_cast<int64_t>(q1) * Np + q1),
-                       a1, c1, s1, t1);
+          const int p1 = rp[k1], q1 = rq[k1], p2 = rp[k2], q2 = rq[k2];
+          const T c1 = rc[k1], s1 = rs[k1], c2 = rc[k2], s2 = rs[k2];
           if (k1 == k2) {
+            const T a1 = ldg_cg(cur + static_cast<int64_t>(p1) * Np + q1);
             const T app = ldg_cg(cur + static_cast<int64_t>(p1) * Np + p1);
             const T aqq = ldg_cg(cur + static_cast<int64_t>(q1) * Np + q1);
             if (s1 != static_cast<T>(0)) {
+              const T t1 = rt[k1];
               nxt[static_cast<int64_t>(p1) * Np + p1] = app - t1 * a1;
               nxt[static_cast<int64_t>(q1) * Np + q1] = aqq + t1 * a1;
               nxt[static_cast<int64_t>(p1) * Np + q1] = static_cast<T>(0);
               nxt[static_cast<int64_t>(q1) * Np + p1] = static_cast<T>(0);
-              L.flags[sweep] = 1;
             } else {
               nxt[static_cast<int64_t>(p1) * Np + p1] = app;
               nxt[static_cast<int64_t>(q1) * Np + q1] = aqq;
@@ -565,10 +615,6 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
             }
             continue;
           }
-          const T a2 = ldg_cg(cur + static_cast<int64_t>(p2) * Np + q2);
-          if (q2 < N && fabs(a2) > thr)
-            jacobi_rot(ldg_cg(cur + static_cast<int64_t>(p2) * Np + p2), ldg_cg(cur + static_cast<int64_t>(q2) * Np + q2),
-                       a2, c2, s2, t2);
           const T x11 = ldg_cg(cur + static_cast<int64_t>(p1) * Np + p2);
           const T x12 = ldg_cg(cur + static_cast<int64_t>(p1) * Np + q2);
           const T x21 = ldg_cg(cur + static_cast<int64_t>(q1) * Np + p2);
@@ -588,14 +634,10 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
         } else {
           const int64_t t2i = task - nblk;
           const int row = static_cast<int>(t2i / H), k = static_cast<int>(t2i - static_cast<int64_t>(row) * H);
-          int pp, qq;
-          rr_pair(k, r, Np, pp, qq);
-          if (qq >= N) continue;
-          const T apq = ldg_cg(cur + static_cast<int64_t>(pp) * Np + qq);
-          if (!(fabs(apq) > thr)) continue;
-          T c, s, t;
-          jacobi_rot(ldg_cg(cur + static_cast<int64_t>(pp) * Np + pp), ldg_cg(cur + static_cast<int64_t>(qq) * Np + qq), apq,
-                     c, s, t);
+          const T s = rs[k];
+          if (s == static_cast<T>(0)) continue;
+          const T c = rc[k];
+          const int pp = rp[k], qq = rq[k];
           T* vr = V + static_cast<int64_t>(row) * Np;
           const T vp = ldg_cg(vr + pp), vq = ldg_cg(vr + qq);
           vr[pp] = c * vp - s * vq;
@@ -607,9 +649,7 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
       cur = nxt;
       nxt = tmp;
     }
-    sweeps = sweep + 1;
-    const int any = __ldcg(L.flags + sweep);
-    if (!any) break;
+    if (!sweep_rot) break;
   }
 
   // U = V max(diag B, 0) V^T on lower tiles; write u and v = u - W
@@ -642,6 +682,7 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *L.sweeps_out = sweeps;
+    p.blk_sweeps[bid] = sweeps;
     *L.warm = warm ? warm_count + 1 : 1;
   }
 }
@@ -787,22 +828,23 @@ int large_grid_size(int N) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_psd_large<T>, 256, 0);
   if (per < 1) per = 1;
-  int g = sms * (per > 2 ? 2 : per);
   (void)N;
-  return g;
+  return sms;  // one CTA per SM: co-resident, and fewer barrier arrivals
+}
+
+size_t large_smem_bytes(int N, size_t es) {
+  const size_t H = static_cast<size_t>(N + (N & 1)) / 2;
+  return H * (3 * es + 2 * sizeof(int));
 }
 
 template <typename T>
 cudaError_t launch_psd_large(const DevPlan<T>& p, int bid, int N, const LargeScratch<T>& ls, int grid, cudaStream_t s) {
-  (void)N;
-  cudaError_t e = cudaMemsetAsync(ls.bar, 0, sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(ls.flags, 0, sizeof(int32_t) * kMaxSweeps, s);
+  cudaError_t e = cudaMemsetAsync(ls.bar, 0, 2 * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = large_smem_bytes(N, sizeof(T));
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

@@ -56,6 +56,7 @@ struct DevPlan {
   double* ra = nullptr;    // residual work (M)
   double* atyl = nullptr;  // residual work (TL)
   int32_t* err = nullptr;  // device error word (nonzero: a bounded wait expired)
+  int32_t* blk_sweeps = nullptr;  // Jacobi sweeps of each block in the last iteration
 };
 
 // Scratch of the large-block (cooperative) projection, one per large block.
@@ -67,8 +68,8 @@ struct LargeScratch {
   T* V = nullptr;    // eigenvectors, kept across iterations (warm start)
   T* T1 = nullptr;   // GEMM temporary
   double* partial = nullptr;   // per-CTA partial sums
-  int32_t* flags = nullptr;    // per-sweep rotation flags [kMaxSweeps]
-  uint32_t* bar = nullptr;     // grid barrier counter (zeroed before each launch)
+  int32_t* flags = nullptr;    // unused (kept for layout)
+  uint32_t* bar = nullptr;     // grid barrier: [arrivals, released generation], zeroed before each launch
   int32_t* sweeps_out = nullptr;  // number of sweeps of the last launch
   int32_t* warm = nullptr;     // 1 if V holds the previous eigenvectors
 };
@@ -95,6 +96,7 @@ cudaError_t prepare_kernels(int max_small_n, int max_teff);
 template <typename T>
 cudaError_t launch_residuals(const DevPlan<T>& p, const LaunchShape& ls, cudaStream_t s);
 size_t psd_small_smem_bytes(int maxN, bool fp64);
+size_t large_smem_bytes(int N, size_t es);
 int psd_small_max_n(bool fp64);
 
 }  // namespace sos

@@ -51,7 +51,8 @@ struct InstResid {
   double nonfinite;   // > 0 if a non-finite value was seen
 };
 
-enum BlockKind : int32_t { kPlain = 0, kWeighted = 1 };
+// kRaw: the projection input is the stored vector itself (standalone projection).
+enum BlockKind : int32_t { kPlain = 0, kWeighted = 1, kRaw = 2 };
 
 struct BlockDesc {
   int64_t x_off;      // first packed entry of the block in x

@@ -1,0 +1,81 @@
+"""GPU parity of the PSD-cone projection kernels (the Gram-block part of
+eq. (20b)) through sos_psd_project, against the oracle's eigen-clamp, on
+random and degenerate symmetric matrices.  Sizes cover the shared-memory
+path (N <= 96) and the grid path (N > 96), odd and even N, and a ragged
+16-wide tile tail."""
+
+import numpy as np
+import pytest
+
+from oracle.admm import proj_psd
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import os
+
+    import torch
+
+    from paper_1708_04174_gb300 import build, capi
+
+    if not os.path.exists(capi.LIB_PATH):
+        build.build()
+    return torch, capi
+
+
+def pack(X):
+    N = X.shape[0]
+    out = []
+    for j in range(N):
+        col = X[j:, j].copy()
+        col[1:] *= np.sqrt(2.0)
+        out.append(col)
+    return np.concatenate(out)
+
+
+def project_gpu(env, X):
+    torch, capi = env
+    w = torch.tensor(pack(X), dtype=torch.float64, device="cuda")
+    u = torch.empty_like(w)
+    capi.psd_project(w.data_ptr(), u.data_ptr(), X.shape[0], torch.cuda.current_stream().cuda_stream)
+    return u.cpu().numpy()
+
+
+def sym(N, seed, scale=1.0):
+    a = np.random.default_rng(seed).standard_normal((N, N)) * scale
+    return 0.5 * (a + a.T)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 7, 16, 17, 28, 33, 64, 84, 96, 97, 130, 231])
+def test_projection_matches_eigh(env, N):
+    X = sym(N, N)
+    got = project_gpu(env, X)
+    want = pack(proj_psd(X))
+    assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(X).max()) * N
+
+
+@pytest.mark.parametrize("N", [5, 40, 120])
+def test_projection_degenerate_inputs(env, N):
+    rng = np.random.default_rng(N)
+    Q, _ = np.linalg.qr(rng.standard_normal((N, N)))
+    lam = np.zeros(N)
+    lam[: N // 3] = rng.uniform(0.5, 2.0, N // 3)  # PSD, rank deficient
+    lam[N // 3: N // 2] = -rng.uniform(0.5, 2.0, N // 2 - N // 3)
+    lam[N // 2: N // 2 + 2] = 1.0  # repeated eigenvalue
+    X = (Q * lam) @ Q.T
+    X = 0.5 * (X + X.T)
+    tol = 1e-12 * N
+    assert np.abs(project_gpu(env, X) - pack(proj_psd(X))).max() <= tol
+    P = proj_psd(X)
+    assert np.abs(project_gpu(env, P) - pack(P)).max() <= tol  # PSD input is a fixed point
+    assert np.abs(project_gpu(env, -P)).max() <= tol  # NSD input maps to 0
+    assert np.abs(project_gpu(env, np.zeros((N, N)))).max() == 0.0
+
+
+def test_projection_rejects_bad_size(env):
+    torch, capi = env
+    w = torch.zeros(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(RuntimeError):
+        capi.psd_project(w.data_ptr(), w.data_ptr(), 0)
