@@ -152,7 +152,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="ball_pop_n20", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tt", action="store_true", help="skip the time-to-1e-4 solves")
     args = ap.parse_args()
@@ -176,7 +176,7 @@ def main():
     from paper_1708_04174_gb300 import capi
 
     prog = make_program(args.workload)
-    prec = capi.PREC_FP64 if args.precision == "fp64" else capi.PREC_FP32
+    prec = {"fp64": capi.PREC_FP64, "mixed": capi.PREC_MIXED, "fp32": capi.PREC_FP32}[args.precision]
     solver = capi.Solver(prog, precision=prec, k_check=10)
     stream = torch.cuda.ExternalStream(solver.stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -290,11 +290,11 @@ def main():
 
     if not args.no_tt:
         tt = {}
-        for nm, pr in (("fp64", capi.PREC_FP64), ("fp32", capi.PREC_FP32)):
+        for nm, pr in (("fp64", capi.PREC_FP64), ("mixed_fp32_projections", capi.PREC_MIXED)):
             s2 = capi.Solver(prog, precision=pr, k_check=10)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            r = s2.solve(1e-4, 20000, want_solution=False)[0]
+            r = s2.solve(1e-4, 3000, want_solution=False)[0]
             dt = time.perf_counter() - t0
             tt[nm] = {"seconds": dt, "iters": r["iters"], "status": r["status"], "obj": r["obj_primal"]}
             s2.close()

@@ -56,9 +56,12 @@ extern "C" {
 #define SOS_MAX_ITER 4
 #define SOS_NUMERICAL 5
 
-/* ---- precision forms (sos_options.precision) ---- */
-#define SOS_PREC_FP64 0  /* plain: FP64 iterates, FP64 PSD projections */
-#define SOS_PREC_FP32 1  /* FP32 iterates and projections; FP64 Woodbury, tau/kappa, residuals */
+/* ---- precision forms (sos_options.precision) ----
+ * The Woodbury core (factor and solve), tau/kappa and every residual are FP64
+ * in all forms. */
+#define SOS_PREC_FP64 0   /* plain: FP64 iterates, FP64 PSD projections */
+#define SOS_PREC_MIXED 1  /* FP64 iterates, PSD projections computed in FP32 */
+#define SOS_PREC_FP32 2   /* FP32 iterates and FP32 projections */
 
 typedef struct sos_handle sos_handle;
 

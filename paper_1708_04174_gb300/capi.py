@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libsos.so")
 SOS_OK = 0
 SOS_ERR_INVALID_ARG, SOS_ERR_CUDA, SOS_ERR_FACTOR, SOS_ERR_TIMEOUT, SOS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5
 RUNNING, SOLVED, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE, MAX_ITER, NUMERICAL = 0, 1, 2, 3, 4, 5
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_MIXED, PREC_FP32 = 0, 1, 2
 
 _i32p = C.POINTER(C.c_int32)
 _f64p = C.POINTER(C.c_double)

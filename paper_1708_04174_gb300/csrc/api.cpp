@@ -18,6 +18,11 @@ using namespace sos;
 
 namespace {
 thread_local std::string g_setup_error;
+}  // namespace
+
+void sos::set_global_error(const std::string& msg) { g_setup_error = msg; }
+
+namespace {
 
 struct SmallClass {
   int maxN;
@@ -47,8 +52,10 @@ struct sos_handle {
   DevPlan<float> d32;
   LaunchShape shape;
   std::vector<SmallClass> small;
-  std::vector<LargeBlock<double>> large64;
-  std::vector<LargeBlock<float>> large32;
+  std::vector<LargeBlock<double>> large64;  // FP64 projections
+  std::vector<LargeBlock<float>> large32;   // FP32 projections
+  SmallWarm<double> warm64;
+  SmallWarm<float> warm32;
   int32_t* active = nullptr;  // device
   std::vector<int32_t> active_h;
   std::vector<int32_t> iters_h, status_h;
@@ -170,9 +177,10 @@ int make_large(sos_handle* h, std::vector<LargeBlock<T>>& out, const std::vector
     lb.bid = bid;
     lb.N = h->blocks[bid].N;
     const size_t Np = lb.N + (lb.N & 1);
-    lb.grid = large_grid_size<T>(lb.N);
+    lb.grid = large_grid_size(lb.N);
     TRY(alloc(h, Np * Np, &lb.scratch.Wf));
     TRY(alloc(h, Np * Np, &lb.scratch.B0));
+    TRY(alloc(h, Np * Np, &lb.scratch.B1));
     TRY(alloc(h, Np * Np, &lb.scratch.V));
     TRY(alloc(h, Np * Np, &lb.scratch.T1));
     TRY(alloc(h, static_cast<size_t>(lb.grid), &lb.scratch.partial));
@@ -185,8 +193,9 @@ int make_large(sos_handle* h, std::vector<LargeBlock<T>>& out, const std::vector
   return SOS_OK;
 }
 
-template <typename T>
-cudaError_t enqueue_stage(sos_handle* h, const DevPlan<T>& p, std::vector<LargeBlock<T>>& large, int stage) {
+template <typename T, typename TC>
+cudaError_t enqueue_stage(sos_handle* h, const DevPlan<T>& p, std::vector<LargeBlock<TC>>& large,
+                          const SmallWarm<TC>& wm, int stage) {
   cudaError_t e = cudaSuccess;
   if (stage == 0 || stage == 3) {
     e = launch_affine<T>(p, h->shape, h->stream);
@@ -194,25 +203,32 @@ cudaError_t enqueue_stage(sos_handle* h, const DevPlan<T>& p, std::vector<LargeB
   }
   if (stage == 1 || stage == 3)
     for (auto& c : h->small) {
-      e = launch_psd_small<T>(p, c.ids, c.count, c.maxN, h->stream);
+      e = launch_psd_small<T, TC>(p, c.ids, c.count, c.maxN, wm, h->stream);
       if (e != cudaSuccess) return e;
     }
   if (stage == 2 || stage == 3)
     for (auto& lb : large) {
-      e = launch_psd_large<T>(p, lb.bid, lb.N, lb.scratch, lb.grid, h->stream);
+      e = launch_psd_large<T, TC>(p, lb.bid, lb.N, lb.scratch, lb.grid, h->stream);
       if (e != cudaSuccess) return e;
     }
   return e;
 }
 
-cudaError_t enqueue_iteration(sos_handle* h) {
-  if (h->precision == SOS_PREC_FP64) return enqueue_stage<double>(h, h->d64, h->large64, 3);
-  return enqueue_stage<float>(h, h->d32, h->large32, 3);
+cudaError_t enqueue_any(sos_handle* h, int stage) {
+  if (h->precision == SOS_PREC_FP64) return enqueue_stage<double, double>(h, h->d64, h->large64, h->warm64, stage);
+  if (h->precision == SOS_PREC_MIXED) return enqueue_stage<double, float>(h, h->d64, h->large32, h->warm32, stage);
+  return enqueue_stage<float, float>(h, h->d32, h->large32, h->warm32, stage);
 }
+
+cudaError_t enqueue_iteration(sos_handle* h) { return enqueue_any(h, 3); }
+
+bool iter64(const sos_handle* h) { return h->precision != SOS_PREC_FP32; }
 
 void reset_warm(sos_handle* h) {
   for (auto& lb : h->large64) cudaMemsetAsync(lb.scratch.warm, 0, sizeof(int32_t), h->stream);
   for (auto& lb : h->large32) cudaMemsetAsync(lb.scratch.warm, 0, sizeof(int32_t), h->stream);
+  if (h->warm64.count) cudaMemsetAsync(h->warm64.count, 0, sizeof(int32_t) * h->blocks.size(), h->stream);
+  if (h->warm32.count) cudaMemsetAsync(h->warm32.count, 0, sizeof(int32_t) * h->blocks.size(), h->stream);
 }
 
 int check_err_word(sos_handle* h) {
@@ -230,7 +246,7 @@ int cold_start(sos_handle* h) {
   std::vector<double> one(h->n_inst, 1.0);
   CK(cudaMemcpyAsync(h->d64.tau, one.data(), sizeof(double) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->d64.kappa, one.data(), sizeof(double) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
-  if (h->precision == SOS_PREC_FP64) {
+  if (iter64(h)) {
     CK(cudaMemsetAsync(h->d64.ux, 0, sizeof(double) * h->NX, h->stream));
     CK(cudaMemsetAsync(h->d64.vx, 0, sizeof(double) * h->NX, h->stream));
     CK(cudaMemsetAsync(h->d64.uy, 0, sizeof(double) * h->M, h->stream));
@@ -339,10 +355,10 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   for (auto& in : P.inst) max_teff = std::max(max_teff, in.t_eff);
 
   // projection classes: small blocks (shared-memory Jacobi) by size class, large blocks (grid Jacobi)
-  const bool fp64 = h->precision == SOS_PREC_FP64;
+  const bool fp64 = h->precision == SOS_PREC_FP64;  // FP64 projections
   const int small_cap = psd_small_max_n(fp64);
-  const int caps[] = {16, 32, 48, 64, 96, 128, 160};
-  std::vector<std::vector<int32_t>> cls(7);
+  const int caps[] = {16, 32, 48, 64, 96, 128};
+  std::vector<std::vector<int32_t>> cls(6);
   std::vector<int> large;
   int max_small = 0;
   for (int b = 0; b < static_cast<int>(P.blocks.size()); ++b) {
@@ -351,32 +367,49 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
       large.push_back(b);
       continue;
     }
-    for (int k = 0; k < 7; ++k)
+    for (int k = 0; k < 6; ++k)
       if (N <= caps[k]) {
         cls[k].push_back(b);
         max_small = std::max(max_small, caps[k]);
         break;
       }
   }
-  for (int k = 0; k < 7; ++k)
+  // eigenvector storage of small blocks (warm start)
+  int64_t voff = 0;
+  for (int k = 0; k < 6; ++k)
+    for (int32_t b : cls[k]) {
+      P.blocks[b].v_off = voff;
+      voff += static_cast<int64_t>(P.blocks[b].N) * P.blocks[b].N;
+    }
+  h->blocks = P.blocks;
+  BlockDesc* bl2;
+  TRY(upload(h, P.blocks, &bl2));
+  c.blocks = bl2;
+  if (fp64) {
+    TRY(alloc(h, static_cast<size_t>(voff), &h->warm64.V));
+    TRY(alloc(h, P.blocks.size(), &h->warm64.count));
+  } else {
+    TRY(alloc(h, static_cast<size_t>(voff), &h->warm32.V));
+    TRY(alloc(h, P.blocks.size(), &h->warm32.count));
+  }
+  for (int k = 0; k < 6; ++k)
     if (!cls[k].empty()) {
       SmallClass sc{caps[k], static_cast<int>(cls[k].size()), nullptr};
       TRY(upload(h, cls[k], &sc.ids));
       h->small.push_back(sc);
     }
-  if (fp64) {
+  if (h->precision == SOS_PREC_FP64) {
     TRY(make_devplan(h, c, max_teff, h->d64));
     TRY(make_large(h, h->large64, large));
-    CK(prepare_kernels<double>(max_small, max_teff));
+    CK((prepare_kernels<double, double>(max_small, max_teff)));
+  } else if (h->precision == SOS_PREC_MIXED) {
+    TRY(make_devplan(h, c, max_teff, h->d64));
+    TRY(make_large(h, h->large32, large));
+    CK((prepare_kernels<double, float>(max_small, max_teff)));
   } else {
     TRY(make_devplan(h, c, max_teff, h->d32));
     TRY(make_large(h, h->large32, large));
-    CK(prepare_kernels<float>(max_small, max_teff));
-    // share the FP64-only pointers through d64 for the common helpers
-    h->d64.tau = c.tau;
-    h->d64.kappa = c.kappa;
-    h->d64.err = c.err;
-    h->d64.resid = c.resid;
+    CK((prepare_kernels<float, float>(max_small, max_teff)));
   }
   h->d64.tau = c.tau;
   h->d64.kappa = c.kappa;
@@ -408,7 +441,7 @@ int copy_iterate_out(sos_handle* h, const DevPlan<T>& p, std::vector<double>& ux
 
 int get_all(sos_handle* h, std::vector<double>& ux, std::vector<double>& vx, std::vector<double>& uy,
             std::vector<double>& vy, std::vector<double>& tau, std::vector<double>& kappa) {
-  if (h->precision == SOS_PREC_FP64) return copy_iterate_out(h, h->d64, ux, vx, uy, vy, tau, kappa);
+  if (iter64(h)) return copy_iterate_out(h, h->d64, ux, vx, uy, vy, tau, kappa);
   return copy_iterate_out(h, h->d32, ux, vx, uy, vy, tau, kappa);
 }
 
@@ -452,7 +485,7 @@ int sos_setup(const sos_program* progs, int32_t n_progs, const sos_options* opts
   *out = nullptr;
   auto h = std::make_unique<sos_handle>();
   if (opts) {
-    if (opts->precision != SOS_PREC_FP64 && opts->precision != SOS_PREC_FP32) {
+    if (opts->precision != SOS_PREC_FP64 && opts->precision != SOS_PREC_MIXED && opts->precision != SOS_PREC_FP32) {
       g_setup_error = "unknown precision";
       return SOS_ERR_INVALID_ARG;
     }
@@ -551,8 +584,8 @@ int sos_solve(sos_handle* h, double tol, int32_t max_iter, sos_result* results) 
     int rc = sos_iterate(h, k);
     if (rc != SOS_OK) return rc;
     it += k;
-    cudaError_t e = h->precision == SOS_PREC_FP64 ? launch_residuals<double>(h->d64, h->shape, h->stream)
-                                                  : launch_residuals<float>(h->d32, h->shape, h->stream);
+    cudaError_t e = iter64(h) ? launch_residuals<double>(h->d64, h->shape, h->stream)
+                              : launch_residuals<float>(h->d32, h->shape, h->stream);
     if (e != cudaSuccess) return set_err(h, SOS_ERR_CUDA, std::string("residuals: ") + cudaGetErrorString(e));
     CK(cudaMemcpyAsync(R.data(), h->d64.resid, sizeof(InstResid) * h->n_inst, cudaMemcpyDeviceToHost, h->stream));
     rc = check_err_word(h);  // synchronises
@@ -640,7 +673,7 @@ int sos_get_iterate(sos_handle* h, double* u, double* v) {
 
 int sos_set_iterate(sos_handle* h, const double* u, const double* v) {
   if (!h || !u || !v) return SOS_ERR_INVALID_ARG;
-  int rc = h->precision == SOS_PREC_FP64 ? copy_iterate_in(h, h->d64, u, v) : copy_iterate_in(h, h->d32, u, v);
+  int rc = iter64(h) ? copy_iterate_in(h, h->d64, u, v) : copy_iterate_in(h, h->d32, u, v);
   if (rc != SOS_OK) return rc;
   std::fill(h->active_h.begin(), h->active_h.end(), 1);
   std::fill(h->iters_h.begin(), h->iters_h.end(), 0);
@@ -739,12 +772,12 @@ int sos_psd_project(const double* in, double* out, int32_t N, void* stream) {
     cudaError_t e;
     if (small) {
       const int cap = N <= 16 ? 16 : N <= 32 ? 32 : N <= 48 ? 48 : N <= 64 ? 64 : 96;
-      e = prepare_kernels<double>(cap, 0);
-      if (e == cudaSuccess) e = launch_psd_small<double>(p, ids, 1, cap, s);
+      e = prepare_kernels<double, double>(cap, 0);
+      if (e == cudaSuccess) e = launch_psd_small<double, double>(p, ids, 1, cap, SmallWarm<double>(), s);
     } else {
       std::vector<LargeBlock<double>> lb;
       if ((rc = make_large(h, lb, std::vector<int>(1, 0))) != SOS_OK) break;
-      e = launch_psd_large<double>(p, 0, N, lb[0].scratch, lb[0].grid, s);
+      e = launch_psd_large<double, double>(p, 0, N, lb[0].scratch, lb[0].grid, s);
     }
     if (e != cudaSuccess) {
       rc = set_err(h, SOS_ERR_CUDA, std::string("projection launch: ") + cudaGetErrorString(e));
@@ -790,8 +823,7 @@ void* sos_stream(sos_handle* h) { return h ? static_cast<void*>(h->stream) : nul
 
 int sos_run_stage(sos_handle* h, int32_t stage) {
   if (!h || stage < 0 || stage > 3) return SOS_ERR_INVALID_ARG;
-  cudaError_t e = h->precision == SOS_PREC_FP64 ? enqueue_stage<double>(h, h->d64, h->large64, stage)
-                                                : enqueue_stage<float>(h, h->d32, h->large32, stage);
+  cudaError_t e = enqueue_any(h, stage);
   if (e != cudaSuccess) return set_err(h, SOS_ERR_CUDA, std::string("stage launch: ") + cudaGetErrorString(e));
   return SOS_OK;
 }

@@ -269,43 +269,72 @@ __device__ __forceinline__ void jacobi_rot(T app, T aqq, T apq, T& c, T& s, T& t
 // memory with the round-robin parallel ordering.  Each round applies Np/2
 // disjoint rotations as 2x2-block updates of A = J^T A J and column updates
 // V = V J.  A sweep without any rotation above eps |W|_F ends the solve.
+// T is the storage type of the iterates, TC the compute type.
+// Warm start: the eigenvectors of the previous iteration (kept per block,
+// re-orthonormalised by one Newton-Schulz step V (3 I - V^T V) / 2 before
+// they are stored) give B = V^T W V, nearly diagonal after the first
+// iterations, so few sweeps remain.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* ids) {
+template <typename T, typename TC>
+__global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* ids, SmallWarm<TC> wm) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[40];
   __shared__ int last_rot;  // index of the last round that had a rotation
-  const BlockDesc bd = p.blocks[ids[blockIdx.x]];
+  const int bid = ids[blockIdx.x];
+  const BlockDesc bd = p.blocks[bid];
   if (!p.active[bd.inst]) return;
-  const double s_sm = p.st[bd.inst].s;
-  const int N = bd.N, Np = N + (N & 1), ld = Np + 1, H = Np / 2;
-  T* A = reinterpret_cast<T*>(smraw);
-  T* V = A + Np * ld;
-  T* rc = V + Np * ld;
-  T* rs = rc + H;
-  T* rt = rs + H;
-  T* lam = rt + H;
-  int* rp = reinterpret_cast<int*>(lam + Np);
-  int* rq = rp + H;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) last_rot = -1;  // block_sum below orders this before any use
+  const double s_sm = p.st[bd.inst].s;
+  const int N = bd.N, Np = N + (N & 1), ld = Np + 1, H = Np / 2;
+  TC* A = reinterpret_cast<TC*>(smraw);
+  TC* V = A + Np * ld;
+  TC* T1 = V + Np * ld;
+  TC* rc = T1 + Np * ld;
+  TC* rs = rc + H;
+  TC* rt = rs + H;
+  TC* lam = rt + H;
+  int* rp = reinterpret_cast<int*>(lam + Np);
+  int* rq = rp + H;
+  TC* gV = (wm.V != nullptr && bd.v_off >= 0) ? wm.V + bd.v_off : nullptr;
+  const int wc = gV ? wm.count[bid] : 0;
+  const bool warm = wc > 0 && wc < wm.limit;
 
   double nrm = 0.0;
   for (int q = tid; q < Np * Np; q += nt) {
     const int i = q / Np, j = q - i * Np;
-    V[i * ld + j] = (i == j) ? static_cast<T>(1) : static_cast<T>(0);
     if (i >= N || j >= N) {
-      A[i * ld + j] = static_cast<T>(0);
+      A[i * ld + j] = static_cast<TC>(0);
+      V[i * ld + j] = (i == j) ? static_cast<TC>(1) : static_cast<TC>(0);
       continue;
     }
+    V[i * ld + j] = warm ? gV[i * N + j] : ((i == j) ? static_cast<TC>(1) : static_cast<TC>(0));
     if (i < j) continue;
     const T w = proj_input(p, bd, packed_index(i, j, N), i != j, s_sm);
     nrm += d(w) * d(w);
-    const T a = (i == j) ? w : w * rsqrt2<T>();
+    const TC a = (i == j) ? static_cast<TC>(w) : static_cast<TC>(d(w) * 0.70710678118654752440);
     A[i * ld + j] = a;
     A[j * ld + i] = a;
   }
-  const T thr = static_cast<T>(sqrt(block_sum(nrm, red))) * teps<T>();
+  const TC thr = static_cast<TC>(sqrt(block_sum(nrm, red))) * teps<TC>();
+  if (warm) {
+    for (int q = tid; q < N * N; q += nt) {  // T1 = W V
+      const int i = q / N, j = q - i * N;
+      TC acc = 0;
+      for (int k = 0; k < N; ++k) acc += A[i * ld + k] * V[k * ld + j];
+      T1[i * ld + j] = acc;
+    }
+    __syncthreads();
+    for (int q = tid; q < N * N; q += nt) {  // A = V^T T1, lower triangle mirrored
+      const int i = q / N, j = q - i * N;
+      if (i < j) continue;
+      TC acc = 0;
+      for (int k = 0; k < N; ++k) acc += V[k * ld + i] * T1[k * ld + j];
+      A[i * ld + j] = acc;
+      A[j * ld + i] = acc;
+    }
+    __syncthreads();
+  }
 
   int sweeps_done = 0;
   int round_id = 0;
@@ -316,9 +345,9 @@ __global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* 
       for (int k = tid; k < H; k += nt) {
         int a, b;
         rr_pair(k, r, Np, a, b);
-        T c = 1, s = 0, t = 0;
+        TC c = 1, s = 0, t = 0;
         if (b < N) {
-          const T apq = A[a * ld + b];
+          const TC apq = A[a * ld + b];
           if (fabs(apq) > thr) {
             jacobi_rot(A[a * ld + a], A[b * ld + b], apq, c, s, t);
             last_rot = round_id;
@@ -339,24 +368,24 @@ __global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* 
           const int k1 = task / H, k2 = task - k1 * H;
           if (k1 > k2) continue;
           const int p1 = rp[k1], q1 = rq[k1], p2 = rp[k2], q2 = rq[k2];
-          const T c1 = rc[k1], s1 = rs[k1];
+          const TC c1 = rc[k1], s1 = rs[k1];
           if (k1 == k2) {
-            if (s1 != static_cast<T>(0)) {
-              const T apq = A[p1 * ld + q1], t1 = rt[k1];
+            if (s1 != static_cast<TC>(0)) {
+              const TC apq = A[p1 * ld + q1], t1 = rt[k1];
               A[p1 * ld + p1] -= t1 * apq;
               A[q1 * ld + q1] += t1 * apq;
-              A[p1 * ld + q1] = static_cast<T>(0);
-              A[q1 * ld + p1] = static_cast<T>(0);
+              A[p1 * ld + q1] = static_cast<TC>(0);
+              A[q1 * ld + p1] = static_cast<TC>(0);
             }
             continue;
           }
-          const T c2 = rc[k2], s2 = rs[k2];
-          if (s1 == static_cast<T>(0) && s2 == static_cast<T>(0)) continue;
-          const T x11 = A[p1 * ld + p2], x12 = A[p1 * ld + q2], x21 = A[q1 * ld + p2], x22 = A[q1 * ld + q2];
-          const T y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
-          const T y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
-          const T z11 = c2 * y11 - s2 * y12, z12 = s2 * y11 + c2 * y12;
-          const T z21 = c2 * y21 - s2 * y22, z22 = s2 * y21 + c2 * y22;
+          const TC c2 = rc[k2], s2 = rs[k2];
+          if (s1 == static_cast<TC>(0) && s2 == static_cast<TC>(0)) continue;
+          const TC x11 = A[p1 * ld + p2], x12 = A[p1 * ld + q2], x21 = A[q1 * ld + p2], x22 = A[q1 * ld + q2];
+          const TC y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
+          const TC y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
+          const TC z11 = c2 * y11 - s2 * y12, z12 = s2 * y11 + c2 * y12;
+          const TC z21 = c2 * y21 - s2 * y22, z22 = s2 * y21 + c2 * y22;
           A[p1 * ld + p2] = z11;
           A[p1 * ld + q2] = z12;
           A[q1 * ld + p2] = z21;
@@ -368,11 +397,11 @@ __global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* 
         } else {
           const int t2 = task - nblk;
           const int row = t2 / H, k = t2 - row * H;
-          const T s = rs[k];
-          if (s == static_cast<T>(0)) continue;
-          const T c = rc[k];
+          const TC s = rs[k];
+          if (s == static_cast<TC>(0)) continue;
+          const TC c = rc[k];
           const int pp = rp[k], qq = rq[k];
-          const T vp = V[row * ld + pp], vq = V[row * ld + qq];
+          const TC vp = V[row * ld + pp], vq = V[row * ld + qq];
           V[row * ld + pp] = c * vp - s * vq;
           V[row * ld + qq] = s * vp + c * vq;
         }
@@ -382,20 +411,36 @@ __global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* 
     if (!rotated) break;
   }
 
-  // P_S+(W) = V max(Lambda, 0) V^T; v = u - W
-  if (tid == 0) p.blk_sweeps[ids[blockIdx.x]] = sweeps_done;
-  for (int k = tid; k < N; k += nt) lam[k] = fmax(A[k * ld + k], static_cast<T>(0));
+  // P_S+(W) = V max(Lambda, 0) V^T; v = u - W (in the storage type)
+  if (tid == 0) p.blk_sweeps[bid] = sweeps_done;
+  for (int k = tid; k < N; k += nt) lam[k] = fmax(A[k * ld + k], static_cast<TC>(0));
   __syncthreads();
   for (int q = tid; q < N * N; q += nt) {
     const int i = q / N, j = q - i * N;
     if (i < j) continue;
-    T u = 0;
+    TC u = 0;
     for (int k = 0; k < N; ++k) u += V[i * ld + k] * lam[k] * V[j * ld + k];
     const int64_t kk = packed_index(i, j, N);
     const T w = proj_input(p, bd, kk, i != j, s_sm);
-    if (i != j) u *= static_cast<T>(kSqrt2);
-    p.ux[bd.x_off + kk] = u;
-    p.vx[bd.x_off + kk] = u - w;
+    const T uu = (i != j) ? static_cast<T>(d(u) * kSqrt2) : static_cast<T>(u);
+    p.ux[bd.x_off + kk] = uu;
+    p.vx[bd.x_off + kk] = uu - w;
+  }
+  if (gV) {  // keep V for the next iteration: V (3 I - V^T V) / 2
+    for (int q = tid; q < N * N; q += nt) {
+      const int i = q / N, j = q - i * N;
+      TC acc = 0;
+      for (int k = 0; k < N; ++k) acc += V[k * ld + i] * V[k * ld + j];
+      T1[i * ld + j] = ((i == j) ? static_cast<TC>(1.5) : static_cast<TC>(0)) - static_cast<TC>(0.5) * acc;
+    }
+    __syncthreads();
+    for (int q = tid; q < N * N; q += nt) {
+      const int i = q / N, j = q - i * N;
+      TC acc = 0;
+      for (int k = 0; k < N; ++k) acc += V[i * ld + k] * T1[k * ld + j];
+      gV[i * N + j] = acc;
+    }
+    if (tid == 0) wm.count[bid] = warm ? wc + 1 : 1;
   }
 }
 
@@ -487,11 +532,11 @@ __device__ T tile_mm(const T* A, const T* B, int Np, int ti, int tj, int mode, T
   return acc;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeScratch<T> L) {
+template <typename T, typename TC>
+__global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeScratch<TC> L) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double red[40];
-  __shared__ T sA[16 * 17], sB[16 * 17];
+  __shared__ TC sA[16 * 17], sB[16 * 17];
   __shared__ int any_rot;
   const BlockDesc bd = p.blocks[bid];
   if (!p.active[bd.inst]) return;
@@ -504,37 +549,37 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
   const unsigned G = gridDim.x;
   int32_t* err = p.err;
   const int warm_count = __ldcg(L.warm);
-  const bool warm = warm_count > 0 && warm_count < 256;
-  T* Wf = L.Wf;
-  T* V = L.V;
+  const bool warm = warm_count > 0 && warm_count < 1024;
+  TC* Wf = L.Wf;
+  TC* V = L.V;
 
   // load W (full symmetric, svec unscaled), norm, V = I when cold
   double nrm = 0.0;
   for (int64_t q = gt; q < static_cast<int64_t>(Np) * Np; q += gs) {
     const int i = static_cast<int>(q / Np), j = static_cast<int>(q - static_cast<int64_t>(i) * Np);
-    if (!warm) V[q] = (i == j) ? static_cast<T>(1) : static_cast<T>(0);
+    if (!warm) V[q] = (i == j) ? static_cast<TC>(1) : static_cast<TC>(0);
     if (i >= N || j >= N) {
-      Wf[q] = static_cast<T>(0);
+      Wf[q] = static_cast<TC>(0);
       continue;
     }
     const int ii = i >= j ? i : j, jj = i >= j ? j : i;
     const T w = proj_input(p, bd, packed_index(ii, jj, N), ii != jj, s_sm);
     if (i >= j) nrm += d(w) * d(w);
-    Wf[q] = (i == j) ? w : w * rsqrt2<T>();
+    Wf[q] = (i == j) ? static_cast<TC>(w) : static_cast<TC>(d(w) * 0.70710678118654752440);
   }
   const double part = block_sum(nrm, red);
   if (threadIdx.x == 0) L.partial[blockIdx.x] = part;
   if (!grid_barrier(L.bar, (++gen) * G, err)) return;
   double tot = 0.0;
   for (unsigned c = 0; c < G; ++c) tot += __ldcg(L.partial + c);
-  const T thr = static_cast<T>(sqrt(tot)) * teps<T>();
+  const TC thr = static_cast<TC>(sqrt(tot)) * teps<TC>();
 
   const int nt = (Np + 15) / 16;
-  T* cur = Wf;
+  TC* cur = Wf;
   if (warm) {
     for (int tile = blockIdx.x; tile < nt * nt; tile += G) {  // T1 = W V
       const int ti = tile / nt, tj = tile - ti * nt;
-      const T v = tile_mm(Wf, V, Np, ti, tj, 0, sA, sB);
+      const TC v = tile_mm(Wf, V, Np, ti, tj, 0, sA, sB);
       const int i = ti * 16 + (threadIdx.x >> 4), j = tj * 16 + (threadIdx.x & 15);
       if (i < Np && j < Np) L.T1[static_cast<int64_t>(i) * Np + j] = v;
     }
@@ -542,7 +587,7 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
     for (int tile = blockIdx.x; tile < nt * nt; tile += G) {  // B = V^T T1 (lower tiles, mirrored)
       const int ti = tile / nt, tj = tile - ti * nt;
       if (ti < tj) continue;
-      const T v = tile_mm(V, L.T1, Np, ti, tj, 1, sA, sB);
+      const TC v = tile_mm(V, L.T1, Np, ti, tj, 1, sA, sB);
       const int i = ti * 16 + (threadIdx.x >> 4), j = tj * 16 + (threadIdx.x & 15);
       if (i < Np && j < Np && i >= j) {
         Wf[static_cast<int64_t>(i) * Np + j] = v;
@@ -557,10 +602,10 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
   // same decisions: a round without rotations writes nothing and is skipped
   // without a barrier, and the sweep loop ends everywhere at once.  Reads of
   // cur never race with writes, which only go to nxt.
-  T* nxt = L.B0;
-  T* rc = reinterpret_cast<T*>(dsm);
-  T* rs = rc + H;
-  T* rt = rs + H;
+  TC* nxt = L.B0;
+  TC* rc = reinterpret_cast<TC*>(dsm);
+  TC* rs = rc + H;
+  TC* rt = rs + H;
   int* rp = reinterpret_cast<int*>(rt + H);
   int* rq = rp + H;
   int sweeps = 0;
@@ -572,9 +617,9 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
       for (int k = threadIdx.x; k < H; k += blockDim.x) {
         int a, b;
         rr_pair(k, r, Np, a, b);
-        T c = 1, s = 0, t = 0;
+        TC c = 1, s = 0, t = 0;
         if (b < N) {
-          const T apq = ldg_cg(cur + static_cast<int64_t>(a) * Np + b);
+          const TC apq = ldg_cg(cur + static_cast<int64_t>(a) * Np + b);
           if (fabs(apq) > thr) {
             jacobi_rot(ldg_cg(cur + static_cast<int64_t>(a) * Np + a), ldg_cg(cur + static_cast<int64_t>(b) * Np + b), apq,
                        c, s, t);
@@ -596,17 +641,17 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
           const int k1 = static_cast<int>(task / H), k2 = static_cast<int>(task - static_cast<int64_t>(k1) * H);
           if (k1 > k2) continue;
           const int p1 = rp[k1], q1 = rq[k1], p2 = rp[k2], q2 = rq[k2];
-          const T c1 = rc[k1], s1 = rs[k1], c2 = rc[k2], s2 = rs[k2];
+          const TC c1 = rc[k1], s1 = rs[k1], c2 = rc[k2], s2 = rs[k2];
           if (k1 == k2) {
-            const T a1 = ldg_cg(cur + static_cast<int64_t>(p1) * Np + q1);
-            const T app = ldg_cg(cur + static_cast<int64_t>(p1) * Np + p1);
-            const T aqq = ldg_cg(cur + static_cast<int64_t>(q1) * Np + q1);
-            if (s1 != static_cast<T>(0)) {
-              const T t1 = rt[k1];
+            const TC a1 = ldg_cg(cur + static_cast<int64_t>(p1) * Np + q1);
+            const TC app = ldg_cg(cur + static_cast<int64_t>(p1) * Np + p1);
+            const TC aqq = ldg_cg(cur + static_cast<int64_t>(q1) * Np + q1);
+            if (s1 != static_cast<TC>(0)) {
+              const TC t1 = rt[k1];
               nxt[static_cast<int64_t>(p1) * Np + p1] = app - t1 * a1;
               nxt[static_cast<int64_t>(q1) * Np + q1] = aqq + t1 * a1;
-              nxt[static_cast<int64_t>(p1) * Np + q1] = static_cast<T>(0);
-              nxt[static_cast<int64_t>(q1) * Np + p1] = static_cast<T>(0);
+              nxt[static_cast<int64_t>(p1) * Np + q1] = static_cast<TC>(0);
+              nxt[static_cast<int64_t>(q1) * Np + p1] = static_cast<TC>(0);
             } else {
               nxt[static_cast<int64_t>(p1) * Np + p1] = app;
               nxt[static_cast<int64_t>(q1) * Np + q1] = aqq;
@@ -615,14 +660,14 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
             }
             continue;
           }
-          const T x11 = ldg_cg(cur + static_cast<int64_t>(p1) * Np + p2);
-          const T x12 = ldg_cg(cur + static_cast<int64_t>(p1) * Np + q2);
-          const T x21 = ldg_cg(cur + static_cast<int64_t>(q1) * Np + p2);
-          const T x22 = ldg_cg(cur + static_cast<int64_t>(q1) * Np + q2);
-          const T y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
-          const T y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
-          const T z11 = c2 * y11 - s2 * y12, z12 = s2 * y11 + c2 * y12;
-          const T z21 = c2 * y21 - s2 * y22, z22 = s2 * y21 + c2 * y22;
+          const TC x11 = ldg_cg(cur + static_cast<int64_t>(p1) * Np + p2);
+          const TC x12 = ldg_cg(cur + static_cast<int64_t>(p1) * Np + q2);
+          const TC x21 = ldg_cg(cur + static_cast<int64_t>(q1) * Np + p2);
+          const TC x22 = ldg_cg(cur + static_cast<int64_t>(q1) * Np + q2);
+          const TC y11 = c1 * x11 - s1 * x21, y12 = c1 * x12 - s1 * x22;
+          const TC y21 = s1 * x11 + c1 * x21, y22 = s1 * x12 + c1 * x22;
+          const TC z11 = c2 * y11 - s2 * y12, z12 = s2 * y11 + c2 * y12;
+          const TC z21 = c2 * y21 - s2 * y22, z22 = s2 * y21 + c2 * y22;
           nxt[static_cast<int64_t>(p1) * Np + p2] = z11;
           nxt[static_cast<int64_t>(p1) * Np + q2] = z12;
           nxt[static_cast<int64_t>(q1) * Np + p2] = z21;
@@ -634,18 +679,18 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
         } else {
           const int64_t t2i = task - nblk;
           const int row = static_cast<int>(t2i / H), k = static_cast<int>(t2i - static_cast<int64_t>(row) * H);
-          const T s = rs[k];
-          if (s == static_cast<T>(0)) continue;
-          const T c = rc[k];
+          const TC s = rs[k];
+          if (s == static_cast<TC>(0)) continue;
+          const TC c = rc[k];
           const int pp = rp[k], qq = rq[k];
-          T* vr = V + static_cast<int64_t>(row) * Np;
-          const T vp = ldg_cg(vr + pp), vq = ldg_cg(vr + qq);
+          TC* vr = V + static_cast<int64_t>(row) * Np;
+          const TC vp = ldg_cg(vr + pp), vq = ldg_cg(vr + qq);
           vr[pp] = c * vp - s * vq;
           vr[qq] = s * vp + c * vq;
         }
       }
       if (!grid_barrier(L.bar, (++gen) * G, err)) return;
-      T* tmp = cur;
+      TC* tmp = cur;
       cur = nxt;
       nxt = tmp;
     }
@@ -659,14 +704,14 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
     if (ti < tj) continue;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int i = ti * 16 + ty, j = tj * 16 + tx;
-    T acc = 0;
+    TC acc = 0;
     for (int k0 = 0; k0 < N; k0 += 16) {
       const int gk = k0 + tx;
       const int ri = ti * 16 + ty, rj = tj * 16 + ty;
-      T lk = 0;
-      if (gk < N) lk = fmax(ldg_cg(cur + static_cast<int64_t>(gk) * Np + gk), static_cast<T>(0));
-      sA[ty * 17 + tx] = (ri < N && gk < N) ? ldg_cg(V + static_cast<int64_t>(ri) * Np + gk) * lk : static_cast<T>(0);
-      sB[ty * 17 + tx] = (rj < N && gk < N) ? ldg_cg(V + static_cast<int64_t>(rj) * Np + gk) : static_cast<T>(0);
+      TC lk = 0;
+      if (gk < N) lk = fmax(ldg_cg(cur + static_cast<int64_t>(gk) * Np + gk), static_cast<TC>(0));
+      sA[ty * 17 + tx] = (ri < N && gk < N) ? ldg_cg(V + static_cast<int64_t>(ri) * Np + gk) * lk : static_cast<TC>(0);
+      sB[ty * 17 + tx] = (rj < N && gk < N) ? ldg_cg(V + static_cast<int64_t>(rj) * Np + gk) : static_cast<TC>(0);
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < 16; ++k) acc += sA[ty * 17 + k] * sB[tx * 17 + k];
@@ -675,10 +720,29 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
     if (i < N && j < N && i >= j) {
       const int64_t kk = packed_index(i, j, N);
       const T w = proj_input(p, bd, kk, i != j, s_sm);
-      const T u = (i != j) ? acc * static_cast<T>(kSqrt2) : acc;
+      const T u = (i != j) ? static_cast<T>(d(acc) * kSqrt2) : static_cast<T>(acc);
       p.ux[bd.x_off + kk] = u;
       p.vx[bd.x_off + kk] = u - w;
     }
+  }
+  if (sizeof(TC) < 8) {  // FP32 eigenvectors: V <- V (3 I - V^T V) / 2 before they are kept
+    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    for (int tile = blockIdx.x; tile < nt * nt; tile += G) {
+      const int ti = tile / nt, tj = tile - ti * nt;
+      const TC v = tile_mm(V, V, Np, ti, tj, 1, sA, sB);
+      const int i = ti * 16 + (threadIdx.x >> 4), j = tj * 16 + (threadIdx.x & 15);
+      if (i < Np && j < Np)
+        L.T1[static_cast<int64_t>(i) * Np + j] = ((i == j) ? static_cast<TC>(1.5) : static_cast<TC>(0)) - static_cast<TC>(0.5) * v;
+    }
+    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    for (int tile = blockIdx.x; tile < nt * nt; tile += G) {
+      const int ti = tile / nt, tj = tile - ti * nt;
+      const TC v = tile_mm(V, L.T1, Np, ti, tj, 0, sA, sB);
+      const int i = ti * 16 + (threadIdx.x >> 4), j = tj * 16 + (threadIdx.x & 15);
+      if (i < Np && j < Np) L.B1[static_cast<int64_t>(i) * Np + j] = v;
+    }
+    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    for (int64_t q = gt; q < static_cast<int64_t>(Np) * Np; q += gs) V[q] = __ldcg(L.B1 + q);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *L.sweeps_out = sweeps;
@@ -808,26 +872,24 @@ cudaError_t launch_affine(const DevPlan<T>& p, const LaunchShape& ls, cudaStream
 size_t psd_small_smem_bytes(int maxN, bool fp64) {
   const int Np = maxN + (maxN & 1), ld = Np + 1, H = Np / 2;
   const size_t es = fp64 ? 8 : 4;
-  return es * (2 * static_cast<size_t>(Np) * ld + 3 * H + Np) + sizeof(int) * 2 * H;
+  return es * (3 * static_cast<size_t>(Np) * ld + 3 * H + Np) + sizeof(int) * 2 * H;
 }
 
-int psd_small_max_n(bool fp64) { return fp64 ? 96 : 160; }
+int psd_small_max_n(bool fp64) { return fp64 ? 96 : 128; }
 
-template <typename T>
-cudaError_t launch_psd_small(const DevPlan<T>& p, const int32_t* ids, int count, int maxN, cudaStream_t s) {
+template <typename T, typename TC>
+cudaError_t launch_psd_small(const DevPlan<T>& p, const int32_t* ids, int count, int maxN, const SmallWarm<TC>& wm,
+                             cudaStream_t s) {
   if (count == 0) return cudaSuccess;
-  const size_t sm = psd_small_smem_bytes(maxN, sizeof(T) == 8);
-  k_psd_small<T><<<count, 256, sm, s>>>(p, ids);
+  const size_t sm = psd_small_smem_bytes(maxN, sizeof(TC) == 8);
+  k_psd_small<T, TC><<<count, 256, sm, s>>>(p, ids, wm);
   return cudaGetLastError();
 }
 
-template <typename T>
 int large_grid_size(int N) {
-  int dev = 0, sms = 0, per = 0;
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_psd_large<T>, 256, 0);
-  if (per < 1) per = 1;
   (void)N;
   return sms;  // one CTA per SM: co-resident, and fewer barrier arrivals
 }
@@ -837,21 +899,22 @@ size_t large_smem_bytes(int N, size_t es) {
   return H * (3 * es + 2 * sizeof(int));
 }
 
-template <typename T>
-cudaError_t launch_psd_large(const DevPlan<T>& p, int bid, int N, const LargeScratch<T>& ls, int grid, cudaStream_t s) {
+template <typename T, typename TC>
+cudaError_t launch_psd_large(const DevPlan<T>& p, int bid, int N, const LargeScratch<TC>& ls, int grid,
+                             cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ls.bar, 0, 2 * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = large_smem_bytes(N, sizeof(T));
+  cfg.dynamicSmemBytes = large_smem_bytes(N, sizeof(TC));
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_psd_large<T>, p, bid, ls);
+  return cudaLaunchKernelEx(&cfg, k_psd_large<T, TC>, p, bid, ls);
 }
 
 template <typename T>
@@ -862,12 +925,12 @@ cudaError_t launch_residuals(const DevPlan<T>& p, const LaunchShape& ls, cudaStr
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, typename TC>
 cudaError_t prepare_kernels(int max_small_n, int max_teff) {
   cudaError_t e = cudaSuccess;
   if (max_small_n > 0) {
-    const size_t sm = psd_small_smem_bytes(max_small_n, sizeof(T) == 8);
-    e = cudaFuncSetAttribute(k_psd_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+    const size_t sm = psd_small_smem_bytes(max_small_n, sizeof(TC) == 8);
+    e = cudaFuncSetAttribute(k_psd_small<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
     if (e != cudaSuccess) return e;
   }
   const size_t wsm = sizeof(double) * 2 * static_cast<size_t>(max_teff > 0 ? max_teff : 1);
@@ -875,16 +938,21 @@ cudaError_t prepare_kernels(int max_small_n, int max_teff) {
   return e;
 }
 
-#define SOS_INSTANTIATE(T)                                                                                \
-  template cudaError_t launch_affine<T>(const DevPlan<T>&, const LaunchShape&, cudaStream_t);             \
-  template cudaError_t launch_psd_small<T>(const DevPlan<T>&, const int32_t*, int, int, cudaStream_t);    \
-  template cudaError_t launch_psd_large<T>(const DevPlan<T>&, int, int, const LargeScratch<T>&, int,      \
-                                           cudaStream_t);                                                 \
-  template int large_grid_size<T>(int);                                                                   \
-  template cudaError_t prepare_kernels<T>(int, int);                                                      \
+#define SOS_INSTANTIATE(T)                                                                       \
+  template cudaError_t launch_affine<T>(const DevPlan<T>&, const LaunchShape&, cudaStream_t);    \
   template cudaError_t launch_residuals<T>(const DevPlan<T>&, const LaunchShape&, cudaStream_t);
+
+#define SOS_INSTANTIATE_PROJ(T, TC)                                                                          \
+  template cudaError_t launch_psd_small<T, TC>(const DevPlan<T>&, const int32_t*, int, int, const SmallWarm<TC>&, \
+                                               cudaStream_t);                                               \
+  template cudaError_t launch_psd_large<T, TC>(const DevPlan<T>&, int, int, const LargeScratch<TC>&, int,     \
+                                               cudaStream_t);                                               \
+  template cudaError_t prepare_kernels<T, TC>(int, int);
 
 SOS_INSTANTIATE(double)
 SOS_INSTANTIATE(float)
+SOS_INSTANTIATE_PROJ(double, double)
+SOS_INSTANTIATE_PROJ(double, float)
+SOS_INSTANTIATE_PROJ(float, float)
 
 }  // namespace sos

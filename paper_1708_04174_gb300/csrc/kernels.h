@@ -76,6 +76,14 @@ struct LargeScratch {
 
 constexpr int kMaxSweeps = 40;
 
+// Eigenvectors kept across iterations for the shared-memory projection.
+template <typename TC>
+struct SmallWarm {
+  TC* V = nullptr;          // per block N x N (offset BlockDesc::v_off), or nullptr: always cold
+  int32_t* count = nullptr; // per block: iterations since the last cold start (0 = cold)
+  int32_t limit = 1024;     // cold restart after this many warm iterations
+};
+
 struct LaunchShape {
   int sms = 152;
   int row_threads = 256;
@@ -84,14 +92,14 @@ struct LaunchShape {
 
 template <typename T>
 cudaError_t launch_affine(const DevPlan<T>& p, const LaunchShape& ls, cudaStream_t s);
-template <typename T>
-cudaError_t launch_psd_small(const DevPlan<T>& p, const int32_t* ids, int count, int maxN, cudaStream_t s);
-template <typename T>
-cudaError_t launch_psd_large(const DevPlan<T>& p, int bid, int N, const LargeScratch<T>& ls, int grid,
+template <typename T, typename TC>
+cudaError_t launch_psd_small(const DevPlan<T>& p, const int32_t* ids, int count, int maxN, const SmallWarm<TC>& wm,
                              cudaStream_t s);
-template <typename T>
+template <typename T, typename TC>
+cudaError_t launch_psd_large(const DevPlan<T>& p, int bid, int N, const LargeScratch<TC>& ls, int grid,
+                             cudaStream_t s);
 int large_grid_size(int N);
-template <typename T>
+template <typename T, typename TC>
 cudaError_t prepare_kernels(int max_small_n, int max_teff);
 template <typename T>
 cudaError_t launch_residuals(const DevPlan<T>& p, const LaunchShape& ls, cudaStream_t s);

@@ -40,6 +40,10 @@ struct HostPlan {
 // Builds the plan; returns SOS_OK or an SOS_ERR_* code with a message.
 int build_plan(const sos_program* progs, int32_t n_progs, HostPlan& plan, std::string& err);
 
+// Message returned by sos_last_error(NULL) (shared by every entry point
+// that has no handle).
+void set_global_error(const std::string& msg);
+
 // Graded monomials of eq. (4); returns the count.
 int64_t enumerate_monomials(int32_t n_vars, int32_t degree, int32_t* out, int64_t capacity);
 

@@ -123,7 +123,40 @@ def test_infeasibility_statuses(capi):
     assert r[1]["status"] == capi.DUAL_INFEASIBLE
 
 
-def test_fp32_form_error_vs_oracle(capi):
+@pytest.mark.parametrize("name,make", [("config0_quartic_n6", lambda: W.quartic_pop(6, 0)),
+                                       ("ball_n6_weighted", lambda: W.ball_pop(6, 1)),
+                                       ("config1_ball_n20", lambda: W.ball_pop(20, 0))])
+def test_mixed_form_objective_error_vs_oracle(capi, name, make):
+    """FP64 iterates with FP32 projections reach the 1e-4 residual, and their
+    objective is within 1e-3 relative of the FP64 oracle's (solved to 1e-7).
+    At tolerance 1e-4 the termination rule itself admits objective errors of
+    a few times 1e-4 (gap <= 1e-4 (1 + |c^T x| + |b^T y|) plus the primal and
+    dual residuals), so the bound is 1e-3."""
+    prog = make()
+    cd = conic.build(prog)
+    ro = admm.solve(cd, 1e-7, 50000, k_check=10)
+    s = capi.Solver(prog, precision=capi.PREC_MIXED, k_check=10)
+    r = s.solve(1e-4, 20000)[0]
+    s.close()
+    assert r["status"] == capi.SOLVED, r
+    err = abs(r["obj_primal"] - ro.res["pobj"]) / abs(ro.res["pobj"])
+    assert err < 1e-3, err
+
+
+def test_mixed_form_iterates_close_to_oracle(capi):
+    """After 100 iterations the FP32-projection iterates stay within the FP32
+    rounding of the projections of the FP64 oracle's iterates."""
+    prog = W.quartic_pop(6, 0)
+    uo, vo = oracle_packed(prog, 100)
+    s = capi.Solver(prog, precision=capi.PREC_MIXED)
+    s.iterate(100)
+    s.sync()
+    ug, vg = s.get_iterate()
+    s.close()
+    assert rel(ug, uo) < 1e-4 and rel(vg, vo) < 1e-4, (rel(ug, uo), rel(vg, vo))
+
+
+def test_fp32_iterate_form_error_vs_oracle(capi):
     prog = W.quartic_pop(6, 0)
     cd = conic.build(prog)
     ro = admm.solve(cd, 1e-6, 50000, k_check=10)
@@ -133,3 +166,18 @@ def test_fp32_form_error_vs_oracle(capi):
     assert r["status"] == capi.SOLVED
     err = abs(r["obj_primal"] - ro.res["pobj"]) / abs(ro.res["pobj"])
     assert err < 1e-3, err
+
+
+def test_warm_start_keeps_fp64_parity_over_many_iterations(capi):
+    """Eigenvectors kept across iterations (warm Jacobi) do not change the FP64
+    iterates beyond rounding: 400 iterations of config 0 stay within 1e-9."""
+    prog = W.quartic_pop(6, 0)
+    uo, vo = oracle_packed(prog, 400)
+    s = capi.Solver(prog, precision=capi.PREC_FP64)
+    s.iterate(400)
+    s.sync()
+    ug, vg = s.get_iterate()
+    st = s.stats()
+    s.close()
+    assert rel(ug, uo) < 1e-9 and rel(vg, vo) < 1e-9, (rel(ug, uo), rel(vg, vo))
+    assert st["max_sweeps"] <= 6, st  # warm start: a few sweeps instead of ~9
