@@ -208,6 +208,31 @@ int sos_host_plan(const sos_program* prog, int64_t dims[6], int32_t* ent_row, do
  * SOS_ERR_CUDA, SOS_ERR_TIMEOUT; the message is in sos_last_error(NULL). */
 int sos_psd_project(const double* in, double* out, int32_t N, void* stream);
 
+/* Allocation-free variant of sos_psd_project, for callers that cannot call
+ * cudaMalloc: code running while another component captures the stream into
+ * a CUDA graph, code whose device memory is owned by a pool or allocator it
+ * may not bypass, latency-critical loops that must not block on the CUDA
+ * allocator, or plugins whose host forbids device allocations after start-up.
+ * The paper has no counterpart: this is a deployment convenience.
+ *
+ * Same contract as sos_psd_project (in, out: DEVICE pointers to N(N+1)/2
+ * packed doubles, not overlapping; work on stream, returns when finished),
+ * except that the call allocates nothing: its scratch is one fixed array of
+ * about 3 MB compiled into the library, resident on every GPU that loads the
+ * library until the process exits.
+ * - N must satisfy 1 <= N <= SOS_NOALLOC_MAX_N; larger N is rejected with
+ *   SOS_ERR_INVALID_ARG and a message in sos_last_error(NULL).
+ * - The first call on each device (with that device current) looks up the
+ *   device address of the scratch array once; make that first call before
+ *   any stream capture begins.
+ * - Every call uses the same scratch array, which keeps the previous call's
+ *   contents (the call clears what must start at zero).  Calls whose work
+ *   overlaps on the GPU -- from several host threads, or on several streams --
+ *   race on that array and corrupt each other's results: serialise them.
+ * Errors: SOS_ERR_INVALID_ARG, SOS_ERR_CUDA, SOS_ERR_TIMEOUT. */
+#define SOS_NOALLOC_MAX_N 256
+int sos_psd_project_noalloc(const double* in, double* out, int32_t N, void* stream);
+
 /* Diagnostics (synchronises the handle's stream): out[0] = iterations run
  * since setup, out[1] = number of Gram blocks, out[2] = largest number of
  * Jacobi sweeps any block needed in the last projection, out[3] = total

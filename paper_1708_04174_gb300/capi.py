@@ -70,6 +70,7 @@ EXPORTS = {
     "sos_launches_per_iteration": (C.c_int, [C.c_void_p]),
     "sos_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "sos_psd_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sos_psd_project_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sos_run_stage": (C.c_int, [C.c_void_p, C.c_int32]),
 }
 
@@ -175,6 +176,15 @@ class _Marshalled:
 def psd_project(in_ptr: int, out_ptr: int, N: int, stream: int = 0):
     """PSD projection of one packed symmetric matrix; device pointers."""
     _check(lib().sos_psd_project(C.c_void_p(in_ptr), C.c_void_p(out_ptr), N, C.c_void_p(stream) if stream else None))
+
+
+NOALLOC_MAX_N = 256
+
+
+def psd_project_noalloc(in_ptr: int, out_ptr: int, N: int, stream: int = 0):
+    """sos_psd_project without any device allocation (fixed library scratch)."""
+    _check(lib().sos_psd_project_noalloc(C.c_void_p(in_ptr), C.c_void_p(out_ptr), N,
+                                         C.c_void_p(stream) if stream else None))
 
 
 def host_plan(prog):
