@@ -34,14 +34,31 @@ class Block:
     weight: Optional[Poly] = None
 
 
-@dataclass
 class Constraint:
-    """One polynomial identity of eq. (7)."""
+    """One polynomial identity of eq. (7).
 
-    degree: int  # rows: all monomials of degree <= degree
-    g0: Poly
-    g: List[Poly]  # t polynomials, one per decision variable
-    blocks: List[Block]
+    ``g`` lists the t polynomials g_1..g_t as sparse dicts.  A generator may
+    instead give them as flat term arrays ``term_arrays = (t, index, exps,
+    coef)`` (term k adds coef[k] x^exps[k] to g_{index[k]+1}); the dict view
+    is then built on first access."""
+
+    def __init__(self, degree: int, g0: Poly, g: Optional[List[Poly]] = None, blocks: Optional[List[Block]] = None,
+                 term_arrays=None):
+        self.degree = degree  # rows: all monomials of degree <= degree
+        self.g0 = g0
+        self._g = g
+        self.blocks = list(blocks or [])
+        self.term_arrays = term_arrays
+
+    @property
+    def g(self) -> List[Poly]:
+        if self._g is None:
+            t, idx, exps, coef = self.term_arrays
+            out: List[Poly] = [dict() for _ in range(t)]
+            for i, e, c in zip(idx.tolist(), map(tuple, exps.tolist()), coef.tolist()):
+                out[i][e] = out[i].get(e, 0.0) + c
+            self._g = out
+        return self._g
 
 
 @dataclass

@@ -215,24 +215,51 @@ def lyapunov_cubic(n: int, seed: int, eps: float = 1e-3, sigma: float = 0.1) -> 
     feasibility (w = 0) of
 
         V - eps |x|^2 SOS (degree 4, basis degree 2),
-        -grad V . f - eps |x|^2 SOS (degree 6, basis degree 3)."""
+        -grad V . f - eps |x|^2 SOS (degree 6, basis degree 3).
+
+    The g polynomials of the second identity, grad m_i . f, are built with
+    array arithmetic (exponents packed base 16) and handed over as term
+    arrays."""
     rng = np.random.default_rng(seed)
-    cubic = _support(n, 3, 3)
-    fx: List[Poly] = []
-    for r in range(n):
-        comp = {e: float(sigma * rng.standard_normal()) for e in cubic}
-        comp[_unit(n, r)] = comp.get(_unit(n, r), 0.0) - 1.0
-        fx.append(comp)
+    cubic = np.array(_support(n, 3, 3), dtype=np.int64)
+    fcoef = np.stack([sigma * rng.standard_normal(len(cubic)) for _ in range(n)])  # [n, K]
     vmons = _support(n, 4, 2)
+    V = np.array(vmons, dtype=np.int64)  # [t, n]
+    t = len(vmons)
+    base = 16 ** np.arange(n, dtype=np.int64)
+    # f_r terms: cubic monomials plus -x_r
+    idx_l, key_l, coef_l = [], [], []
+    eye = np.eye(n, dtype=np.int64)
+    for r in range(n):
+        a_r = V[:, r]  # d m_i / d x_r = a_r x^(a - e_r)
+        sel = np.nonzero(a_r > 0)[0]
+        if len(sel) == 0:
+            continue
+        dexp = V[sel] - eye[r]  # [s, n]
+        fe = np.concatenate([cubic, eye[r:r + 1]])  # [K+1, n]
+        fc = np.concatenate([fcoef[r], [-1.0]])
+        ex = dexp[:, None, :] + fe[None, :, :]  # [s, K+1, n]
+        co = a_r[sel][:, None] * fc[None, :]
+        idx_l.append(np.repeat(sel, fe.shape[0]))
+        key_l.append((ex.reshape(-1, n) * base).sum(axis=1))
+        coef_l.append(co.reshape(-1))
+    idx = np.concatenate(idx_l)
+    key = np.concatenate(key_l)
+    coef = np.concatenate(coef_l)
+    comb = idx * (16 ** n) + key
+    uniq, inv = np.unique(comb, return_inverse=True)
+    csum = np.bincount(inv, weights=coef)
+    keep = csum != 0.0
+    uniq, csum = uniq[keep], csum[keep]
+    gi = uniq // (16 ** n)
+    gk = uniq % (16 ** n)
+    gexp = (gk[:, None] // base[None, :]) % 16
     c1 = Constraint(degree=4, g0=sq_norm(n, -eps), g=[{m: -1.0} for m in vmons], blocks=[Block(2)])
-    g2 = []
-    for m in vmons:
-        gi: Poly = {}
-        for r in range(n):
-            gi = padd(gi, pmul(pdiff({m: 1.0}, r), fx[r]))
-        g2.append(gi)
-    c2 = Constraint(degree=6, g0=sq_norm(n, -eps), g=g2, blocks=[Block(3)])
-    return SOSProgram(n=n, w=np.zeros(len(vmons)), constraints=[c1, c2],
+    c2 = Constraint(degree=6, g0=sq_norm(n, -eps), blocks=[Block(3)],
+                    term_arrays=(t, gi.astype(np.int64), gexp.astype(np.int32), csum))
+    fx = [dict(zip(map(tuple, np.concatenate([cubic, eye[r:r + 1]]).tolist()),
+                   np.concatenate([fcoef[r], [-1.0]]).tolist())) for r in range(n)]
+    return SOSProgram(n=n, w=np.zeros(t), constraints=[c1, c2],
                       name=f"lyapunov_cubic(n={n},seed={seed})", meta={"f": fx})
 
 

@@ -130,16 +130,25 @@ class _Marshalled:
             cons = (sos_constraint * len(pg.constraints))()
             for ci, con in enumerate(pg.constraints):
                 rows = mono(n, con.degree)
-                polys = [con.g0] + list(con.g)
                 tp, te, tc = [], [], []
+                arrays = getattr(con, "term_arrays", None)
+                polys = [con.g0] + ([] if arrays is not None else list(con.g))
                 for k, poly in enumerate(polys):
                     for e, cval in poly.items():
                         tp.append(k)
                         te.append(e)
                         tc.append(cval)
-                tp = np.ascontiguousarray(tp, dtype=np.int32)
-                te = np.ascontiguousarray(np.array(te, dtype=np.int32).reshape(-1, n))
-                tc = np.ascontiguousarray(tc, dtype=np.float64)
+                tp = np.array(tp, dtype=np.int32)
+                te = np.array(te, dtype=np.int32).reshape(-1, n)
+                tc = np.array(tc, dtype=np.float64)
+                if arrays is not None:  # g_1..g_t given as flat term arrays
+                    _, idx, exps, coef = arrays
+                    tp = np.concatenate([tp, np.asarray(idx, dtype=np.int32) + 1])
+                    te = np.concatenate([te, np.asarray(exps, dtype=np.int32).reshape(-1, n)])
+                    tc = np.concatenate([tc, np.asarray(coef, dtype=np.float64)])
+                tp = np.ascontiguousarray(tp)
+                te = np.ascontiguousarray(te)
+                tc = np.ascontiguousarray(tc)
                 blks = (sos_block * len(con.blocks))()
                 for bi, blk in enumerate(con.blocks):
                     bas = mono(n, blk.basis_degree)
