@@ -102,11 +102,24 @@ typedef struct {
   const sos_constraint* constraints; /* [n_constraints] */
 } sos_program;
 
+/* solve_mode: how iterations are launched.
+ *   0 auto: the persistent launch for a batch (n_progs > 1) whose Gram
+ *     blocks are all small (N <= 96 FP64 projections, <= 128 FP32), else
+ *     one CUDA graph of per-phase kernels per iteration;
+ *   1 one CUDA graph of per-phase kernels per iteration (any block size);
+ *   2 the persistent launch (error SOS_ERR_UNSUPPORTED with a large block).
+ * The persistent launch runs all iterations of a solve in one cooperative
+ * kernel; residual checks and termination happen on the device.  At setup an
+ * autotuner times a few iterations of every candidate -- persistent grids of
+ * 1..4 CTAs per SM with a round-robin or a work-queue block schedule and, in
+ * auto mode, the per-phase graph -- keeps the fastest, and resets the iterate
+ * to the cold start. */
 typedef struct {
   int32_t precision;      /* SOS_PREC_* */
   int32_t k_check;        /* residual check period in iterations (>= 1) */
   void* cuda_stream;      /* cudaStream_t to issue work on, or NULL */
-  int32_t reserved[8];    /* must be zero */
+  int32_t solve_mode;     /* 0, 1 or 2 as above */
+  int32_t reserved[7];    /* must be zero */
 } sos_options;
 
 /* Per-instance solve report.  x, y, s are optional caller-allocated HOST
@@ -238,6 +251,13 @@ int sos_psd_project_noalloc(const double* in, double* out, int32_t N, void* stre
  * Jacobi sweeps any block needed in the last projection, out[3] = total
  * sweeps over all blocks in the last projection. */
 int sos_stats(sos_handle* h, int64_t out[4]);
+
+/* Launch configuration chosen for the handle: out[0] = 1 for the persistent
+ * launch (0: per-phase kernels), out[1] = its grid size (CTAs), out[2] = 1
+ * for the work-queue block schedule (0: round-robin, largest block first),
+ * out[3] = candidates timed by the autotuner, out[4] = microseconds per
+ * iteration of the chosen candidate during tuning. */
+int sos_tuning(const sos_handle* h, int32_t out[5]);
 
 /* Number of CUDA kernels one ADMM iteration launches for this handle. */
 int sos_launches_per_iteration(const sos_handle* h);

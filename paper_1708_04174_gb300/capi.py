@@ -45,7 +45,7 @@ class sos_program(C.Structure):
 
 class sos_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("k_check", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("reserved", C.c_int32 * 8)]
+                ("solve_mode", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
 class sos_result(C.Structure):
@@ -68,6 +68,7 @@ EXPORTS = {
     "sos_host_plan": (C.c_int, [C.POINTER(sos_program), C.POINTER(C.c_int64), _i32p, _f64p, _f64p, _f64p]),
     "sos_stream": (C.c_void_p, [C.c_void_p]),
     "sos_launches_per_iteration": (C.c_int, [C.c_void_p]),
+    "sos_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "sos_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "sos_psd_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sos_psd_project_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
@@ -214,7 +215,7 @@ def host_plan(prog):
 class Solver:
     """One libsos handle over a batch of SOS programs (instances)."""
 
-    def __init__(self, progs, precision: int = PREC_FP64, k_check: int = 10, stream=None):
+    def __init__(self, progs, precision: int = PREC_FP64, k_check: int = 10, stream=None, solve_mode: int = 0):
         if not isinstance(progs, (list, tuple)):
             progs = [progs]
         self.n_inst = len(progs)
@@ -223,6 +224,7 @@ class Solver:
         opts.precision = precision
         opts.k_check = k_check
         opts.cuda_stream = C.c_void_p(stream) if stream else None
+        opts.solve_mode = solve_mode
         h = C.c_void_p()
         _check(lib().sos_setup(m.progs, len(progs), C.byref(opts), C.byref(h)))
         self.h = h
@@ -260,6 +262,12 @@ class Solver:
         out = (C.c_int64 * 4)()
         _check(lib().sos_stats(self.h, out), self.h)
         return {"iterations": out[0], "blocks": out[1], "max_sweeps": out[2], "total_sweeps": out[3]}
+
+    def tuning(self) -> dict:
+        out = (C.c_int32 * 5)()
+        _check(lib().sos_tuning(self.h, out), self.h)
+        return {"persistent": out[0], "grid": out[1], "dynamic": out[2], "candidates": out[3],
+                "us_per_iter": out[4]}
 
     def launches_per_iteration(self) -> int:
         return int(lib().sos_launches_per_iteration(self.h))

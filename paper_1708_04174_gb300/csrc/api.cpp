@@ -61,6 +61,15 @@ struct sos_handle {
   std::vector<int32_t> iters_h, status_h;
   int64_t iter_count = 0;
   int32_t* blk_sweeps = nullptr;  // device
+  // persistent batched path
+  bool persistent = false;
+  int32_t solve_mode = 0;
+  int32_t p_grid = 0, p_dynamic = 0, p_tried = 0, p_max_small = 0, p_max_teff = 0;
+  float p_best_ms = 0.f;
+  uint32_t *p_bar = nullptr, *p_queue = nullptr;
+  int32_t *p_nactive = nullptr, *p_iters = nullptr, *p_sched = nullptr;
+  int32_t p_nsched = 0;
+  InstReport* p_rep = nullptr;
   cudaGraphExec_t graph = nullptr;
   bool graph_tried = false;
   std::string err;
@@ -267,6 +276,102 @@ int cold_start(sos_handle* h) {
   return SOS_OK;
 }
 
+template <typename T, typename TC>
+PersistArgs<TC> persist_args(sos_handle* h, const SmallWarm<TC>& wm, int32_t max_iter, int32_t k_check, double tol) {
+  PersistArgs<TC> a;
+  a.max_iter = max_iter;
+  a.k_check = k_check;
+  a.tol = tol;
+  a.bar = h->p_bar;
+  a.queue = h->p_queue;
+  a.active = h->active;
+  a.n_active = h->p_nactive;
+  a.rep = h->p_rep;
+  a.sched = h->p_sched;
+  a.n_sched = h->p_nsched;
+  a.dynamic = h->p_dynamic;
+  a.wm = wm;
+  a.iters_done = h->p_iters;
+  return a;
+}
+
+cudaError_t launch_persist(sos_handle* h, int32_t max_iter, int32_t k_check, double tol) {
+  if (h->precision == SOS_PREC_FP64)
+    return launch_persistent<double, double>(h->d64, persist_args<double, double>(h, h->warm64, max_iter, k_check, tol),
+                                             h->p_grid, h->p_max_small, h->p_max_teff, h->stream);
+  if (h->precision == SOS_PREC_MIXED)
+    return launch_persistent<double, float>(h->d64, persist_args<double, float>(h, h->warm32, max_iter, k_check, tol),
+                                            h->p_grid, h->p_max_small, h->p_max_teff, h->stream);
+  return launch_persistent<float, float>(h->d32, persist_args<float, float>(h, h->warm32, max_iter, k_check, tol),
+                                         h->p_grid, h->p_max_small, h->p_max_teff, h->stream);
+}
+
+int max_ctas_per_sm(sos_handle* h) {
+  if (h->precision == SOS_PREC_FP64) return persistent_max_ctas_per_sm<double, double>(h->p_max_small, h->p_max_teff);
+  if (h->precision == SOS_PREC_MIXED) return persistent_max_ctas_per_sm<double, float>(h->p_max_small, h->p_max_teff);
+  return persistent_max_ctas_per_sm<float, float>(h->p_max_small, h->p_max_teff);
+}
+
+int cold_start(sos_handle* h);
+}  // namespace
+extern "C" int sos_iterate(sos_handle* h, int32_t iters);
+namespace {
+
+// Autotuner of the persistent launch: times a few iterations for every
+// (CTAs per SM, schedule) candidate from the cold start, keeps the fastest,
+// and returns the iterate to the cold start.
+int autotune_persistent(sos_handle* h) {
+  const int occ = max_ctas_per_sm(h);
+  if (occ < 1) return set_err(h, SOS_ERR_CUDA, "persistent kernel cannot be resident");
+  const int max_per = occ < 4 ? occ : 4;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_grid = h->shape.sms, best_dyn = 0, tried = 0;
+  const int32_t reps = 3;
+  for (int per = 1; per <= max_per; ++per)
+    for (int dyn = 0; dyn <= 1; ++dyn) {
+      h->p_grid = h->shape.sms * per;
+      h->p_dynamic = dyn;
+      CK(launch_persist(h, 1, 0, 0.0));  // warm-up of this shape
+      CK(cudaEventRecord(e0, h->stream));
+      CK(launch_persist(h, reps, 0, 0.0));
+      CK(cudaEventRecord(e1, h->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      ++tried;
+      if (ms < best) {
+        best = ms;
+        best_grid = h->p_grid;
+        best_dyn = dyn;
+      }
+    }
+  // the per-phase kernel path (one CUDA graph per iteration) is a candidate too
+  float graph_ms = 1e30f;
+  if (h->solve_mode == 0) {
+    h->persistent = false;
+    int rc = sos_iterate(h, 1);  // builds the graph
+    if (rc != SOS_OK) return rc;
+    CK(cudaEventRecord(e0, h->stream));
+    rc = sos_iterate(h, reps);
+    if (rc != SOS_OK) return rc;
+    CK(cudaEventRecord(e1, h->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(&graph_ms, e0, e1));
+    ++tried;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->persistent = !(graph_ms < best);
+  h->p_grid = best_grid;
+  h->p_dynamic = best_dyn;
+  h->p_tried = tried;
+  h->p_best_ms = (h->persistent ? best : graph_ms) / reps;
+  return cold_start(h);
+}
+
 int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   HostPlan P;
   std::string err;
@@ -411,10 +516,34 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
     TRY(make_large(h, h->large32, large));
     CK((prepare_kernels<float, float>(max_small, max_teff)));
   }
-  h->d64.tau = c.tau;
+  h->d64.tau = c.tau;  // FP64 scalars shared by every form
   h->d64.kappa = c.kappa;
   h->d64.err = c.err;
   h->d64.resid = c.resid;
+  // persistent batched path: every block small, and either requested or a batch
+  const bool eligible = large.empty();
+  h->persistent = eligible && (h->solve_mode == 2 || (h->solve_mode == 0 && n_progs > 1));
+  // (auto mode keeps the persistent launch only if the autotuner finds it faster)
+  if (h->solve_mode == 2 && !eligible)
+    return set_err(h, SOS_ERR_UNSUPPORTED, "the persistent solver needs every Gram block to be small");
+  if (h->persistent) {
+    std::vector<int32_t> order;
+    for (int k = 5; k >= 0; --k)
+      for (int32_t b : cls[k]) order.push_back(b);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return P.blocks[x].N > P.blocks[y].N; });
+    h->p_nsched = static_cast<int32_t>(order.size());
+    TRY(upload(h, order, &h->p_sched));
+    TRY(alloc(h, 2, &h->p_bar));
+    TRY(alloc(h, 1, &h->p_queue));
+    TRY(alloc(h, 1, &h->p_nactive));
+    TRY(alloc(h, 1, &h->p_iters));
+    TRY(alloc(h, h->n_inst, &h->p_rep));
+    h->p_max_small = max_small;
+    h->p_max_teff = max_teff;
+    TRY(cold_start(h));
+    return autotune_persistent(h);
+  }
   return cold_start(h);
 }
 
@@ -492,6 +621,11 @@ int sos_setup(const sos_program* progs, int32_t n_progs, const sos_options* opts
     h->precision = opts->precision;
     h->k_check = opts->k_check > 0 ? opts->k_check : 10;
     h->stream = static_cast<cudaStream_t>(opts->cuda_stream);
+    h->solve_mode = opts->solve_mode;
+    if (h->solve_mode < 0 || h->solve_mode > 2) {
+      g_setup_error = "unknown solve_mode";
+      return SOS_ERR_INVALID_ARG;
+    }
   }
   if (!h->stream) {
     cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
@@ -542,6 +676,18 @@ int sos_dims(const sos_handle* h, int32_t inst, int64_t dims[6]) {
 
 int sos_iterate(sos_handle* h, int32_t iters) {
   if (!h || iters < 0) return SOS_ERR_INVALID_ARG;
+  if (h->persistent) {
+    if (iters == 0) return SOS_OK;
+    int32_t na = 0;
+    for (int i = 0; i < h->n_inst; ++i) na += h->active_h[i];
+    CK(cudaMemcpyAsync(h->p_nactive, &na, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    CK(launch_persist(h, iters, 0, 0.0));
+    h->iter_count += iters;
+    for (int i = 0; i < h->n_inst; ++i)
+      if (h->active_h[i]) h->iters_h[i] += iters;
+    CK(cudaStreamSynchronize(h->stream));  // na lives on this stack frame
+    return SOS_OK;
+  }
   if (!h->graph_tried) {
     h->graph_tried = true;
     cudaGraph_t g = nullptr;
@@ -579,6 +725,36 @@ int sos_solve(sos_handle* h, double tol, int32_t max_iter, sos_result* results) 
   int32_t done = 0;
   for (int i = 0; i < h->n_inst; ++i) done += h->active_h[i] ? 0 : 1;
   int32_t it = 0;
+  if (h->persistent && done < h->n_inst && max_iter > 0) {
+    int32_t na = h->n_inst - done;
+    CK(cudaMemcpyAsync(h->p_nactive, &na, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    CK(launch_persist(h, max_iter, h->k_check, tol));
+    std::vector<InstReport> rp_h(h->n_inst);
+    std::vector<int32_t> act(h->n_inst);
+    int32_t ran = 0;
+    CK(cudaMemcpyAsync(rp_h.data(), h->p_rep, sizeof(InstReport) * h->n_inst, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(act.data(), h->active, sizeof(int32_t) * h->n_inst, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&ran, h->p_iters, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    int rc = check_err_word(h);
+    if (rc != SOS_OK) return rc;
+    h->iter_count += ran;
+    for (int i = 0; i < h->n_inst; ++i) {
+      if (!h->active_h[i]) continue;
+      if (!act[i]) {
+        h->status_h[i] = rp_h[i].status;
+        h->iters_h[i] += rp_h[i].iters;
+        h->active_h[i] = 0;
+      } else {
+        h->iters_h[i] += ran;
+      }
+      rp[i] = rp_h[i].rp;
+      rd[i] = rp_h[i].rd;
+      gp[i] = rp_h[i].gap;
+      po[i] = rp_h[i].pobj;
+      dobj[i] = rp_h[i].dobj;
+    }
+    it = max_iter;
+  }
   while (it < max_iter && done < h->n_inst) {
     const int32_t k = std::min(h->k_check, max_iter - it);
     int rc = sos_iterate(h, k);
@@ -813,8 +989,19 @@ int sos_stats(sos_handle* h, int64_t out[4]) {
   return SOS_OK;
 }
 
+int sos_tuning(const sos_handle* h, int32_t out[5]) {
+  if (!h || !out) return SOS_ERR_INVALID_ARG;
+  out[0] = h->persistent ? 1 : 0;
+  out[1] = h->p_grid;
+  out[2] = h->p_dynamic;
+  out[3] = h->p_tried;
+  out[4] = static_cast<int32_t>(h->p_best_ms * 1000.f);
+  return SOS_OK;
+}
+
 int sos_launches_per_iteration(const sos_handle* h) {
   if (!h) return SOS_ERR_INVALID_ARG;
+  if (h->persistent) return 0;  // one launch for all iterations of a call
   const int affine = h->TL > 0 ? 6 : 4;
   return affine + static_cast<int>(h->small.size()) + static_cast<int>(h->large64.size() + h->large32.size());
 }

@@ -59,9 +59,8 @@ __device__ __forceinline__ double d(T x) {
 // ---------------------------------------------------------------------------
 
 template <typename T>
-__global__ void k_rows_r(DevPlan<T> p) {
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t a = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; a < p.M; a += stride) {
+__device__ void d_rows_r(const DevPlan<T>& p, int64_t g0, int64_t stride) {
+  for (int64_t a = g0; a < p.M; a += stride) {
     const int i = p.row_inst[a];
     if (!p.active[i]) continue;
     const double om3 = p.tau[i] + p.kappa[i];
@@ -84,10 +83,13 @@ __global__ void k_rows_r(DevPlan<T> p) {
 }
 
 template <typename T>
-__global__ void k_lr_y(DevPlan<T> p) {
+__global__ void k_rows_r(DevPlan<T> p) {
+  d_rows_r(p, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, static_cast<int64_t>(gridDim.x) * blockDim.x);
+}
+
+template <typename T>
+__device__ void d_lr_y(const DevPlan<T>& p, int warp, int nwarps) {
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int j = warp; j < p.TL; j += nwarps) {
     if (!p.active[p.lr_inst[j]]) continue;
     double acc = 0.0;
@@ -98,11 +100,14 @@ __global__ void k_lr_y(DevPlan<T> p) {
   }
 }
 
+template <typename T>
+__global__ void k_lr_y(DevPlan<T> p) {
+  d_lr_y(p, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
+}
+
 // z = L^{-T} L^{-1} y per instance (one CTA per instance).
 template <typename T>
-__global__ void k_woodbury(DevPlan<T> p) {
-  extern __shared__ double sh[];
-  const int i = blockIdx.x;
+__device__ void d_woodbury(const DevPlan<T>& p, int i, double* sh) {
   if (!p.active[i]) return;
   const InstInfo in = p.inst[i];
   const int te = in.t_eff;
@@ -130,9 +135,14 @@ __global__ void k_woodbury(DevPlan<T> p) {
 }
 
 template <typename T>
-__global__ void k_rows_sigma2(DevPlan<T> p) {
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t a = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; a < p.M; a += stride) {
+__global__ void k_woodbury(DevPlan<T> p) {
+  extern __shared__ double shw[];
+  d_woodbury(p, blockIdx.x, shw);
+}
+
+template <typename T>
+__device__ void d_rows_sigma2(const DevPlan<T>& p, int64_t g0, int64_t stride) {
+  for (int64_t a = g0; a < p.M; a += stride) {
     if (!p.active[p.row_inst[a]]) continue;
     double acc = 0.0;
     const int l1 = p.lrr_ptr[a + 1];
@@ -141,12 +151,16 @@ __global__ void k_rows_sigma2(DevPlan<T> p) {
   }
 }
 
+template <typename T>
+__global__ void k_rows_sigma2(DevPlan<T> p) {
+  d_rows_sigma2(p, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, static_cast<int64_t>(gridDim.x) * blockDim.x);
+}
+
 // Per instance: b^T sigma_2, c^T sigma_1, Sherman-Morrison coefficient,
 // u_hat_3, the tau/kappa update and the free variables.
 template <typename T>
-__global__ void k_inst_scalar(DevPlan<T> p) {
+__device__ void d_inst_scalar(const DevPlan<T>& p, int i) {
   __shared__ double sh[40];
-  const int i = blockIdx.x;
   if (!p.active[i]) return;
   const InstInfo in = p.inst[i];
   const double tau = p.tau[i], kappa = p.kappa[i];
@@ -184,9 +198,13 @@ __global__ void k_inst_scalar(DevPlan<T> p) {
 }
 
 template <typename T>
-__global__ void k_rows_y(DevPlan<T> p) {
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t a = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; a < p.M; a += stride) {
+__global__ void k_inst_scalar(DevPlan<T> p) {
+  d_inst_scalar(p, blockIdx.x);
+}
+
+template <typename T>
+__device__ void d_rows_y(const DevPlan<T>& p, int64_t g0, int64_t stride) {
+  for (int64_t a = g0; a < p.M; a += stride) {
     const int i = p.row_inst[a];
     if (!p.active[i]) continue;
     const double uh2 = p.sig2[a] - p.st[i].s * p.h2[a];
@@ -196,6 +214,11 @@ __global__ void k_rows_y(DevPlan<T> p) {
     p.vy[a] = static_cast<T>((vy - uh2) + un);
     p.uh2[a] = static_cast<T>(uh2);
   }
+}
+
+template <typename T>
+__global__ void k_rows_y(DevPlan<T> p) {
+  d_rows_y(p, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, static_cast<int64_t>(gridDim.x) * blockDim.x);
 }
 
 // Input of the PSD projection for packed entry e of block bd:
@@ -276,11 +299,9 @@ __device__ __forceinline__ void jacobi_rot(T app, T aqq, T apq, T& c, T& s, T& t
 // iterations, so few sweeps remain.
 // ---------------------------------------------------------------------------
 template <typename T, typename TC>
-__global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* ids, SmallWarm<TC> wm) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+__device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& wm, unsigned char* smraw) {
   __shared__ double red[40];
   __shared__ int last_rot;  // index of the last round that had a rotation
-  const int bid = ids[blockIdx.x];
   const BlockDesc bd = p.blocks[bid];
   if (!p.active[bd.inst]) return;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -442,6 +463,12 @@ __global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* 
     }
     if (tid == 0) wm.count[bid] = warm ? wc + 1 : 1;
   }
+}
+
+template <typename T, typename TC>
+__global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* ids, SmallWarm<TC> wm) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  d_psd_small(p, ids[blockIdx.x], wm, smraw);
 }
 
 // ---------------------------------------------------------------------------
@@ -755,9 +782,8 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
 // residuals (every k_check iterations)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_res_rows(DevPlan<T> p) {
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t a = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; a < p.M; a += stride) {
+__device__ void d_res_rows(const DevPlan<T>& p, int64_t g0, int64_t stride) {
+  for (int64_t a = g0; a < p.M; a += stride) {
     if (!p.active[p.row_inst[a]]) continue;
     double acc = 0.0;
     const int k1 = p.row_ptr[a + 1];
@@ -773,10 +799,13 @@ __global__ void k_res_rows(DevPlan<T> p) {
 }
 
 template <typename T>
-__global__ void k_res_lr(DevPlan<T> p) {
+__global__ void k_res_rows(DevPlan<T> p) {
+  d_res_rows(p, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, static_cast<int64_t>(gridDim.x) * blockDim.x);
+}
+
+template <typename T>
+__device__ void d_res_lr(const DevPlan<T>& p, int warp, int nwarps) {
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int j = warp; j < p.TL; j += nwarps) {
     if (!p.active[p.lr_inst[j]]) continue;
     double acc = 0.0;
@@ -788,9 +817,13 @@ __global__ void k_res_lr(DevPlan<T> p) {
 }
 
 template <typename T>
-__global__ void k_res_inst(DevPlan<T> p) {
+__global__ void k_res_lr(DevPlan<T> p) {
+  d_res_lr(p, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
+}
+
+template <typename T>
+__device__ void d_res_inst(const DevPlan<T>& p, int i) {
   __shared__ double sh[40];
-  const int i = blockIdx.x;
   if (!p.active[i]) return;
   const InstInfo in = p.inst[i];
   const double tau = p.tau[i];
@@ -842,6 +875,113 @@ __global__ void k_res_inst(DevPlan<T> p) {
     R.nonfinite = sbad;
     p.resid[i] = R;
   }
+}
+
+template <typename T>
+__global__ void k_res_inst(DevPlan<T> p) {
+  d_res_inst(p, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batched solver: one cooperative launch runs many iterations of
+// every instance.  The phases of an iteration are the device functions used
+// by the per-kernel path, separated by grid barriers.  Every k_check
+// iterations the residuals are reduced and each instance is checked on the
+// device (same rule as sos_solve); a finished instance is frozen and the
+// launch ends when none is running.  Gram blocks are handed to CTAs either
+// round-robin over a fixed order (largest first) or from an atomic work queue.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void d_check(const DevPlan<T>& p, int i, int it, double tol, InstReport* rep, int32_t* active,
+                        int32_t* n_active) {
+  if (threadIdx.x != 0 || !active[i]) return;
+  const InstInfo in = p.inst[i];
+  const InstResid r = p.resid[i];
+  InstReport R;
+  R.rp = R.rd = R.gap = R.pobj = R.dobj = nan("");
+  double res = INFINITY;
+  if (r.tau > 1e-12 * (r.kappa + 1.0)) {
+    R.rp = sqrt(r.pr2) / r.tau / (1.0 + in.norm_b);
+    R.rd = sqrt(r.dr2) / r.tau / (1.0 + in.norm_c);
+    R.pobj = r.cx / r.tau;
+    R.dobj = r.by / r.tau;
+    R.gap = fabs(R.pobj - R.dobj) / (1.0 + fabs(R.pobj) + fabs(R.dobj));
+    res = fmax(R.rp, fmax(R.rd, R.gap));
+  }
+  const double pinf = r.by > 0 ? sqrt(r.aty2) / r.by : INFINITY;
+  const double dinf = r.cx < 0 ? sqrt(r.ax2) / (-r.cx) : INFINITY;
+  int st = 0;
+  if (r.nonfinite > 0 || !isfinite(r.tau) || !isfinite(r.kappa))
+    st = 5;  // NUMERICAL
+  else if (res <= tol)
+    st = 1;  // SOLVED
+  else if (pinf <= tol)
+    st = 2;  // PRIMAL_INFEASIBLE
+  else if (dinf <= tol)
+    st = 3;  // DUAL_INFEASIBLE
+  R.status = st;
+  R.iters = it;
+  rep[i] = R;
+  if (st != 0) {
+    active[i] = 0;
+    atomicSub(n_active, 1);
+  }
+}
+
+template <typename T, typename TC>
+__global__ void __launch_bounds__(256) k_persistent(DevPlan<T> p, PersistArgs<TC> a) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ int s_item;
+  const unsigned G = gridDim.x;
+  unsigned gen = 0;
+  const int64_t gt = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t gs = static_cast<int64_t>(G) * blockDim.x;
+  const int warp0 = static_cast<int>(gt >> 5), nwarps = static_cast<int>(gs >> 5);
+  int32_t* err = p.err;
+#define SOS_GRID_SYNC() \
+  if (!grid_barrier(a.bar, (++gen) * G, err)) return
+  int it = 0;
+  for (it = 1; it <= a.max_iter; ++it) {
+    d_rows_r(p, gt, gs);
+    SOS_GRID_SYNC();
+    d_lr_y(p, warp0, nwarps);
+    SOS_GRID_SYNC();
+    for (int i = blockIdx.x; i < p.n_inst; i += G) d_woodbury(p, i, reinterpret_cast<double*>(dsm));
+    SOS_GRID_SYNC();
+    d_rows_sigma2(p, gt, gs);
+    SOS_GRID_SYNC();
+    for (int i = blockIdx.x; i < p.n_inst; i += G) d_inst_scalar(p, i);
+    SOS_GRID_SYNC();
+    d_rows_y(p, gt, gs);
+    SOS_GRID_SYNC();
+    if (a.dynamic) {
+      const int64_t base = static_cast<int64_t>(it - 1) * (a.n_sched + G);
+      while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = static_cast<int>(static_cast<int64_t>(atomicAdd(a.queue, 1u)) - base);
+        __syncthreads();
+        const int k = s_item;
+        if (k >= a.n_sched) break;
+        d_psd_small(p, a.sched[k], a.wm, dsm);
+      }
+    } else {
+      for (int k = blockIdx.x; k < a.n_sched; k += G) d_psd_small(p, a.sched[k], a.wm, dsm);
+    }
+    SOS_GRID_SYNC();
+    if (a.k_check > 0 && (it % a.k_check == 0 || it == a.max_iter)) {
+      d_res_rows(p, gt, gs);
+      d_res_lr(p, warp0, nwarps);
+      SOS_GRID_SYNC();
+      for (int i = blockIdx.x; i < p.n_inst; i += G) {
+        d_res_inst(p, i);
+        d_check(p, i, it, a.tol, a.rep, a.active, a.n_active);
+      }
+      SOS_GRID_SYNC();
+      if (__ldcg(a.n_active) == 0) break;
+    }
+  }
+#undef SOS_GRID_SYNC
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.iters_done = it > a.max_iter ? a.max_iter : it;
 }
 
 int grid_for(int64_t n, int threads, int sms) {
@@ -938,6 +1078,45 @@ cudaError_t prepare_kernels(int max_small_n, int max_teff) {
   return e;
 }
 
+
+template <typename T, typename TC>
+size_t persistent_smem_bytes(int max_small_n, int max_teff) {
+  size_t a = psd_small_smem_bytes(max_small_n, sizeof(TC) == 8);
+  size_t b = sizeof(double) * 2 * static_cast<size_t>(max_teff > 0 ? max_teff : 1);
+  return a > b ? a : b;
+}
+
+template <typename T, typename TC>
+int persistent_max_ctas_per_sm(int max_small_n, int max_teff) {
+  const size_t sm = persistent_smem_bytes<T, TC>(max_small_n, max_teff);
+  if (cudaFuncSetAttribute(k_persistent<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)) !=
+      cudaSuccess)
+    return 0;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent<T, TC>, 256, sm) != cudaSuccess) return 0;
+  return per;
+}
+
+template <typename T, typename TC>
+cudaError_t launch_persistent(const DevPlan<T>& p, const PersistArgs<TC>& a, int grid, int max_small_n, int max_teff,
+                              cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.queue, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = persistent_smem_bytes<T, TC>(max_small_n, max_teff);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_persistent<T, TC>, p, a);
+}
+
 #define SOS_INSTANTIATE(T)                                                                       \
   template cudaError_t launch_affine<T>(const DevPlan<T>&, const LaunchShape&, cudaStream_t);    \
   template cudaError_t launch_residuals<T>(const DevPlan<T>&, const LaunchShape&, cudaStream_t);
@@ -947,7 +1126,10 @@ cudaError_t prepare_kernels(int max_small_n, int max_teff) {
                                                cudaStream_t);                                               \
   template cudaError_t launch_psd_large<T, TC>(const DevPlan<T>&, int, int, const LargeScratch<TC>&, int,     \
                                                cudaStream_t);                                               \
-  template cudaError_t prepare_kernels<T, TC>(int, int);
+  template cudaError_t prepare_kernels<T, TC>(int, int);                                                     \
+  template int persistent_max_ctas_per_sm<T, TC>(int, int);                                                  \
+  template cudaError_t launch_persistent<T, TC>(const DevPlan<T>&, const PersistArgs<TC>&, int, int, int,     \
+                                                cudaStream_t);
 
 SOS_INSTANTIATE(double)
 SOS_INSTANTIATE(float)

@@ -84,6 +84,30 @@ struct SmallWarm {
   int32_t limit = 1024;     // cold restart after this many warm iterations
 };
 
+// Per-instance result of the device-side checks of the persistent solver.
+struct InstReport {
+  double rp, rd, gap, pobj, dobj;
+  int32_t status;  // SOS_* status (0 while running)
+  int32_t iters;   // iteration of the last check
+};
+
+template <typename TC>
+struct PersistArgs {
+  int32_t max_iter = 0;
+  int32_t k_check = 0;        // 0: no checks (fixed number of iterations)
+  double tol = 0.0;
+  uint32_t* bar = nullptr;     // grid barrier [2], zeroed by the launcher
+  uint32_t* queue = nullptr;   // work queue counter, zeroed by the launcher
+  int32_t* active = nullptr;   // same array as DevPlan::active
+  int32_t* n_active = nullptr; // running instances
+  InstReport* rep = nullptr;
+  const int32_t* sched = nullptr;  // Gram blocks, largest first
+  int32_t n_sched = 0;
+  int32_t dynamic = 0;         // 1: atomic work queue, 0: round-robin
+  SmallWarm<TC> wm;
+  int32_t* iters_done = nullptr;
+};
+
 struct LaunchShape {
   int sms = 152;
   int row_threads = 256;
@@ -103,6 +127,11 @@ template <typename T, typename TC>
 cudaError_t prepare_kernels(int max_small_n, int max_teff);
 template <typename T>
 cudaError_t launch_residuals(const DevPlan<T>& p, const LaunchShape& ls, cudaStream_t s);
+template <typename T, typename TC>
+int persistent_max_ctas_per_sm(int max_small_n, int max_teff);
+template <typename T, typename TC>
+cudaError_t launch_persistent(const DevPlan<T>& p, const PersistArgs<TC>& a, int grid, int max_small_n, int max_teff,
+                              cudaStream_t s);
 size_t psd_small_smem_bytes(int maxN, bool fp64);
 size_t large_smem_bytes(int N, size_t es);
 int psd_small_max_n(bool fp64);
