@@ -145,13 +145,78 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def warmstart_arm(args):
+    """Learned warm start (parametric quartic POP, n = 10, Gram 66, m = 1001):
+    time to a 1e-4 residual per instance for 1024 unseen members, batched with
+    FP32 projections and started from the network's prediction, against the
+    same batch from a cold start and against the plain FP64 form one instance
+    at a time (sample)."""
+    import torch
+
+    from instances import workloads as W
+    from paper_1708_04174_gb300 import capi, warmstart
+
+    fam = W.ParametricPOP(n=10, K=16, seed=0)
+    th_train = W.ParametricPOP.thetas(args.train, 100)
+    th_test = W.ParametricPOP.thetas(1024, 200)
+    ws = warmstart.WarmStart(fam, hidden=512, seed=0)
+    t0 = time.perf_counter()
+    res, dims, t_solve_train, tune = ws.solve(th_train, 1e-4, 5000)
+    ok = np.array([r["status"] == capi.SOLVED for r in res])
+    targets = warmstart.solution_vectors([r for r, k in zip(res, ok) if k], [d for d, k in zip(dims, ok) if k])
+    t_data = time.perf_counter() - t0
+    losses = ws.train(th_train[ok], targets, epochs=args.epochs, batch=256, lr=1e-3)
+    pred = ws.predict(th_test)
+    torch.cuda.synchronize()
+    warm, _, t_warm, _ = ws.solve(th_test, 1e-4, 5000, start=pred)
+    cold, _, t_cold, _ = ws.solve(th_test, 1e-4, 5000)
+    it_w = np.array([r["iters"] for r in warm])
+    it_c = np.array([r["iters"] for r in cold])
+    # plain FP64 form, one instance at a time, on a sample of the same test set
+    sample = list(range(0, 1024, 64))
+    t_plain = 0.0
+    it_plain = []
+    for i in sample:
+        s = capi.Solver(fam.program(th_test[i]), precision=capi.PREC_FP64, k_check=10)
+        t1 = time.perf_counter()
+        r = s.solve(1e-4, 5000, want_solution=False)[0]
+        t_plain += time.perf_counter() - t1
+        it_plain.append(r["iters"])
+        s.close()
+    per_plain = t_plain / len(sample)
+    per_warm = t_warm / 1024
+    obj_err = np.array([abs(a["obj_primal"] - b["obj_primal"]) / max(1.0, abs(b["obj_primal"]))
+                        for a, b in zip(warm, cold)])
+    line = {"metric": "time to a 1e-4 residual per instance (learned warm start + FP32 projections + batched)",
+            "value": per_warm, "unit": "s/instance", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64 iterates, f32 proj",
+            "data": "synthetic",
+            "config": {"workload": "parametric_warmstart", "family": "p0 + sum_k theta_k q_k, n=10, K=16, Gram 66, m=1001",
+                       "train": int(args.train), "test": 1024, "mlp": "16-512-512-5425", "epochs": args.epochs},
+            "speedup_vs_plain_fp64": per_plain / per_warm,
+            "speedup_vs_cold_batched": t_cold / t_warm,
+            "warm": {"seconds": t_warm, "iters_mean": float(it_w.mean()), "iters_max": int(it_w.max()),
+                     "solved": int(sum(r["status"] == capi.SOLVED for r in warm))},
+            "cold_batched": {"seconds": t_cold, "iters_mean": float(it_c.mean()), "iters_max": int(it_c.max()),
+                             "solved": int(sum(r["status"] == capi.SOLVED for r in cold))},
+            "plain_fp64_single": {"seconds_per_instance": per_plain, "iters_mean": float(np.mean(it_plain)),
+                                  "sample": len(sample)},
+            "objective_rel_diff_warm_vs_cold": {"max": float(obj_err.max()), "median": float(np.median(obj_err))},
+            "training": {"data_seconds": t_data, "solve_seconds": t_solve_train, "solved": int(ok.sum()),
+                         "train_seconds": ws.log["train_seconds"], "loss_first": losses[0], "loss_last": losses[-1]},
+            "tuning": tune}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="ball_pop_n20", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="ball_pop_n20", choices=sorted(WORKLOADS) + ["parametric_warmstart"])
+    ap.add_argument("--train", type=int, default=20000, help="training members (parametric_warmstart)")
+    ap.add_argument("--epochs", type=int, default=40, help="training epochs (parametric_warmstart)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tt", action="store_true", help="skip the time-to-1e-4 solves")
@@ -162,6 +227,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         return reference_arm(args, rank)
+    if args.workload == "parametric_warmstart":
+        return warmstart_arm(args)
 
     import torch
 

@@ -119,7 +119,11 @@ typedef struct {
   int32_t k_check;        /* residual check period in iterations (>= 1) */
   void* cuda_stream;      /* cudaStream_t to issue work on, or NULL */
   int32_t solve_mode;     /* 0, 1 or 2 as above */
-  int32_t reserved[7];    /* must be zero */
+  int32_t large_method;   /* projection of blocks too large for one CTA:
+                             0 auto = Newton-Schulz on the tensor cores for
+                             FP32 projections, grid Jacobi for FP64;
+                             1 grid Jacobi; 2 Newton-Schulz (FP32 forms) */
+  int32_t reserved[6];    /* must be zero */
 } sos_options;
 
 /* Per-instance solve report.  x, y, s are optional caller-allocated HOST
@@ -246,10 +250,41 @@ int sos_psd_project(const double* in, double* out, int32_t N, void* stream);
 #define SOS_NOALLOC_MAX_N 256
 int sos_psd_project_noalloc(const double* in, double* out, int32_t N, void* stream);
 
+/* ---- learned warm start: the network ----
+ * A multilayer perceptron theta -> predicted iterate used to warm-start the
+ * solver on a parametric family of SOS programs (the paper has no learned
+ * component; this is the warm-start form built around its solver):
+ *   h1 = relu(X W1^T + b1), h2 = relu(h1 W2^T + b2), y = h2 W3^T + b3,
+ * trained with Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared
+ * error of targets standardised per output column (mean/std set by
+ * sos_mlp_fit_scaling; identity until then).  All products run on the tensor
+ * cores (tcgen05) with BF16 operands and FP32 accumulation; weights, moments
+ * and activations are FP32.  Flat parameter order: W1 [n_hidden x n_in], b1,
+ * W2 [n_hidden x n_hidden], b2, W3 [n_out x n_hidden], b3.
+ * Data pointers X [batch x n_in] and Y [batch x n_out] are row-major DEVICE
+ * pointers owned by the caller; params/grads are HOST arrays of
+ * sos_mlp_param_count floats.  Work runs on the stream given at creation and
+ * every call returns after it has finished.  Errors: SOS_ERR_INVALID_ARG,
+ * SOS_ERR_CUDA, SOS_ERR_TIMEOUT (message in sos_last_error(NULL)). */
+typedef struct sos_mlp sos_mlp;
+int sos_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed, void* cuda_stream, sos_mlp** out);
+void sos_mlp_destroy(sos_mlp* net);
+int64_t sos_mlp_param_count(const sos_mlp* net);
+int sos_mlp_set_params(sos_mlp* net, const float* params);  /* also resets the Adam moments */
+int sos_mlp_get_params(const sos_mlp* net, float* params);
+/* per-column mean and standard deviation of the training targets Y [rows x n_out] */
+int sos_mlp_fit_scaling(sos_mlp* net, const float* Y, int32_t rows);
+/* loss (standardised targets) and, if grads != NULL, its gradient */
+int sos_mlp_gradients(sos_mlp* net, const float* X, const float* Y, int32_t batch, double* loss, float* grads);
+/* one Adam step on a batch; *loss (may be NULL) is the loss before the step */
+int sos_mlp_train_step(sos_mlp* net, const float* X, const float* Y, int32_t batch, float lr, double* loss);
+/* Y = de-standardised prediction for X */
+int sos_mlp_predict(sos_mlp* net, const float* X, float* Y, int32_t batch);
+
 /* Diagnostics (synchronises the handle's stream): out[0] = iterations run
  * since setup, out[1] = number of Gram blocks, out[2] = largest number of
- * Jacobi sweeps any block needed in the last projection, out[3] = total
- * sweeps over all blocks in the last projection. */
+ * Jacobi sweeps (or Newton-Schulz iterations) any block needed in the last
+ * projection, out[3] = their total over all blocks. */
 int sos_stats(sos_handle* h, int64_t out[4]);
 
 /* Launch configuration chosen for the handle: out[0] = 1 for the persistent

@@ -42,13 +42,24 @@ class Constraint:
     coef)`` (term k adds coef[k] x^exps[k] to g_{index[k]+1}); the dict view
     is then built on first access."""
 
-    def __init__(self, degree: int, g0: Poly, g: Optional[List[Poly]] = None, blocks: Optional[List[Block]] = None,
-                 term_arrays=None):
+    def __init__(self, degree: int, g0: Optional[Poly] = None, g: Optional[List[Poly]] = None,
+                 blocks: Optional[List[Block]] = None, term_arrays=None, g0_arrays=None):
         self.degree = degree  # rows: all monomials of degree <= degree
-        self.g0 = g0
+        self._g0 = g0
         self._g = g
         self.blocks = list(blocks or [])
         self.term_arrays = term_arrays
+        self.g0_arrays = g0_arrays  # (exps [K x n] int, coef [K]) alternative to the dict g0
+
+    @property
+    def g0(self) -> Poly:
+        if self._g0 is None:
+            exps, coef = self.g0_arrays
+            self._g0 = {}
+            for e, c in zip(map(tuple, np.asarray(exps).tolist()), np.asarray(coef).tolist()):
+                if c != 0.0:
+                    self._g0[e] = self._g0.get(e, 0.0) + c
+        return self._g0
 
     @property
     def g(self) -> List[Poly]:

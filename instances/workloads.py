@@ -288,6 +288,26 @@ class ParametricPOP:
     def program(self, theta: np.ndarray) -> SOSProgram:
         return _pop_program(self.n, self.poly(theta), f"parametric_pop(n={self.n})", ball=False)
 
+    def programs(self, thetas: np.ndarray) -> List[SOSProgram]:
+        """Programs for many parameter vectors at once: every member has the
+        same support, so its coefficients are one row of [1, theta] C."""
+        support = sorted(set(self.p0).union(*[set(q) for q in self.q]), key=lambda e: (sum(e), tuple(-x for x in e)))
+        index = {e: i for i, e in enumerate(support)}
+        Cm = np.zeros((len(support), 1 + self.K))
+        for e, c in self.p0.items():
+            Cm[index[e], 0] = c
+        for k, q in enumerate(self.q):
+            for e, c in q.items():
+                Cm[index[e], 1 + k] = c
+        coefs = np.hstack([np.ones((len(thetas), 1)), np.asarray(thetas, float)]) @ Cm.T
+        exps = np.array(support, dtype=np.int32)
+        z = _zero(self.n)
+        out = []
+        for i in range(len(thetas)):
+            con = Constraint(degree=4, g=[{z: 1.0}], blocks=[Block(2)], g0_arrays=(exps, coefs[i]))
+            out.append(SOSProgram(n=self.n, w=np.array([-1.0]), constraints=[con], name=f"parametric_pop(n={self.n})"))
+        return out
+
     @staticmethod
     def thetas(count: int, seed: int, K: int = 16) -> np.ndarray:
         return np.random.default_rng(seed).uniform(-1.0, 1.0, size=(count, K))

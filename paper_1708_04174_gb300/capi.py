@@ -45,7 +45,7 @@ class sos_program(C.Structure):
 
 class sos_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("k_check", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("solve_mode", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("solve_mode", C.c_int32), ("large_method", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class sos_result(C.Structure):
@@ -73,6 +73,17 @@ EXPORTS = {
     "sos_psd_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sos_psd_project_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sos_run_stage": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sos_mlp_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "sos_mlp_destroy": (None, [C.c_void_p]),
+    "sos_mlp_param_count": (C.c_int64, [C.c_void_p]),
+    "sos_mlp_set_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "sos_mlp_get_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "sos_mlp_fit_scaling": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "sos_mlp_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_float)]),
+    "sos_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float,
+                                     C.POINTER(C.c_double)]),
+    "sos_mlp_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
 }
 
 _lib = None
@@ -133,15 +144,21 @@ class _Marshalled:
                 rows = mono(n, con.degree)
                 tp, te, tc = [], [], []
                 arrays = getattr(con, "term_arrays", None)
-                polys = [con.g0] + ([] if arrays is not None else list(con.g))
+                g0a = getattr(con, "g0_arrays", None)
+                polys = ([] if g0a is not None else [con.g0]) + ([] if arrays is not None else list(con.g))
+                base = 0 if g0a is None else 1  # index of the first polynomial in polys
                 for k, poly in enumerate(polys):
                     for e, cval in poly.items():
-                        tp.append(k)
+                        tp.append(k + base)
                         te.append(e)
                         tc.append(cval)
                 tp = np.array(tp, dtype=np.int32)
                 te = np.array(te, dtype=np.int32).reshape(-1, n)
                 tc = np.array(tc, dtype=np.float64)
+                if g0a is not None:  # g_0 given as arrays
+                    tp = np.concatenate([np.zeros(len(g0a[1]), dtype=np.int32), tp])
+                    te = np.concatenate([np.asarray(g0a[0], dtype=np.int32).reshape(-1, n), te])
+                    tc = np.concatenate([np.asarray(g0a[1], dtype=np.float64), tc])
                 if arrays is not None:  # g_1..g_t given as flat term arrays
                     _, idx, exps, coef = arrays
                     tp = np.concatenate([tp, np.asarray(idx, dtype=np.int32) + 1])
@@ -215,7 +232,8 @@ def host_plan(prog):
 class Solver:
     """One libsos handle over a batch of SOS programs (instances)."""
 
-    def __init__(self, progs, precision: int = PREC_FP64, k_check: int = 10, stream=None, solve_mode: int = 0):
+    def __init__(self, progs, precision: int = PREC_FP64, k_check: int = 10, stream=None, solve_mode: int = 0,
+                 large_method: int = 0):
         if not isinstance(progs, (list, tuple)):
             progs = [progs]
         self.n_inst = len(progs)
@@ -225,6 +243,7 @@ class Solver:
         opts.k_check = k_check
         opts.cuda_stream = C.c_void_p(stream) if stream else None
         opts.solve_mode = solve_mode
+        opts.large_method = large_method
         h = C.c_void_p()
         _check(lib().sos_setup(m.progs, len(progs), C.byref(opts), C.byref(h)))
         self.h = h
@@ -314,3 +333,56 @@ class Solver:
                         "gap": r.gap, "obj_primal": r.obj_primal, "obj_dual": r.obj_dual, "tau": r.tau,
                         "kappa": r.kappa, "x": bufs[i][0], "y": bufs[i][1], "s": bufs[i][2]})
         return out
+
+
+class MLP:
+    """Warm-start network (tensor-core kernels of libsos).  Data arguments are
+    device pointers (e.g. ``tensor.data_ptr()`` of contiguous float32 CUDA
+    tensors); parameters and gradients are host float32 arrays."""
+
+    def __init__(self, n_in: int, n_hidden: int, n_out: int, seed: int = 0, stream: int = 0):
+        h = C.c_void_p()
+        _check(lib().sos_mlp_create(n_in, n_hidden, n_out, seed, C.c_void_p(stream) if stream else None, C.byref(h)))
+        self.h = h
+        self.shape = (n_in, n_hidden, n_out)
+        self.n_param = int(lib().sos_mlp_param_count(h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sos_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat: np.ndarray):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.n_param
+        _check(lib().sos_mlp_set_params(self.h, _ptr(flat, C.c_float)))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.n_param, dtype=np.float32)
+        _check(lib().sos_mlp_get_params(self.h, _ptr(out, C.c_float)))
+        return out
+
+    def fit_scaling(self, Y_ptr: int, rows: int):
+        _check(lib().sos_mlp_fit_scaling(self.h, C.c_void_p(Y_ptr), rows))
+
+    def gradients(self, X_ptr: int, Y_ptr: int, batch: int):
+        loss = C.c_double(0)
+        g = np.zeros(self.n_param, dtype=np.float32)
+        _check(lib().sos_mlp_gradients(self.h, C.c_void_p(X_ptr), C.c_void_p(Y_ptr), batch, C.byref(loss),
+                                       _ptr(g, C.c_float)))
+        return loss.value, g
+
+    def train_step(self, X_ptr: int, Y_ptr: int, batch: int, lr: float, want_loss: bool = False):
+        loss = C.c_double(0)
+        _check(lib().sos_mlp_train_step(self.h, C.c_void_p(X_ptr), C.c_void_p(Y_ptr), batch, lr,
+                                        C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def predict(self, X_ptr: int, Y_ptr: int, batch: int):
+        _check(lib().sos_mlp_predict(self.h, C.c_void_p(X_ptr), C.c_void_p(Y_ptr), batch))

@@ -35,6 +35,11 @@ struct LargeBlock {
   int bid, N, grid;
   LargeScratch<T> scratch;
 };
+
+struct NsBlock {
+  int bid, N;
+  NsScratch s;
+};
 }  // namespace
 
 struct sos_handle {
@@ -56,6 +61,8 @@ struct sos_handle {
   std::vector<LargeBlock<float>> large32;   // FP32 projections
   SmallWarm<double> warm64;
   SmallWarm<float> warm32;
+  std::vector<NsBlock> ns_large;  // large blocks projected by Newton-Schulz on the tensor cores
+  int32_t large_method = 0;
   int32_t* active = nullptr;  // device
   std::vector<int32_t> active_h;
   std::vector<int32_t> iters_h, status_h;
@@ -215,11 +222,16 @@ cudaError_t enqueue_stage(sos_handle* h, const DevPlan<T>& p, std::vector<LargeB
       e = launch_psd_small<T, TC>(p, c.ids, c.count, c.maxN, wm, h->stream);
       if (e != cudaSuccess) return e;
     }
-  if (stage == 2 || stage == 3)
+  if (stage == 2 || stage == 3) {
     for (auto& lb : large) {
       e = launch_psd_large<T, TC>(p, lb.bid, lb.N, lb.scratch, lb.grid, h->stream);
       if (e != cudaSuccess) return e;
     }
+    for (auto& nb : h->ns_large) {
+      e = launch_psd_ns<T>(p, nb.bid, nb.N, nb.s, h->stream);
+      if (e != cudaSuccess) return e;
+    }
+  }
   return e;
 }
 
@@ -507,14 +519,37 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
     TRY(make_devplan(h, c, max_teff, h->d64));
     TRY(make_large(h, h->large64, large));
     CK((prepare_kernels<double, double>(max_small, max_teff)));
-  } else if (h->precision == SOS_PREC_MIXED) {
-    TRY(make_devplan(h, c, max_teff, h->d64));
-    TRY(make_large(h, h->large32, large));
-    CK((prepare_kernels<double, float>(max_small, max_teff)));
   } else {
-    TRY(make_devplan(h, c, max_teff, h->d32));
-    TRY(make_large(h, h->large32, large));
-    CK((prepare_kernels<float, float>(max_small, max_teff)));
+    // FP32 projections: large blocks by Newton-Schulz on the tensor cores
+    // unless the Jacobi grid kernel is requested
+    std::vector<int> jac;
+    for (int b : large) {
+      if (h->large_method == 1) {
+        jac.push_back(b);
+        continue;
+      }
+      NsBlock nb{};
+      nb.bid = b;
+      nb.N = P.blocks[b].N;
+      const size_t Np = static_cast<size_t>(ns_padded(nb.N));
+      TRY(alloc(h, Np * Np, &nb.s.Wf));
+      TRY(alloc(h, Np * Np, &nb.s.X));
+      TRY(alloc(h, Np * Np, &nb.s.Y));
+      TRY(alloc(h, Np * Np, &nb.s.Xn));
+      TRY(alloc(h, static_cast<size_t>(ns_grid(nb.N)), &nb.s.partial));
+      TRY(alloc(h, 2, &nb.s.bar));
+      TRY(alloc(h, 1, &nb.s.iters_out));
+      h->ns_large.push_back(nb);
+    }
+    if (h->precision == SOS_PREC_MIXED) {
+      TRY(make_devplan(h, c, max_teff, h->d64));
+      TRY(make_large(h, h->large32, jac));
+      CK((prepare_kernels<double, float>(max_small, max_teff)));
+    } else {
+      TRY(make_devplan(h, c, max_teff, h->d32));
+      TRY(make_large(h, h->large32, jac));
+      CK((prepare_kernels<float, float>(max_small, max_teff)));
+    }
   }
   h->d64.tau = c.tau;  // FP64 scalars shared by every form
   h->d64.kappa = c.kappa;
@@ -622,6 +657,11 @@ int sos_setup(const sos_program* progs, int32_t n_progs, const sos_options* opts
     h->k_check = opts->k_check > 0 ? opts->k_check : 10;
     h->stream = static_cast<cudaStream_t>(opts->cuda_stream);
     h->solve_mode = opts->solve_mode;
+    h->large_method = opts->large_method;
+    if (h->large_method < 0 || h->large_method > 2 || (h->large_method == 2 && h->precision == SOS_PREC_FP64)) {
+      g_setup_error = "large_method must be 0, 1, or 2 (2 needs FP32 projections)";
+      return SOS_ERR_INVALID_ARG;
+    }
     if (h->solve_mode < 0 || h->solve_mode > 2) {
       g_setup_error = "unknown solve_mode";
       return SOS_ERR_INVALID_ARG;
@@ -1003,7 +1043,8 @@ int sos_launches_per_iteration(const sos_handle* h) {
   if (!h) return SOS_ERR_INVALID_ARG;
   if (h->persistent) return 0;  // one launch for all iterations of a call
   const int affine = h->TL > 0 ? 6 : 4;
-  return affine + static_cast<int>(h->small.size()) + static_cast<int>(h->large64.size() + h->large32.size());
+  return affine + static_cast<int>(h->small.size()) +
+         static_cast<int>(h->large64.size() + h->large32.size() + h->ns_large.size());
 }
 
 void* sos_stream(sos_handle* h) { return h ? static_cast<void*>(h->stream) : nullptr; }

@@ -16,10 +16,13 @@
 //   A_L^T sigma_2 = z            (since (I + A_L^T P^{-1} A_L) z = A_L^T P^{-1} r)
 //   u_hat_1 = w1hat - s c + A^T u_hat_2, and for a plain Gram entry
 //   W_e = u_hat_1,e - v_e = u_e + a_e u_hat_2[row(e)].
+#include <cuda_bf16.h>
+
 #include <cfloat>
 #include <cstdio>
 
 #include "kernels.h"
+#include "tcgen05.cuh"
 
 namespace sos {
 namespace {
@@ -779,6 +782,298 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
 }
 
 // ---------------------------------------------------------------------------
+// PSD projection of large blocks on the tensor cores (FP32-compute forms).
+// P_S+(W) = (W + W sign(W)) / 2, sign(W) by the Newton-Schulz iteration
+// X <- (3 X - X^3) / 2 from X_0 = W / |W|_F (Higham, Functions of Matrices,
+// ch. 5).  Every product is a tcgen05.mma GEMM: BF16 operands split into a
+// high and a low part (x = x_hi + x_lo, so X Y ~ X_hi Y_hi + X_hi Y_lo +
+// X_lo Y_hi) with FP32 accumulation in tensor memory.  The iterates are
+// symmetric polynomials of W, so each CTA computes one 128 x 64 tile of the
+// lower triangle (using rows of both operands, K-major) and writes it and its
+// mirror.  Operands are staged from L2 into shared memory in the no-swizzle
+// core-matrix layout (8 rows x 16 bytes per core matrix).
+// ---------------------------------------------------------------------------
+
+
+constexpr int kNsTM = 128, kNsTN = 64, kNsKC = 64;
+
+// Byte offset of element (r, k) of an R x kNsKC operand chunk in the core-matrix layout.
+__device__ __forceinline__ uint32_t ns_off(int r, int k) {
+  return static_cast<uint32_t>((r >> 3) * ((kNsKC / 8) * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Stage rows [r0, r0 + R) x cols [k0, k0 + kNsKC) of the Np x Np FP32 matrix
+// M (Np is a multiple of 128, so the chunk is always inside) as three BF16
+// parts x = x_hi + x_mid + x_lo (each the rounding of what the previous parts
+// leave).  A thread converts 8 consecutive values (two 16-byte loads) into
+// one 16-byte core-matrix row of each part; the loads of a thread's groups
+// are issued before any is used.
+__device__ __forceinline__ void ns_split8(const float4& a, const float4& b, uint4& h, uint4& m, uint4& l) {
+  const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  __nv_bfloat16 hh[8], mm[8], ll[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    hh[j] = __float2bfloat16_rn(x[j]);
+    const float r1 = x[j] - __bfloat162float(hh[j]);
+    mm[j] = __float2bfloat16_rn(r1);
+    ll[j] = __float2bfloat16_rn(r1 - __bfloat162float(mm[j]));
+  }
+  h = *reinterpret_cast<const uint4*>(hh);
+  m = *reinterpret_cast<const uint4*>(mm);
+  l = *reinterpret_cast<const uint4*>(ll);
+}
+
+template <int R>
+__device__ __forceinline__ void ns_stage(const float* M, int Np, int r0, int k0, unsigned char* p0, unsigned char* p1,
+                                         unsigned char* p2) {
+  constexpr int kGroups = R * (kNsKC / 8);  // 8-element groups in the chunk
+  constexpr int kPer = (kGroups + 255) / 256;
+  float4 va[kPer], vb[kPer];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int g = threadIdx.x + q * 256;
+    if (g < kGroups) {
+      const int r = g >> 3, c = g & 7;  // row, 8-column group
+      const float4* src = reinterpret_cast<const float4*>(M + static_cast<int64_t>(r0 + r) * Np + k0 + c * 8);
+      va[q] = __ldcg(src);
+      vb[q] = __ldcg(src + 1);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int g = threadIdx.x + q * 256;
+    if (g < kGroups) {
+      const int r = g >> 3, c = g & 7;
+      uint4 h, m, l;
+      ns_split8(va[q], vb[q], h, m, l);
+      const uint32_t o = ns_off(r, c * 8);
+      *reinterpret_cast<uint4*>(p0 + o) = h;
+      *reinterpret_cast<uint4*>(p1 + o) = m;
+      *reinterpret_cast<uint4*>(p2 + o) = l;
+    }
+  }
+}
+
+struct NsState {
+  uint64_t* mbar;
+  uint32_t tmem;
+  uint32_t phase;
+  bool ok;
+};
+
+constexpr size_t kNsSmem = 3 * (kNsTM + kNsTN) * kNsKC * 2;  // three parts of both operand chunks
+
+// acc[128 x 64] (TMEM) = A[m0.., :] * B[n0.., :]^T over k in [0, Np), with the
+// six products of the three-part split whose exponent sum is at most 2^-16.
+__device__ void ns_gemm(const float* A, const float* B, int Np, int m0, int n0, unsigned char* smem, NsState& st) {
+  unsigned char* a[3];
+  unsigned char* b[3];
+  for (int q = 0; q < 3; ++q) a[q] = smem + q * kNsTM * kNsKC * 2;
+  for (int q = 0; q < 3; ++q) b[q] = smem + 3 * kNsTM * kNsKC * 2 + q * kNsTN * kNsKC * 2;
+  constexpr uint32_t LBO = 128, SBO = (kNsKC / 8) * 128;
+  constexpr uint32_t idesc = tc::idesc_bf16(kNsTM, kNsTN);
+  const int pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
+  for (int k0 = 0; k0 < Np; k0 += kNsKC) {
+    ns_stage<kNsTM>(A, Np, m0, k0, a[0], a[1], a[2]);
+    ns_stage<kNsTN>(B, Np, n0, k0, b[0], b[1], b[2]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (threadIdx.x == 0 && st.ok) {
+      for (int s = 0; s < kNsKC / 16; ++s) {
+        const uint32_t so = s * 2 * LBO;
+        for (int q = 0; q < 6; ++q) {
+          const uint32_t acc = (k0 > 0 || s > 0 || q > 0) ? 1u : 0u;
+          tc::mma(st.tmem, tc::desc(tc::smem_u32(a[pa[q]]) + so, LBO, SBO), tc::desc(tc::smem_u32(b[pb[q]]) + so, LBO, SBO),
+                  idesc, acc);
+        }
+      }
+      tc::commit(st.mbar);
+    }
+    // every thread waits for the MMAs before the chunk buffers are rewritten
+    const bool good = st.ok ? tc::wait(st.mbar, st.phase) : false;
+    st.phase ^= 1u;
+    if (!good) st.ok = false;
+    tc::fence_after();
+  }
+}
+
+
+__host__ __device__ __forceinline__ int ns_np(int N) { return (N + kNsTM - 1) / kNsTM * kNsTM; }
+__host__ __device__ __forceinline__ int ns_tiles(int N) {
+  const int nti = ns_np(N) / kNsTM;
+  return nti * (nti + 1) * (kNsTM / kNsTN) / 2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch S) {
+  extern __shared__ __align__(1024) unsigned char nsm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ double red[40];
+  const BlockDesc bd = p.blocks[bid];
+  if (!p.active[bd.inst]) return;
+  const double s_sm = p.st[bd.inst].s;
+  const int N = bd.N, Np = ns_np(N);
+  const unsigned G = gridDim.x;
+  unsigned gen = 0;
+  int32_t* err = p.err;
+  const int64_t gt = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t gs = static_cast<int64_t>(G) * blockDim.x;
+  // this CTA's lower tile: row tile ti holds column tiles 0 .. 2 ti + 1
+  int ti = 0, rem = blockIdx.x;
+  while (rem >= (ti + 1) * (kNsTM / kNsTN)) {
+    rem -= (ti + 1) * (kNsTM / kNsTN);
+    ++ti;
+  }
+  const int m0 = ti * kNsTM, n0 = rem * kNsTN;
+
+  NsState st;
+  st.mbar = &mbar;
+  st.phase = 0;
+  st.ok = true;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_base)),
+                 "r"(kNsTN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+
+  bool alive = true;
+#define NS_SYNC()                                   \
+  do {                                              \
+    tc::fence_before();                             \
+    alive = grid_barrier(S.bar, (++gen) * G, err);  \
+    tc::fence_after();                              \
+  } while (0)
+  // load W (unscaled, FP32) and its Frobenius norm
+  double nrm = 0.0;
+  for (int64_t q = gt; q < static_cast<int64_t>(Np) * Np; q += gs) {
+    const int i = static_cast<int>(q / Np), j = static_cast<int>(q - static_cast<int64_t>(i) * Np);
+    float w = 0.f;
+    if (i < N && j < N) {
+      const int ii = i >= j ? i : j, jj = i >= j ? j : i;
+      const T wv = proj_input(p, bd, packed_index(ii, jj, N), ii != jj, s_sm);
+      if (i >= j) nrm += d(wv) * d(wv);
+      w = (i == j) ? static_cast<float>(wv) : static_cast<float>(d(wv) * 0.70710678118654752440);
+    }
+    S.Wf[q] = w;
+  }
+  const double part = block_sum(nrm, red);
+  if (threadIdx.x == 0) S.partial[blockIdx.x] = part;
+  NS_SYNC();
+  st.tmem = tmem_base;
+  const int wq = (threadIdx.x >> 5) & 3;  // TMEM lane quarter of this warp
+  const int chalf = (threadIdx.x >> 7);   // warps 4..7 take the upper 32 columns
+  const int row = m0 + wq * 32 + (threadIdx.x & 31);
+  int it = 0;
+  float* X = S.X;
+  if (alive) {
+  double tot = 0.0;
+  for (unsigned c = 0; c < G; ++c) tot += __ldcg(S.partial + c);
+  const float inv = tot > 0.0 ? static_cast<float>(1.0 / sqrt(tot)) : 0.f;
+  for (int64_t q = gt; q < static_cast<int64_t>(Np) * Np; q += gs) S.X[q] = __ldcg(S.Wf + q) * inv;
+  NS_SYNC();
+
+  float* Xn = S.Xn;
+  // Scaled Newton-Schulz: with |eigenvalues| of X_k in [ell_k, 1], the step
+  // X <- (3 a X - a^3 X^3) / 2, a = sqrt(3 / (1 + ell + ell^2)), maps them into
+  // [ell_{k+1}, 1] with ell_{k+1} = a ell (3 - a^2 ell^2) / 2; smaller ones grow
+  // by about 1.5 a per step.  ell_0 is an assumed floor (eigenvalues below it
+  // still grow, only not optimally); a -> 1 recovers the plain iteration.
+  double ell = 1e-6;
+  double alpha = sqrt(3.0 / (1.0 + ell + ell * ell));
+  for (it = 0; alive && it < S.max_iter; ++it) {
+    // Y = X X
+    ns_gemm(X, X, Np, m0, n0, nsm, st);
+    for (int c0 = chalf * 32; c0 < chalf * 32 + 32; c0 += 8) {
+      float v[8];
+      tc::ld8(st.tmem + (static_cast<uint32_t>(wq * 32) << 16) + c0, v);
+      for (int j = 0; j < 8; ++j) {
+        const int col = n0 + c0 + j;
+        if (row >= col) {
+          S.Y[static_cast<int64_t>(row) * Np + col] = v[j];
+          S.Y[static_cast<int64_t>(col) * Np + row] = v[j];
+        }
+      }
+    }
+    NS_SYNC();
+    if (!alive) break;
+    // X_next = 1.5 a X - 0.5 a^3 Y X (scaled Newton-Schulz), and |X_next - X|^2
+    const float ca = static_cast<float>(1.5 * alpha), cb = static_cast<float>(0.5 * alpha * alpha * alpha);
+    ell = 0.5 * alpha * ell * (3.0 - alpha * alpha * ell * ell);
+    alpha = sqrt(3.0 / (1.0 + ell + ell * ell));
+    ns_gemm(S.Y, X, Np, m0, n0, nsm, st);
+    double dsq = 0.0;
+    for (int c0 = chalf * 32; c0 < chalf * 32 + 32; c0 += 8) {
+      float v[8];
+      tc::ld8(st.tmem + (static_cast<uint32_t>(wq * 32) << 16) + c0, v);
+      for (int j = 0; j < 8; ++j) {
+        const int col = n0 + c0 + j;
+        if (row >= col) {
+          const float x = __ldcg(X + static_cast<int64_t>(row) * Np + col);
+          const float xn = ca * x - cb * v[j];
+          Xn[static_cast<int64_t>(row) * Np + col] = xn;
+          Xn[static_cast<int64_t>(col) * Np + row] = xn;
+          const double df = static_cast<double>(xn) - x;
+          dsq += (row == col ? 1.0 : 2.0) * df * df;
+        }
+      }
+    }
+    const double pd = block_sum(dsq, red);
+    if (threadIdx.x == 0) S.partial[blockIdx.x] = pd;
+    NS_SYNC();
+    if (!alive) break;
+    double dtot = 0.0;
+    for (unsigned c = 0; c < G; ++c) dtot += __ldcg(S.partial + c);
+    float* tmp = X;
+    X = Xn;
+    Xn = tmp;
+    if (dtot <= static_cast<double>(S.tol) * S.tol * Np) {  // same decision in every CTA
+      ++it;
+      break;
+    }
+  }
+  }
+  // U = (W + W S) / 2 with S = sign(W) ~ X; outputs u = svec(U), v = u - W
+  if (alive) ns_gemm(S.Wf, X, Np, m0, n0, nsm, st);
+  if (alive && st.ok) {
+  for (int c0 = chalf * 32; c0 < chalf * 32 + 32; c0 += 8) {
+    float v[8];
+    tc::ld8(st.tmem + (static_cast<uint32_t>(wq * 32) << 16) + c0, v);
+    for (int j = 0; j < 8; ++j) {
+      const int col = n0 + c0 + j;
+      if (row >= col && row < N && col < N) {
+        const float w = __ldcg(S.Wf + static_cast<int64_t>(row) * Np + col);
+        const float u = 0.5f * (w + v[j]);
+        const int64_t kk = packed_index(row, col, N);
+        const T wv = proj_input(p, bd, kk, row != col, s_sm);
+        const T uu = (row != col) ? static_cast<T>(static_cast<double>(u) * kSqrt2) : static_cast<T>(u);
+        p.ux[bd.x_off + kk] = uu;
+        p.vx[bd.x_off + kk] = uu - wv;
+      }
+    }
+  }
+  }
+#undef NS_SYNC
+  // cleanup on every path: MMAs still in flight after a failed wait get one
+  // more bounded wait, then the tensor memory is released
+  if (!st.ok) tc::wait(st.mbar, st.phase ^ 1u);
+  tc::fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(st.tmem), "r"(kNsTN));
+  if (!st.ok && threadIdx.x == 0) atomicExch(err, 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *S.iters_out = it;
+    p.blk_sweeps[bid] = it;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // residuals (every k_check iterations)
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -1117,9 +1412,33 @@ cudaError_t launch_persistent(const DevPlan<T>& p, const PersistArgs<TC>& a, int
   return cudaLaunchKernelEx(&cfg, k_persistent<T, TC>, p, a);
 }
 
+int ns_grid(int N) { return ns_tiles(N); }
+int ns_padded(int N) { return ns_np(N); }
+size_t ns_smem_bytes() { return kNsSmem; }
+
+template <typename T>
+cudaError_t launch_psd_ns(const DevPlan<T>& p, int bid, int N, const NsScratch& S, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_psd_ns<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kNsSmem));
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(S.bar, 0, 2 * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ns_tiles(N));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = kNsSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_psd_ns<T>, p, bid, S);
+}
+
 #define SOS_INSTANTIATE(T)                                                                       \
   template cudaError_t launch_affine<T>(const DevPlan<T>&, const LaunchShape&, cudaStream_t);    \
-  template cudaError_t launch_residuals<T>(const DevPlan<T>&, const LaunchShape&, cudaStream_t);
+  template cudaError_t launch_residuals<T>(const DevPlan<T>&, const LaunchShape&, cudaStream_t);             \
+  template cudaError_t launch_psd_ns<T>(const DevPlan<T>&, int, int, const NsScratch&, cudaStream_t);
 
 #define SOS_INSTANTIATE_PROJ(T, TC)                                                                          \
   template cudaError_t launch_psd_small<T, TC>(const DevPlan<T>&, const int32_t*, int, int, const SmallWarm<TC>&, \

@@ -76,6 +76,19 @@ struct LargeScratch {
 
 constexpr int kMaxSweeps = 40;
 
+// Scratch of the Newton-Schulz projection (tensor cores) of one large block.
+struct NsScratch {
+  float* Wf = nullptr;  // W, Np x Np (Np = N rounded up to 128)
+  float* X = nullptr;
+  float* Y = nullptr;
+  float* Xn = nullptr;
+  double* partial = nullptr;  // per CTA
+  uint32_t* bar = nullptr;    // grid barrier [2], zeroed by the launcher
+  int32_t* iters_out = nullptr;
+  int32_t max_iter = 60;
+  float tol = 2e-5f;          // stop when |X_next - X|_F <= tol sqrt(Np)
+};
+
 // Eigenvectors kept across iterations for the shared-memory projection.
 template <typename TC>
 struct SmallWarm {
@@ -127,6 +140,10 @@ template <typename T, typename TC>
 cudaError_t prepare_kernels(int max_small_n, int max_teff);
 template <typename T>
 cudaError_t launch_residuals(const DevPlan<T>& p, const LaunchShape& ls, cudaStream_t s);
+template <typename T>
+cudaError_t launch_psd_ns(const DevPlan<T>& p, int bid, int N, const NsScratch& S, cudaStream_t s);
+int ns_grid(int N);
+int ns_padded(int N);
 template <typename T, typename TC>
 int persistent_max_ctas_per_sm(int max_small_n, int max_teff);
 template <typename T, typename TC>

@@ -27,7 +27,7 @@ def capi():
 
 def test_exports_match_header(capi):
     hdr = open(os.path.join(ROOT, "include", "sos.h")).read()
-    declared = set(re.findall(r"^\s*(?:int|void\*|void|const char\*)\s+(sos_\w+)\s*\(", hdr, re.M))
+    declared = set(re.findall(r"^\s*(?:int|int64_t|void\*|void|const char\*)\s+(sos_\w+)\s*\(", hdr, re.M))
     assert declared, "no declarations parsed"
     for name in declared:
         assert hasattr(capi.lib(), name), name
