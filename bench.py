@@ -105,6 +105,21 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max(x: float, dist, device: str) -> float:
+    """Maximum of x over the ranks of the default process group."""
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job throughput of independent replicas: all units over the
+    slowest rank's time."""
+    return world * units_per_rank / max_seconds
+
+
 def run_oracle_iters(prog, seconds: float, max_iters: int):
     """Times the CPU oracle's ADMM iterations (bounded sample)."""
     from oracle import admm, conic
@@ -277,10 +292,8 @@ def main():
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = float(np.sum(step_ms))
     if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ips = world * args.steps / (total_ms / 1e3)
+        total_ms = reduce_max(total_ms, dist, "cuda")
+    ips = aggregate_rate(args.steps, world, total_ms / 1e3)
 
     # dominant kernel: time each stage alone with events on the solver's stream
     stage_ms = {}
@@ -355,6 +368,30 @@ def main():
     out["roofline"]["peak_source"] = "FMA-loop probe on this GB300 (FP64 1.19 TFLOP/s, FP32 69.7 TFLOP/s)"
     out["clocks"] = clk.summary(local)
 
+    # the FP32-projection form (tensor-core Newton-Schulz for the large block)
+    # on the same instance and the same step definition, for comparison
+    if prec == capi.PREC_FP64 and not args.no_tt:
+        sm = capi.Solver(prog, precision=capi.PREC_MIXED, k_check=10)
+        sm.iterate(args.warmup)
+        sm.sync()
+        stm = torch.cuda.ExternalStream(sm.stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a0, a1 in ev:
+            with torch.cuda.stream(stm):
+                flush.zero_()
+                a0.record(stm)
+            sm.iterate(1)
+            with torch.cuda.stream(stm):
+                a1.record(stm)
+        sm.sync()
+        mixed_ms = float(np.sum([a0.elapsed_time(a1) for a0, a1 in ev]))
+        out_mixed = {"value": args.steps / (mixed_ms / 1e3), "unit": "iter/s", "ms_per_step": mixed_ms / args.steps,
+                     "form": "FP64 iterates, FP32 projections (tensor-core Newton-Schulz for N=231)",
+                     "stats": sm.stats()}
+        sm.close()
+    else:
+        out_mixed = None
+
     if not args.no_tt:
         tt = {}
         for nm, pr in (("fp64", capi.PREC_FP64), ("mixed_fp32_projections", capi.PREC_MIXED)):
@@ -366,6 +403,8 @@ def main():
             tt[nm] = {"seconds": dt, "iters": r["iters"], "status": r["status"], "obj": r["obj_primal"]}
             s2.close()
         out["time_to_1e-4"] = tt
+    if out_mixed is not None:
+        out["mixed_form"] = out_mixed
 
     if rank == 0 and not args.no_cpu_baseline:
         k, dt = run_oracle_iters(prog, seconds=15.0, max_iters=10**9)

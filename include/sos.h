@@ -288,7 +288,10 @@ int sos_mlp_predict(sos_mlp* net, const float* X, float* Y, int32_t batch);
 int sos_stats(sos_handle* h, int64_t out[4]);
 
 /* Launch configuration chosen for the handle: out[0] = 1 for the persistent
- * launch (0: per-phase kernels), out[1] = its grid size (CTAs), out[2] = 1
+ * launch (0: per-phase kernels), out[1] = its grid size (CTAs) -- or, for the
+ * per-phase path with a large block projected by the grid Jacobi kernel, the
+ * grid size the autotuner chose for that kernel (a quarter, half or all of
+ * the SMs) --, out[2] = 1
  * for the work-queue block schedule (0: round-robin, largest block first),
  * out[3] = candidates timed by the autotuner, out[4] = microseconds per
  * iteration of the chosen candidate during tuning. */

@@ -68,6 +68,7 @@ struct sos_handle {
   std::vector<int32_t> iters_h, status_h;
   int64_t iter_count = 0;
   int32_t* blk_sweeps = nullptr;  // device
+  int32_t large_grid_best = 0;    // grid chosen for the cooperative Jacobi kernel
   // persistent batched path
   bool persistent = false;
   int32_t solve_mode = 0;
@@ -384,6 +385,46 @@ int autotune_persistent(sos_handle* h) {
   return cold_start(h);
 }
 
+// Grid size of the cooperative Jacobi kernel of each large block: times one
+// projection (after one affine step from the cold start, so the input is a
+// realistic W) for 1/4, 1/2 and all SMs, keeps the fastest, and resets the
+// iterate.  Fewer CTAs make each grid barrier cheaper; more give more FP64
+// and FP32 throughput per round.
+template <typename TC>
+int autotune_large(sos_handle* h, std::vector<LargeBlock<TC>>& large) {
+  if (large.empty()) return SOS_OK;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(enqueue_any(h, 0));
+  const int sms = h->shape.sms;
+  const int cands[3] = {sms / 4, sms / 2, sms};
+  for (auto& lb : large) {
+    float best = 1e30f;
+    int best_g = sms;
+    for (int g : cands) {
+      if (g < 1) continue;
+      lb.grid = g;
+      for (auto& other : large) CK(cudaMemsetAsync(other.scratch.warm, 0, sizeof(int32_t), h->stream));
+      CK(cudaEventRecord(e0, h->stream));
+      CK(enqueue_any(h, 2));
+      CK(cudaEventRecord(e1, h->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_g = g;
+      }
+    }
+    lb.grid = best_g;
+    h->large_grid_best = best_g;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return check_err_word(h);
+}
+
 int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   HostPlan P;
   std::string err;
@@ -561,6 +602,9 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   // (auto mode keeps the persistent launch only if the autotuner finds it faster)
   if (h->solve_mode == 2 && !eligible)
     return set_err(h, SOS_ERR_UNSUPPORTED, "the persistent solver needs every Gram block to be small");
+  // grid size of the large-block Jacobi kernel
+  TRY(cold_start(h));
+  TRY(h->precision == SOS_PREC_FP64 ? autotune_large(h, h->large64) : autotune_large(h, h->large32));
   if (h->persistent) {
     std::vector<int32_t> order;
     for (int k = 5; k >= 0; --k)
@@ -1036,6 +1080,7 @@ int sos_tuning(const sos_handle* h, int32_t out[5]) {
   out[2] = h->p_dynamic;
   out[3] = h->p_tried;
   out[4] = static_cast<int32_t>(h->p_best_ms * 1000.f);
+  if (!h->persistent && h->large_grid_best > 0) out[1] = h->large_grid_best;
   return SOS_OK;
 }
 

@@ -980,13 +980,12 @@ __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch
   NS_SYNC();
 
   float* Xn = S.Xn;
-  // Scaled Newton-Schulz: with |eigenvalues| of X_k in [ell_k, 1], the step
-  // X <- (3 a X - a^3 X^3) / 2, a = sqrt(3 / (1 + ell + ell^2)), maps them into
-  // [ell_{k+1}, 1] with ell_{k+1} = a ell (3 - a^2 ell^2) / 2; smaller ones grow
-  // by about 1.5 a per step.  ell_0 is an assumed floor (eigenvalues below it
-  // still grow, only not optimally); a -> 1 recovers the plain iteration.
-  double ell = 1e-6;
-  double alpha = sqrt(3.0 / (1.0 + ell + ell * ell));
+  // Plain Newton-Schulz, X <- (3 X - X^3) / 2: eigenvalues of X in (0, 1]
+  // converge to sign(lambda) quadratically near 1 and grow by 1.5x per step
+  // near 0.  The optimally scaled variant (step a-dependent, a > 1) sends
+  // eigenvalues near 1 down to the current floor ell before they return; in
+  // FP32 with split-BF16 products those lose their relative accuracy there and
+  // the outer ADMM iteration stalls near a 2e-4 dual residual, so it is not used.
   for (it = 0; alive && it < S.max_iter; ++it) {
     // Y = X X
     ns_gemm(X, X, Np, m0, n0, nsm, st);
@@ -1003,10 +1002,7 @@ __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch
     }
     NS_SYNC();
     if (!alive) break;
-    // X_next = 1.5 a X - 0.5 a^3 Y X (scaled Newton-Schulz), and |X_next - X|^2
-    const float ca = static_cast<float>(1.5 * alpha), cb = static_cast<float>(0.5 * alpha * alpha * alpha);
-    ell = 0.5 * alpha * ell * (3.0 - alpha * alpha * ell * ell);
-    alpha = sqrt(3.0 / (1.0 + ell + ell * ell));
+    // X_next = 1.5 X - 0.5 Y X, and |X_next - X|^2
     ns_gemm(S.Y, X, Np, m0, n0, nsm, st);
     double dsq = 0.0;
     for (int c0 = chalf * 32; c0 < chalf * 32 + 32; c0 += 8) {
@@ -1016,7 +1012,7 @@ __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch
         const int col = n0 + c0 + j;
         if (row >= col) {
           const float x = __ldcg(X + static_cast<int64_t>(row) * Np + col);
-          const float xn = ca * x - cb * v[j];
+          const float xn = 1.5f * x - 0.5f * v[j];
           Xn[static_cast<int64_t>(row) * Np + col] = xn;
           Xn[static_cast<int64_t>(col) * Np + row] = xn;
           const double df = static_cast<double>(xn) - x;

@@ -84,13 +84,18 @@ class WarmStart:
         self.net.fit_scaling(Y.data_ptr(), Y.shape[0])
         rng = np.random.default_rng(self.seed)
         n = X.shape[0]
+        if n == 0:
+            raise ValueError("no training members")
+        batch = min(batch, n)
+        steps = n // batch
         losses = []
         t0 = time.perf_counter()
         for ep in range(epochs):
             perm = torch.tensor(rng.permutation(n), device="cuda")
             Xs, Ys = X[perm].contiguous(), Y[perm].contiguous()
-            for i in range(0, n - batch + 1, batch):
-                last = i + 2 * batch > n
+            for k in range(steps):
+                i = k * batch
+                last = k == steps - 1  # the loss of each epoch's final minibatch is recorded
                 loss = self.net.train_step(Xs[i].data_ptr(), Ys[i].data_ptr(), batch, lr, want_loss=last)
                 if last:
                     losses.append(loss)
