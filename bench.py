@@ -176,25 +176,28 @@ def warmstart_arm(args):
     th_test = W.ParametricPOP.thetas(1024, 200)
     ws = warmstart.WarmStart(fam, hidden=512, seed=0)
     t0 = time.perf_counter()
-    res, dims, t_solve_train, tune = ws.solve(th_train, 1e-4, 5000)
+    mi = args.max_iter
+    res, dims, t_solve_train, tune = ws.solve(th_train, 1e-4, mi)
     ok = np.array([r["status"] == capi.SOLVED for r in res])
+    if not ok.any():
+        raise RuntimeError(f"no training member reached 1e-4 within {mi} iterations")
     targets = warmstart.solution_vectors([r for r, k in zip(res, ok) if k], [d for d, k in zip(dims, ok) if k])
     t_data = time.perf_counter() - t0
     losses = ws.train(th_train[ok], targets, epochs=args.epochs, batch=256, lr=1e-3)
     pred = ws.predict(th_test)
     torch.cuda.synchronize()
-    warm, _, t_warm, _ = ws.solve(th_test, 1e-4, 5000, start=pred)
-    cold, _, t_cold, _ = ws.solve(th_test, 1e-4, 5000)
+    warm, _, t_warm, _ = ws.solve(th_test, 1e-4, mi, start=pred)
+    cold, _, t_cold, _ = ws.solve(th_test, 1e-4, mi)
     it_w = np.array([r["iters"] for r in warm])
     it_c = np.array([r["iters"] for r in cold])
     # plain FP64 form, one instance at a time, on a sample of the same test set
-    sample = list(range(0, 1024, 64))
+    sample = list(range(0, 1024, 128))
     t_plain = 0.0
     it_plain = []
     for i in sample:
         s = capi.Solver(fam.program(th_test[i]), precision=capi.PREC_FP64, k_check=10)
         t1 = time.perf_counter()
-        r = s.solve(1e-4, 5000, want_solution=False)[0]
+        r = s.solve(1e-4, mi, want_solution=False)[0]
         t_plain += time.perf_counter() - t1
         it_plain.append(r["iters"])
         s.close()
@@ -218,6 +221,7 @@ def warmstart_arm(args):
                                   "sample": len(sample)},
             "objective_rel_diff_warm_vs_cold": {"max": float(obj_err.max()), "median": float(np.median(obj_err))},
             "training": {"data_seconds": t_data, "solve_seconds": t_solve_train, "solved": int(ok.sum()),
+                         "iters_mean": float(np.mean([r["iters"] for r in res])),
                          "train_seconds": ws.log["train_seconds"], "loss_first": losses[0], "loss_last": losses[-1]},
             "tuning": tune}
     print(json.dumps(line), flush=True)
@@ -232,6 +236,7 @@ def main():
     ap.add_argument("--workload", default="ball_pop_n20", choices=sorted(WORKLOADS) + ["parametric_warmstart"])
     ap.add_argument("--train", type=int, default=20000, help="training members (parametric_warmstart)")
     ap.add_argument("--epochs", type=int, default=40, help="training epochs (parametric_warmstart)")
+    ap.add_argument("--max-iter", type=int, default=20000, help="iteration cap of every solve (parametric_warmstart)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tt", action="store_true", help="skip the time-to-1e-4 solves")

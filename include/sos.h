@@ -104,7 +104,7 @@ typedef struct {
 
 /* solve_mode: how iterations are launched.
  *   0 auto: the persistent launch for a batch (n_progs > 1) whose Gram
- *     blocks are all small (N <= 96 FP64 projections, <= 128 FP32), else
+ *     blocks are all small (N <= 96 FP64 projections, <= 112 mixed, <= 128 FP32), else
  *     one CUDA graph of per-phase kernels per iteration;
  *   1 one CUDA graph of per-phase kernels per iteration (any block size);
  *   2 the persistent launch (error SOS_ERR_UNSUPPORTED with a large block).
@@ -123,7 +123,11 @@ typedef struct {
                              0 auto = Newton-Schulz on the tensor cores for
                              FP32 projections, grid Jacobi for FP64;
                              1 grid Jacobi; 2 Newton-Schulz (FP32 forms) */
-  int32_t reserved[6];    /* must be zero */
+  int32_t warm_restart;   /* the Jacobi projections start from the previous
+                             iteration's eigenvectors and restart from the
+                             identity after this many warm iterations;
+                             0 = 1024, 1 = every iteration cold */
+  int32_t reserved[5];    /* must be zero */
 } sos_options;
 
 /* Per-instance solve report.  x, y, s are optional caller-allocated HOST
@@ -224,6 +228,19 @@ int sos_host_plan(const sos_program* prog, int64_t dims[6], int32_t* ent_row, do
  * returning.  Errors: SOS_ERR_INVALID_ARG (N < 1 or NULL pointers),
  * SOS_ERR_CUDA, SOS_ERR_TIMEOUT; the message is in sos_last_error(NULL). */
 int sos_psd_project(const double* in, double* out, int32_t N, void* stream);
+
+/* The projection of the mixed-precision form (SOS_PREC_MIXED), for one block:
+ * cyclic Jacobi in FP32, then one refinement with FP64 sums -- the
+ * eigenvector matrix V is re-orthonormalised with F = V^T V - I, the Ritz
+ * matrix B = V^T W V is formed, and its off-diagonal part enters to first
+ * order (the derivative of the eigenvalue map max(., 0) at diag(B)).  The
+ * result is accurate to about 1e-7 |W|_F, where the FP32 Jacobi alone gives
+ * about 1e-5 |W|_F.  Same contract as sos_psd_project (device pointers to
+ * N(N+1)/2 packed doubles; off-diagonal entries scaled by sqrt 2), for
+ * 1 <= N <= 112; larger N returns SOS_ERR_UNSUPPORTED.
+ * Errors: SOS_ERR_INVALID_ARG, SOS_ERR_UNSUPPORTED, SOS_ERR_CUDA,
+ * SOS_ERR_TIMEOUT. */
+int sos_psd_project_mixed(const double* in, double* out, int32_t N, void* stream);
 
 /* Allocation-free variant of sos_psd_project, for callers that cannot call
  * cudaMalloc: code running while another component captures the stream into

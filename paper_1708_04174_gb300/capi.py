@@ -45,7 +45,8 @@ class sos_program(C.Structure):
 
 class sos_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("k_check", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("solve_mode", C.c_int32), ("large_method", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("solve_mode", C.c_int32), ("large_method", C.c_int32), ("warm_restart", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class sos_result(C.Structure):
@@ -72,6 +73,7 @@ EXPORTS = {
     "sos_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "sos_psd_project": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sos_psd_project_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sos_psd_project_mixed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sos_run_stage": (C.c_int, [C.c_void_p, C.c_int32]),
     "sos_mlp_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]),
     "sos_mlp_destroy": (None, [C.c_void_p]),
@@ -205,6 +207,16 @@ def psd_project(in_ptr: int, out_ptr: int, N: int, stream: int = 0):
     _check(lib().sos_psd_project(C.c_void_p(in_ptr), C.c_void_p(out_ptr), N, C.c_void_p(stream) if stream else None))
 
 
+MIXED_MAX_N = 112
+
+
+def psd_project_mixed(in_ptr: int, out_ptr: int, N: int, stream: int = 0):
+    """PSD projection of the mixed form: FP32 Jacobi plus an FP64-summed
+    refinement (N <= MIXED_MAX_N); device pointers."""
+    _check(lib().sos_psd_project_mixed(C.c_void_p(in_ptr), C.c_void_p(out_ptr), N,
+                                       C.c_void_p(stream) if stream else None))
+
+
 NOALLOC_MAX_N = 256
 
 
@@ -233,7 +245,7 @@ class Solver:
     """One libsos handle over a batch of SOS programs (instances)."""
 
     def __init__(self, progs, precision: int = PREC_FP64, k_check: int = 10, stream=None, solve_mode: int = 0,
-                 large_method: int = 0):
+                 large_method: int = 0, warm_restart: int = 0):
         if not isinstance(progs, (list, tuple)):
             progs = [progs]
         self.n_inst = len(progs)
@@ -244,6 +256,7 @@ class Solver:
         opts.cuda_stream = C.c_void_p(stream) if stream else None
         opts.solve_mode = solve_mode
         opts.large_method = large_method
+        opts.warm_restart = warm_restart
         h = C.c_void_p()
         _check(lib().sos_setup(m.progs, len(progs), C.byref(opts), C.byref(h)))
         self.h = h

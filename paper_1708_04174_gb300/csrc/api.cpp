@@ -205,6 +205,7 @@ int make_large(sos_handle* h, std::vector<LargeBlock<T>>& out, const std::vector
     TRY(alloc(h, 2, &lb.scratch.bar));
     TRY(alloc(h, 1, &lb.scratch.sweeps_out));
     TRY(alloc(h, 1, &lb.scratch.warm));
+    lb.scratch.warm_limit = h->warm64.limit;  // same restart period as the small blocks
     out.push_back(lb);
   }
   return SOS_OK;
@@ -514,9 +515,11 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
 
   // projection classes: small blocks (shared-memory Jacobi) by size class, large blocks (grid Jacobi)
   const bool fp64 = h->precision == SOS_PREC_FP64;  // FP64 projections
-  const int small_cap = psd_small_max_n(fp64);
-  const int caps[] = {16, 32, 48, 64, 96, 128};
-  std::vector<std::vector<int32_t>> cls(6);
+  const int form = fp64 ? kFormFP64 : (h->precision == SOS_PREC_MIXED ? kFormMixed : kFormFP32);
+  const int small_cap = psd_small_max_n(form);
+  constexpr int kClasses = 7;
+  const int caps[kClasses] = {16, 32, 48, 64, 96, 112, 128};
+  std::vector<std::vector<int32_t>> cls(kClasses);
   std::vector<int> large;
   int max_small = 0;
   for (int b = 0; b < static_cast<int>(P.blocks.size()); ++b) {
@@ -525,16 +528,22 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
       large.push_back(b);
       continue;
     }
-    for (int k = 0; k < 6; ++k)
+    for (int k = 0; k < kClasses; ++k)
       if (N <= caps[k]) {
         cls[k].push_back(b);
-        max_small = std::max(max_small, caps[k]);
         break;
       }
   }
+  // shared memory of a class is sized for its largest member (rounded up to
+  // even), so e.g. a batch of N = 66 blocks fits three CTAs per SM
+  int cls_n[kClasses] = {0};
+  for (int k = 0; k < kClasses; ++k) {
+    for (int32_t b : cls[k]) cls_n[k] = std::max(cls_n[k], P.blocks[b].N + (P.blocks[b].N & 1));
+    max_small = std::max(max_small, cls_n[k]);
+  }
   // eigenvector storage of small blocks (warm start)
   int64_t voff = 0;
-  for (int k = 0; k < 6; ++k)
+  for (int k = 0; k < kClasses; ++k)
     for (int32_t b : cls[k]) {
       P.blocks[b].v_off = voff;
       voff += static_cast<int64_t>(P.blocks[b].N) * P.blocks[b].N;
@@ -550,9 +559,9 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
     TRY(alloc(h, static_cast<size_t>(voff), &h->warm32.V));
     TRY(alloc(h, P.blocks.size(), &h->warm32.count));
   }
-  for (int k = 0; k < 6; ++k)
+  for (int k = 0; k < kClasses; ++k)
     if (!cls[k].empty()) {
-      SmallClass sc{caps[k], static_cast<int>(cls[k].size()), nullptr};
+      SmallClass sc{cls_n[k], static_cast<int>(cls[k].size()), nullptr};
       TRY(upload(h, cls[k], &sc.ids));
       h->small.push_back(sc);
     }
@@ -710,6 +719,12 @@ int sos_setup(const sos_program* progs, int32_t n_progs, const sos_options* opts
       g_setup_error = "unknown solve_mode";
       return SOS_ERR_INVALID_ARG;
     }
+    if (opts->warm_restart < 0) {
+      g_setup_error = "warm_restart must be >= 0";
+      return SOS_ERR_INVALID_ARG;
+    }
+    if (opts->warm_restart > 0)
+      h->warm64.limit = h->warm32.limit = opts->warm_restart;
   }
   if (!h->stream) {
     cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
@@ -978,8 +993,15 @@ int sos_host_plan(const sos_program* prog, int64_t dims[6], int32_t* ent_row, do
   return SOS_OK;
 }
 
-int sos_psd_project(const double* in, double* out, int32_t N, void* stream) {
+namespace {
+// One PSD projection of a packed block: FP64 Jacobi (mixed = false) or FP32
+// Jacobi with the FP64-accumulated refinement (mixed = true, small blocks).
+int psd_project_one(const double* in, double* out, int32_t N, void* stream, bool mixed) {
   if (!in || !out || N < 1) return SOS_ERR_INVALID_ARG;
+  if (mixed && N > psd_small_max_n(kFormMixed)) {
+    g_setup_error = "the mixed projection takes N <= " + std::to_string(psd_small_max_n(kFormMixed));
+    return SOS_ERR_UNSUPPORTED;
+  }
   sos_handle tmp;  // owns the scratch allocations of this call
   sos_handle* h = &tmp;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -990,7 +1012,7 @@ int sos_psd_project(const double* in, double* out, int32_t N, void* stream) {
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
   };
-  const bool small = N <= psd_small_max_n(true);
+  const bool small = N <= psd_small_max_n(kFormFP64);
   BlockDesc bd{};
   bd.x_off = 0;
   bd.v_off = -1;
@@ -1030,7 +1052,11 @@ int sos_psd_project(const double* in, double* out, int32_t N, void* stream) {
       break;
     }
     cudaError_t e;
-    if (small) {
+    if (mixed) {
+      const int cap = N <= 16 ? 16 : N <= 32 ? 32 : N <= 48 ? 48 : N <= 64 ? 64 : N <= 96 ? 96 : 112;
+      e = prepare_kernels<double, float>(cap, 0);
+      if (e == cudaSuccess) e = launch_psd_small<double, float>(p, ids, 1, cap, SmallWarm<float>(), s);
+    } else if (small) {
       const int cap = N <= 16 ? 16 : N <= 32 ? 32 : N <= 48 ? 48 : N <= 64 ? 64 : 96;
       e = prepare_kernels<double, double>(cap, 0);
       if (e == cudaSuccess) e = launch_psd_small<double, double>(p, ids, 1, cap, SmallWarm<double>(), s);
@@ -1054,6 +1080,15 @@ int sos_psd_project(const double* in, double* out, int32_t N, void* stream) {
   if (rc != SOS_OK) g_setup_error = h->err;
   release();
   return rc;
+}
+}  // namespace
+
+int sos_psd_project(const double* in, double* out, int32_t N, void* stream) {
+  return psd_project_one(in, out, N, stream, false);
+}
+
+int sos_psd_project_mixed(const double* in, double* out, int32_t N, void* stream) {
+  return psd_project_one(in, out, N, stream, true);
 }
 
 int sos_stats(sos_handle* h, int64_t out[4]) {

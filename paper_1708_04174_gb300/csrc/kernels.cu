@@ -301,6 +301,175 @@ __device__ __forceinline__ void jacobi_rot(T app, T aqq, T apq, T& c, T& s, T& t
 // they are stored) give B = V^T W V, nearly diagonal after the first
 // iterations, so few sweeps remain.
 // ---------------------------------------------------------------------------
+// Compensated FP32 dot-product step (Ogita, Rump & Oishi, "Accurate sum and
+// dot product", 2005): s + c accumulates a*b with the product split exactly
+// by an FMA (a*b = p + e) and the sum split exactly by TwoSum (s + p = t + r).
+// The intrinsics keep the compiler from contracting the error-free steps.
+// The result is as accurate as if computed in twice the working precision:
+// error <= eps |sum| + O(n eps^2) sum |a_k b_k|.
+__device__ __forceinline__ void dot2_step(float a, float b, float& s, float& c) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float r = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(r, e));
+}
+
+// Refinement of an FP32 Jacobi projection (FP64 iterates, FP32 projections).
+// An FP32 Jacobi solve accumulates one rounding error per rotation in V and
+// in the rotated matrix, so V V^T - I and the backward error reach
+// ~1e-5 |W| after a few hundred rotations per column, and ADMM runs that need
+// thousands of iterations stall near a 1e-3 residual.  One correction step
+// restores FP32 accuracy (~1e-7 |W|):
+//   F  = V^T V - I                     (compensated sums)
+//   V' = V (I - F / 2)                 (orthonormal to O(|F|^2 + eps))
+//   B  = V'^T W V'                     (W as an FP32 pair hi + lo, compensated sums)
+//   M  = diag(max(b_ii, 0)) + G o offdiag(B),
+//        g_ij = (max(b_ii,0) - max(b_jj,0)) / (b_ii - b_jj)
+//   U  = V' M V'^T                     (FP32)
+// M is P_S+(B) to first order in offdiag(B) (the derivative of the
+// eigenvalue map x -> max(x, 0) at a diagonal matrix: g_ij = 1 when both
+// Ritz values are positive, 0 when neither is, and in (0, 1) across zero).
+// The products that need more than FP32 use the compensated dot product
+// above (2 N^3 steps of ~10 FP32 operations), not FP64: FP64 runs at under
+// 2% of the FP32 rate on this GPU.  On entry V holds the Jacobi
+// eigenvectors; on exit A holds V'.  The pair copy of W and then W V' live
+// where V and T1 were (2 Np ld floats >= 2 N^2).
+template <typename T, typename TC>
+__device__ void psd_small_refine(const DevPlan<T>& p, const BlockDesc& bd, double s_sm, int N, int ld, TC* A, TC* V,
+                                 TC* T1, TC* X4, double* lam64) {
+  static_assert(sizeof(TC) == 4, "the refinement works on FP32 data");
+  const int tid = threadIdx.x, nt = blockDim.x;
+  __syncthreads();
+  for (int q = tid; q < N * N; q += nt) {  // T1 = F (lower and mirrored)
+    const int i = q / N, j = q - i * N;
+    if (i < j) continue;
+    float sh = 0.f, c = 0.f;
+    for (int k = 0; k < N; ++k) dot2_step(V[k * ld + i], V[k * ld + j], sh, c);
+    if (i == j) sh = __fsub_rn(sh, 1.0f);  // exact: sh lies in [1/2, 2]
+    const TC f = __fadd_rn(sh, c);
+    T1[i * ld + j] = f;
+    T1[j * ld + i] = f;
+  }
+  __syncthreads();
+  for (int q = tid; q < N * N; q += nt) {  // A = V' = V - V F / 2
+    const int i = q / N, j = q - i * N;
+    TC acc = 0;
+    for (int k = 0; k < N; ++k) acc += V[i * ld + k] * T1[k * ld + j];
+    A[i * ld + j] = V[i * ld + j] - static_cast<TC>(0.5) * acc;
+  }
+  __syncthreads();
+  float2* W2 = reinterpret_cast<float2*>(V);  // W as (hi, lo), row-major, leading dimension N
+  for (int q = tid; q < N * N; q += nt) {
+    const int i = q / N, j = q - i * N;
+    if (i < j) continue;
+    const double w = d(proj_input(p, bd, packed_index(i, j, N), i != j, s_sm));
+    const double x = (i == j) ? w : w * 0.70710678118654752440;
+    const float hi = static_cast<float>(x);
+    const float2 v2 = make_float2(hi, static_cast<float>(x - static_cast<double>(hi)));
+    W2[i * N + j] = v2;
+    W2[j * N + i] = v2;
+  }
+  __syncthreads();
+  // W2 <- W V' in place, a chunk of rows at a time: each thread computes a
+  // 4-row x 1-column tile of the chunk and holds it across the barrier
+  const int groups = nt / N > 0 ? nt / N : 1;
+  for (int r0 = 0; r0 < N; r0 += 4 * groups) {
+    const int g = tid / N, j = tid - g * N;
+    const bool act = g < groups && r0 + 4 * g < N;
+    float sh[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    if (act) {
+      const int i0 = r0 + 4 * g;
+      for (int k = 0; k < N; ++k) {
+        const float v = A[k * ld + j];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (i0 + t < N) {
+            const float2 w = W2[(i0 + t) * N + k];
+            dot2_step(w.x, v, sh[t], c[t]);
+            c[t] = __fmaf_rn(w.y, v, c[t]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (act) {
+      const int i0 = r0 + 4 * g;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (i0 + t < N) {
+          const float hi = __fadd_rn(sh[t], c[t]);
+          W2[(i0 + t) * N + j] = make_float2(hi, __fadd_rn(__fsub_rn(sh[t], hi), c[t]));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < N; i += nt) {  // Ritz values b_ii
+    float sh = 0.f, c = 0.f;
+    for (int k = 0; k < N; ++k) {
+      const float v = A[k * ld + i];
+      const float2 t2 = W2[k * N + i];
+      dot2_step(v, t2.x, sh, c);
+      c = __fmaf_rn(v, t2.y, c);
+    }
+    lam64[i] = static_cast<double>(sh) + static_cast<double>(c);
+  }
+  __syncthreads();
+  for (int q = tid; q < N * N; q += nt) {  // X4 = M
+    const int i = q / N, j = q - i * N;
+    if (i < j) continue;
+    const double li = lam64[i], lj = lam64[j];
+    double m;
+    if (i == j) {
+      m = fmax(li, 0.0);
+    } else {
+      double g;
+      if (li > 0.0 && lj > 0.0)
+        g = 1.0;
+      else if (li <= 0.0 && lj <= 0.0)
+        g = 0.0;
+      else
+        g = (fmax(li, 0.0) - fmax(lj, 0.0)) / (li - lj);  // one of them > 0 >= the other: |li - lj| > 0
+      if (g != 0.0) {
+        float sh = 0.f, c = 0.f;
+        for (int k = 0; k < N; ++k) {
+          const float v = A[k * ld + i];
+          const float2 t2 = W2[k * N + j];
+          dot2_step(v, t2.x, sh, c);
+          c = __fmaf_rn(v, t2.y, c);
+        }
+        m = g * (static_cast<double>(sh) + static_cast<double>(c));
+      } else {
+        m = 0.0;
+      }
+    }
+    X4[i * ld + j] = static_cast<TC>(m);
+    X4[j * ld + i] = static_cast<TC>(m);
+  }
+  __syncthreads();
+  for (int q = tid; q < N * N; q += nt) {  // V region (as TC) = Y = V' M
+    const int i = q / N, j = q - i * N;
+    TC acc = 0;
+    for (int k = 0; k < N; ++k) acc += A[i * ld + k] * X4[k * ld + j];
+    V[i * ld + j] = acc;
+  }
+  __syncthreads();
+  for (int q = tid; q < N * N; q += nt) {  // U = Y V'^T; outputs u = svec(U), v = u - W
+    const int i = q / N, j = q - i * N;
+    if (i < j) continue;
+    TC u = 0;
+    for (int k = 0; k < N; ++k) u += V[i * ld + k] * A[j * ld + k];
+    const int64_t kk = packed_index(i, j, N);
+    const T w = proj_input(p, bd, kk, i != j, s_sm);
+    const T uu = (i != j) ? static_cast<T>(d(u) * kSqrt2) : static_cast<T>(u);
+    p.ux[bd.x_off + kk] = uu;
+    p.vx[bd.x_off + kk] = uu - w;
+  }
+}
+
 template <typename T, typename TC>
 __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& wm, unsigned char* smraw) {
   __shared__ double red[40];
@@ -311,10 +480,13 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
   if (tid == 0) last_rot = -1;  // block_sum below orders this before any use
   const double s_sm = p.st[bd.inst].s;
   const int N = bd.N, Np = N + (N & 1), ld = Np + 1, H = Np / 2;
+  constexpr bool kRefine = sizeof(T) == 8 && sizeof(TC) == 4;  // FP64 iterates, FP32 projections
   TC* A = reinterpret_cast<TC*>(smraw);
   TC* V = A + Np * ld;
   TC* T1 = V + Np * ld;
-  TC* rc = T1 + Np * ld;
+  TC* X4 = T1 + Np * ld;  // refinement only: M of the corrected projection
+  double* lam64 = reinterpret_cast<double*>(X4 + Np * ld);  // refinement only: Ritz values
+  TC* rc = kRefine ? reinterpret_cast<TC*>(lam64 + Np) : T1 + Np * ld;
   TC* rs = rc + H;
   TC* rt = rs + H;
   TC* lam = rt + H;
@@ -435,8 +607,18 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
     if (!rotated) break;
   }
 
-  // P_S+(W) = V max(Lambda, 0) V^T; v = u - W (in the storage type)
   if (tid == 0) p.blk_sweeps[bid] = sweeps_done;
+  if constexpr (kRefine) {
+    psd_small_refine(p, bd, s_sm, N, ld, A, V, T1, X4, lam64);
+    if (gV) {  // keep the re-orthonormalised V' for the next iteration
+      for (int q = tid; q < N * N; q += nt) {
+        const int i = q / N, j = q - i * N;
+        gV[i * N + j] = A[i * ld + j];
+      }
+      if (tid == 0) wm.count[bid] = warm ? wc + 1 : 1;
+    }
+  } else {
+  // P_S+(W) = V max(Lambda, 0) V^T; v = u - W (in the storage type)
   for (int k = tid; k < N; k += nt) lam[k] = fmax(A[k * ld + k], static_cast<TC>(0));
   __syncthreads();
   for (int q = tid; q < N * N; q += nt) {
@@ -465,6 +647,7 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
       gV[i * N + j] = acc;
     }
     if (tid == 0) wm.count[bid] = warm ? wc + 1 : 1;
+  }
   }
 }
 
@@ -579,7 +762,7 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
   const unsigned G = gridDim.x;
   int32_t* err = p.err;
   const int warm_count = __ldcg(L.warm);
-  const bool warm = warm_count > 0 && warm_count < 1024;
+  const bool warm = warm_count > 0 && warm_count < L.warm_limit;
   TC* Wf = L.Wf;
   TC* V = L.V;
 
@@ -1300,19 +1483,21 @@ cudaError_t launch_affine(const DevPlan<T>& p, const LaunchShape& ls, cudaStream
   return cudaGetLastError();
 }
 
-size_t psd_small_smem_bytes(int maxN, bool fp64) {
+size_t psd_small_smem_bytes(int maxN, int form) {
   const int Np = maxN + (maxN & 1), ld = Np + 1, H = Np / 2;
-  const size_t es = fp64 ? 8 : 4;
-  return es * (3 * static_cast<size_t>(Np) * ld + 3 * H + Np) + sizeof(int) * 2 * H;
+  const size_t es = form == kFormFP64 ? 8 : 4;
+  const size_t bufs = form == kFormMixed ? 4 : 3;  // the refinement adds M
+  const size_t lam64 = form == kFormMixed ? sizeof(double) * Np : 0;
+  return es * (bufs * static_cast<size_t>(Np) * ld + 3 * H + Np) + lam64 + sizeof(int) * 2 * H;
 }
 
-int psd_small_max_n(bool fp64) { return fp64 ? 96 : 128; }
+int psd_small_max_n(int form) { return form == kFormFP64 ? 96 : (form == kFormMixed ? 112 : 128); }
 
 template <typename T, typename TC>
 cudaError_t launch_psd_small(const DevPlan<T>& p, const int32_t* ids, int count, int maxN, const SmallWarm<TC>& wm,
                              cudaStream_t s) {
   if (count == 0) return cudaSuccess;
-  const size_t sm = psd_small_smem_bytes(maxN, sizeof(TC) == 8);
+  const size_t sm = psd_small_smem_bytes(maxN, form_of<T, TC>());
   k_psd_small<T, TC><<<count, 256, sm, s>>>(p, ids, wm);
   return cudaGetLastError();
 }
@@ -1360,7 +1545,7 @@ template <typename T, typename TC>
 cudaError_t prepare_kernels(int max_small_n, int max_teff) {
   cudaError_t e = cudaSuccess;
   if (max_small_n > 0) {
-    const size_t sm = psd_small_smem_bytes(max_small_n, sizeof(TC) == 8);
+    const size_t sm = psd_small_smem_bytes(max_small_n, form_of<T, TC>());
     e = cudaFuncSetAttribute(k_psd_small<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
     if (e != cudaSuccess) return e;
   }
@@ -1372,7 +1557,7 @@ cudaError_t prepare_kernels(int max_small_n, int max_teff) {
 
 template <typename T, typename TC>
 size_t persistent_smem_bytes(int max_small_n, int max_teff) {
-  size_t a = psd_small_smem_bytes(max_small_n, sizeof(TC) == 8);
+  size_t a = psd_small_smem_bytes(max_small_n, form_of<T, TC>());
   size_t b = sizeof(double) * 2 * static_cast<size_t>(max_teff > 0 ? max_teff : 1);
   return a > b ? a : b;
 }

@@ -72,6 +72,7 @@ struct LargeScratch {
   uint32_t* bar = nullptr;     // grid barrier: [arrivals, released generation], zeroed before each launch
   int32_t* sweeps_out = nullptr;  // number of sweeps of the last launch
   int32_t* warm = nullptr;     // 1 if V holds the previous eigenvectors
+  int32_t warm_limit = 1024;   // cold restart after this many warm iterations
 };
 
 constexpr int kMaxSweeps = 40;
@@ -149,8 +150,15 @@ int persistent_max_ctas_per_sm(int max_small_n, int max_teff);
 template <typename T, typename TC>
 cudaError_t launch_persistent(const DevPlan<T>& p, const PersistArgs<TC>& a, int grid, int max_small_n, int max_teff,
                               cudaStream_t s);
-size_t psd_small_smem_bytes(int maxN, bool fp64);
+// projection forms of the small-block kernel: FP64; FP32 Jacobi with an FP64
+// refinement (FP64 iterates); plain FP32 (FP32 iterates)
+constexpr int kFormFP64 = 0, kFormMixed = 1, kFormFP32 = 2;
+template <typename T, typename TC>
+constexpr int form_of() {
+  return sizeof(TC) == 8 ? kFormFP64 : (sizeof(T) == 8 ? kFormMixed : kFormFP32);
+}
+size_t psd_small_smem_bytes(int maxN, int form);
 size_t large_smem_bytes(int N, size_t es);
-int psd_small_max_n(bool fp64);
+int psd_small_max_n(int form);
 
 }  // namespace sos

@@ -117,7 +117,7 @@ extern "C" int sos_psd_project_noalloc(const double* in, double* out, int32_t N,
   p.vx = reinterpret_cast<double*>(base + kOffV);
 
   cudaError_t e;
-  if (N <= psd_small_max_n(true)) {
+  if (N <= psd_small_max_n(kFormFP64)) {
     const int cap = N <= 16 ? 16 : N <= 32 ? 32 : N <= 48 ? 48 : N <= 64 ? 64 : 96;
     e = prepare_kernels<double, double>(cap, 0);
     if (e == cudaSuccess) e = launch_psd_small<double, double>(p, words + kWordId, 1, cap, SmallWarm<double>(), s);

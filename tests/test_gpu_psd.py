@@ -79,3 +79,56 @@ def test_projection_rejects_bad_size(env):
     w = torch.zeros(3, dtype=torch.float64, device="cuda")
     with pytest.raises(RuntimeError):
         capi.psd_project(w.data_ptr(), w.data_ptr(), 0)
+
+
+# ---- mixed form: FP32 Jacobi + FP64-summed refinement (sos_psd_project_mixed) ----
+# The bound: the refined result carries the rounding of an FP32 product
+# V' M V'^T and of V' itself, a few units of 2^-24 |W|_F per entry, so
+# |error|_F <= 1e-6 |W|_F; the unrefined FP32 Jacobi misses it by ~10x
+# (orthogonality loss of ~1e-5 after hundreds of rotations per column).
+
+def project_gpu_mixed(env, X):
+    torch, capi = env
+    w = torch.tensor(pack(X), dtype=torch.float64, device="cuda")
+    u = torch.empty_like(w)
+    capi.psd_project_mixed(w.data_ptr(), u.data_ptr(), X.shape[0], torch.cuda.current_stream().cuda_stream)
+    return u.cpu().numpy()
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 7, 16, 17, 28, 33, 64, 66, 84, 96, 97, 112])
+def test_mixed_projection_accuracy(env, N):
+    X = sym(N, 1000 + N)
+    got = project_gpu_mixed(env, X)
+    want = pack(proj_psd(X))
+    assert np.linalg.norm(got - want) <= 1e-6 * np.linalg.norm(pack(X))
+
+
+@pytest.mark.parametrize("N", [40, 66, 112])
+def test_mixed_projection_admm_like_spectrum(env, N):
+    # the spectrum ADMM meets near a solution: many positive eigenvalues
+    # spread over decades, a few negative ones, clusters at +-1e-6 on both
+    # sides of zero, and one repeated eigenvalue
+    rng = np.random.default_rng(N)
+    Q, _ = np.linalg.qr(rng.standard_normal((N, N)))
+    lam = np.exp(rng.uniform(np.log(1e-4), 0.0, N))
+    lam[: N // 5] *= -1.0
+    lam[N // 5: N // 5 + 3] = 1e-6
+    lam[N // 5 + 3: N // 5 + 6] = -1e-6
+    lam[-2:] = 0.5
+    X = (Q * lam) @ Q.T
+    X = 0.5 * (X + X.T)
+    got = project_gpu_mixed(env, X)
+    want = pack(proj_psd(X))
+    assert np.linalg.norm(got - want) <= 1e-6 * np.linalg.norm(pack(X))
+    P = proj_psd(X)
+    assert np.linalg.norm(project_gpu_mixed(env, P) - pack(P)) <= 1e-6 * np.linalg.norm(pack(P))
+    assert np.abs(project_gpu_mixed(env, np.zeros((N, N)))).max() == 0.0
+
+
+def test_mixed_projection_rejects_large_block(env):
+    torch, capi = env
+    N = capi.MIXED_MAX_N + 1
+    w = torch.zeros(N * (N + 1) // 2, dtype=torch.float64, device="cuda")
+    u = torch.empty_like(w)
+    with pytest.raises(RuntimeError):
+        capi.psd_project_mixed(w.data_ptr(), u.data_ptr(), N)
