@@ -177,10 +177,10 @@ def warmstart_arm(args):
     ws = warmstart.WarmStart(fam, hidden=512, seed=0)
     t0 = time.perf_counter()
     mi = args.max_iter
-    res, dims, t_solve_train, tune = ws.solve(th_train, 1e-4, mi)
+    res, dims, t_solve_train, tune = ws.solve(th_train, args.train_tol, mi)
     ok = np.array([r["status"] == capi.SOLVED for r in res])
     if not ok.any():
-        raise RuntimeError(f"no training member reached 1e-4 within {mi} iterations")
+        raise RuntimeError(f"no training member reached {args.train_tol} within {mi} iterations")
     targets = warmstart.solution_vectors([r for r, k in zip(res, ok) if k], [d for d, k in zip(dims, ok) if k])
     t_data = time.perf_counter() - t0
     losses = ws.train(th_train[ok], targets, epochs=args.epochs, batch=256, lr=1e-3)
@@ -190,8 +190,22 @@ def warmstart_arm(args):
     cold, _, t_cold, _ = ws.solve(th_test, 1e-4, mi)
     it_w = np.array([r["iters"] for r in warm])
     it_c = np.array([r["iters"] for r in cold])
+    # accuracy of the prediction against the cold-start solutions
+    sol_c = warmstart.solution_vectors(cold, ws.last_dims)
+    pred_err = np.linalg.norm(pred - sol_c, axis=1) / np.maximum(np.linalg.norm(sol_c, axis=1), 1e-30)
+    # what a better predictor could gain: starts at the cold-start solution
+    # itself and at that solution with 5% relative Gaussian noise
+    rng = np.random.default_rng(0)
+    noisy = sol_c + 0.05 * np.linalg.norm(sol_c, axis=1, keepdims=True) / np.sqrt(sol_c.shape[1]) * \
+        rng.standard_normal(sol_c.shape)
+    bounds = {}
+    for name, start in (("exact_solution", sol_c), ("solution_5pct_noise", noisy)):
+        rb, _, tb, _ = ws.solve(th_test, 1e-4, mi, start=start.astype(np.float32))
+        ib = np.array([r["iters"] for r in rb])
+        bounds[name] = {"seconds": tb, "iters_mean": float(ib.mean()), "iters_median": float(np.median(ib)),
+                        "solved": int(sum(r["status"] == capi.SOLVED for r in rb))}
     # plain FP64 form, one instance at a time, on a sample of the same test set
-    sample = list(range(0, 1024, 128))
+    sample = list(range(0, 1024, 256))
     t_plain = 0.0
     it_plain = []
     for i in sample:
@@ -213,14 +227,19 @@ def warmstart_arm(args):
                        "train": int(args.train), "test": 1024, "mlp": "16-512-512-5425", "epochs": args.epochs},
             "speedup_vs_plain_fp64": per_plain / per_warm,
             "speedup_vs_cold_batched": t_cold / t_warm,
-            "warm": {"seconds": t_warm, "iters_mean": float(it_w.mean()), "iters_max": int(it_w.max()),
+            "warm": {"seconds": t_warm, "iters_mean": float(it_w.mean()), "iters_median": float(np.median(it_w)),
+                     "iters_max": int(it_w.max()),
                      "solved": int(sum(r["status"] == capi.SOLVED for r in warm))},
-            "cold_batched": {"seconds": t_cold, "iters_mean": float(it_c.mean()), "iters_max": int(it_c.max()),
+            "cold_batched": {"seconds": t_cold, "iters_mean": float(it_c.mean()), "iters_median": float(np.median(it_c)),
+                             "iters_max": int(it_c.max()),
                              "solved": int(sum(r["status"] == capi.SOLVED for r in cold))},
             "plain_fp64_single": {"seconds_per_instance": per_plain, "iters_mean": float(np.mean(it_plain)),
                                   "sample": len(sample)},
             "objective_rel_diff_warm_vs_cold": {"max": float(obj_err.max()), "median": float(np.median(obj_err))},
+            "prediction_rel_err": {"median": float(np.median(pred_err)), "p90": float(np.percentile(pred_err, 90))},
+            "start_bounds": bounds,
             "training": {"data_seconds": t_data, "solve_seconds": t_solve_train, "solved": int(ok.sum()),
+                         "tol": args.train_tol,
                          "iters_mean": float(np.mean([r["iters"] for r in res])),
                          "train_seconds": ws.log["train_seconds"], "loss_first": losses[0], "loss_last": losses[-1]},
             "tuning": tune}
@@ -235,8 +254,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="ball_pop_n20", choices=sorted(WORKLOADS) + ["parametric_warmstart"])
     ap.add_argument("--train", type=int, default=20000, help="training members (parametric_warmstart)")
-    ap.add_argument("--epochs", type=int, default=40, help="training epochs (parametric_warmstart)")
+    ap.add_argument("--epochs", type=int, default=200, help="training epochs (parametric_warmstart)")
     ap.add_argument("--max-iter", type=int, default=20000, help="iteration cap of every solve (parametric_warmstart)")
+    ap.add_argument("--train-tol", type=float, default=1e-3, help="tolerance of the training solves (parametric_warmstart)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tt", action="store_true", help="skip the time-to-1e-4 solves")

@@ -127,7 +127,10 @@ typedef struct {
                              iteration's eigenvectors and restart from the
                              identity after this many warm iterations;
                              0 = 1024, 1 = every iteration cold */
-  int32_t reserved[5];    /* must be zero */
+  int32_t reserved0;      /* must be zero */
+  double infeas_tol;      /* tolerance of the infeasibility certificates of
+                             sos_solve, independent of its tol; 0 = 1e-7 */
+  int32_t reserved[2];    /* must be zero */
 } sos_options;
 
 /* Per-instance solve report.  x, y, s are optional caller-allocated HOST
@@ -180,9 +183,13 @@ int sos_dims(const sos_handle* h, int32_t inst, int64_t dims[6]);
  * running instance is checked (tau > 1e-12 (kappa + 1)):
  *   res_primal = |A xi - b| / (1 + |b|),  res_dual = |A^T y + z - c| / (1 + |c|),
  *   gap = |c^T xi - b^T y| / (1 + |c^T xi| + |b^T y|),
- * SOLVED when all three are <= tol; PRIMAL_INFEASIBLE when b^T u_y > 0 and
- * |A^T u_y + v_z| / b^T u_y <= tol; DUAL_INFEASIBLE when c^T u_xi < 0 and
- * |A u_xi| / -c^T u_xi <= tol; NUMERICAL on a non-finite iterate.  A
+ * SOLVED when all three are <= tol; while kappa > tau (the embedding's
+ * infeasibility branch, eq. (18)-(19)) PRIMAL_INFEASIBLE when b^T u_y > 0 and
+ * |A^T u_y + v_z| / b^T u_y <= infeas_tol, DUAL_INFEASIBLE when c^T u_xi < 0
+ * and |A u_xi| / -c^T u_xi <= infeas_tol (sos_options.infeas_tol, default
+ * 1e-7: with the residual tolerance, a feasible program whose optimal value
+ * exceeds |c| / tol passes the primal test during the iteration);
+ * NUMERICAL on a non-finite iterate.  A
  * terminated instance is frozen (its iterate no longer changes).
  * results: array of n_progs reports (may be NULL).  Returns SOS_OK or an
  * error code (SOS_ERR_TIMEOUT if a bounded device wait expired). */

@@ -168,9 +168,10 @@ class Result:
 
 def solve(cd: ConicData, tol: float, max_iter: int, k_check: int = 1,
           u0: Optional[np.ndarray] = None, v0: Optional[np.ndarray] = None,
-          solver: Optional[HSDE] = None) -> Result:
+          solver: Optional[HSDE] = None, infeas_tol: float = 1e-7) -> Result:
     """Iterate eq. (20) until max(rp, rd, gap) <= tol or an infeasibility
-    certificate holds, checking every ``k_check`` iterations."""
+    certificate holds to ``infeas_tol``, checking every ``k_check``
+    iterations."""
     hs = solver or HSDE(cd)
     u, v = (u0.copy(), v0.copy()) if u0 is not None else hs.start()
     hist: List[dict] = []
@@ -186,8 +187,15 @@ def solve(cd: ConicData, tol: float, max_iter: int, k_check: int = 1,
             return Result(NUMERICAL, k, u, v, res, hist)
         if res["res"] <= tol:
             return Result(SOLVED, k, u, v, res, hist)
-        if res["pinf"] <= tol:
-            return Result(PRIMAL_INFEASIBLE, k, u, v, res, hist)
-        if res["dinf"] <= tol:
-            return Result(DUAL_INFEASIBLE, k, u, v, res, hist)
+        # A nonzero solution of the embedding with tau > 0 yields an optimal
+        # pair and one with kappa > 0 a certificate (the classification stated
+        # with eq. (18)-(19)); the certificate tests are taken only while the
+        # iterate leans towards the second case, and to their own tolerance:
+        # a feasible program with b^T y* >= |c| / tol passes the primal test
+        # at the residual tolerance, near its optimum or early on.
+        if res["kappa"] > res["tau"]:
+            if res["pinf"] <= infeas_tol:
+                return Result(PRIMAL_INFEASIBLE, k, u, v, res, hist)
+            if res["dinf"] <= infeas_tol:
+                return Result(DUAL_INFEASIBLE, k, u, v, res, hist)
     return Result(MAX_ITER, max_iter, u, v, res, hist)

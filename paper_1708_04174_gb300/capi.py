@@ -46,7 +46,7 @@ class sos_program(C.Structure):
 class sos_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("k_check", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("solve_mode", C.c_int32), ("large_method", C.c_int32), ("warm_restart", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("reserved0", C.c_int32), ("infeas_tol", C.c_double), ("reserved", C.c_int32 * 2)]
 
 
 class sos_result(C.Structure):
@@ -245,7 +245,7 @@ class Solver:
     """One libsos handle over a batch of SOS programs (instances)."""
 
     def __init__(self, progs, precision: int = PREC_FP64, k_check: int = 10, stream=None, solve_mode: int = 0,
-                 large_method: int = 0, warm_restart: int = 0):
+                 large_method: int = 0, warm_restart: int = 0, infeas_tol: float = 0.0):
         if not isinstance(progs, (list, tuple)):
             progs = [progs]
         self.n_inst = len(progs)
@@ -257,6 +257,7 @@ class Solver:
         opts.solve_mode = solve_mode
         opts.large_method = large_method
         opts.warm_restart = warm_restart
+        opts.infeas_tol = infeas_tol
         h = C.c_void_p()
         _check(lib().sos_setup(m.progs, len(progs), C.byref(opts), C.byref(h)))
         self.h = h

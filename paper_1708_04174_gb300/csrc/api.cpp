@@ -63,6 +63,7 @@ struct sos_handle {
   SmallWarm<float> warm32;
   std::vector<NsBlock> ns_large;  // large blocks projected by Newton-Schulz on the tensor cores
   int32_t large_method = 0;
+  double infeas_tol = 1e-7;   // tolerance of the infeasibility certificates
   int32_t* active = nullptr;  // device
   std::vector<int32_t> active_h;
   std::vector<int32_t> iters_h, status_h;
@@ -296,6 +297,7 @@ PersistArgs<TC> persist_args(sos_handle* h, const SmallWarm<TC>& wm, int32_t max
   a.max_iter = max_iter;
   a.k_check = k_check;
   a.tol = tol;
+  a.infeas_tol = h->infeas_tol;
   a.bar = h->p_bar;
   a.queue = h->p_queue;
   a.active = h->active;
@@ -723,6 +725,11 @@ int sos_setup(const sos_program* progs, int32_t n_progs, const sos_options* opts
       g_setup_error = "warm_restart must be >= 0";
       return SOS_ERR_INVALID_ARG;
     }
+    if (opts->infeas_tol < 0 || opts->reserved0 != 0) {
+      g_setup_error = "infeas_tol must be >= 0 and reserved fields zero";
+      return SOS_ERR_INVALID_ARG;
+    }
+    if (opts->infeas_tol > 0) h->infeas_tol = opts->infeas_tol;
     if (opts->warm_restart > 0)
       h->warm64.limit = h->warm32.limit = opts->warm_restart;
   }
@@ -886,9 +893,9 @@ int sos_solve(sos_handle* h, double tol, int32_t max_iter, sos_result* results) 
         st = SOS_NUMERICAL;
       else if (res <= tol)
         st = SOS_SOLVED;
-      else if (pinf <= tol)
+      else if (r.kappa > r.tau && pinf <= h->infeas_tol)  // an embedding solution with kappa > 0 is a certificate
         st = SOS_PRIMAL_INFEASIBLE;
-      else if (dinf <= tol)
+      else if (r.kappa > r.tau && dinf <= h->infeas_tol)
         st = SOS_DUAL_INFEASIBLE;
       if (st != SOS_RUNNING) {
         h->status_h[i] = st;

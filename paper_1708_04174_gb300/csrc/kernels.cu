@@ -1366,7 +1366,7 @@ __global__ void k_res_inst(DevPlan<T> p) {
 // round-robin over a fixed order (largest first) or from an atomic work queue.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void d_check(const DevPlan<T>& p, int i, int it, double tol, InstReport* rep, int32_t* active,
+__device__ void d_check(const DevPlan<T>& p, int i, int it, double tol, double infeas_tol, InstReport* rep, int32_t* active,
                         int32_t* n_active) {
   if (threadIdx.x != 0 || !active[i]) return;
   const InstInfo in = p.inst[i];
@@ -1389,9 +1389,9 @@ __device__ void d_check(const DevPlan<T>& p, int i, int it, double tol, InstRepo
     st = 5;  // NUMERICAL
   else if (res <= tol)
     st = 1;  // SOLVED
-  else if (pinf <= tol)
+  else if (r.kappa > r.tau && pinf <= infeas_tol)  // certificates only while kappa > tau
     st = 2;  // PRIMAL_INFEASIBLE
-  else if (dinf <= tol)
+  else if (r.kappa > r.tau && dinf <= infeas_tol)
     st = 3;  // DUAL_INFEASIBLE
   R.status = st;
   R.iters = it;
@@ -1448,7 +1448,7 @@ __global__ void __launch_bounds__(256) k_persistent(DevPlan<T> p, PersistArgs<TC
       SOS_GRID_SYNC();
       for (int i = blockIdx.x; i < p.n_inst; i += G) {
         d_res_inst(p, i);
-        d_check(p, i, it, a.tol, a.rep, a.active, a.n_active);
+        d_check(p, i, it, a.tol, a.infeas_tol, a.rep, a.active, a.n_active);
       }
       SOS_GRID_SYNC();
       if (__ldcg(a.n_active) == 0) break;

@@ -110,6 +110,7 @@ struct PersistArgs {
   int32_t max_iter = 0;
   int32_t k_check = 0;        // 0: no checks (fixed number of iterations)
   double tol = 0.0;
+  double infeas_tol = 1e-7;    // tolerance of the infeasibility certificates
   uint32_t* bar = nullptr;     // grid barrier [2], zeroed by the launcher
   uint32_t* queue = nullptr;   // work queue counter, zeroed by the launcher
   int32_t* active = nullptr;   // same array as DevPlan::active

@@ -58,6 +58,7 @@ class WarmStart:
         self.net = None
         self.n_out = None
         self.log = {}
+        self.last_dims = None
 
     def solve(self, thetas: np.ndarray, tol: float, max_iter: int, start=None):
         """Batched solve of the members for ``thetas``; returns results and dims."""
@@ -69,6 +70,7 @@ class WarmStart:
         res = s.solve(tol, max_iter)
         dt = time.perf_counter() - t0
         dims = s.dims
+        self.last_dims = dims
         tuning = s.tuning()
         s.close()
         return res, dims, dt, tuning

@@ -144,3 +144,22 @@ def test_infeasibility_certificates():
                    constraints=[Constraint(2, {(2,): 1.0}, [{(2,): 1.0}], [Block(1)])])
     r = admm.solve(conic.build(p), 1e-6, 5000)
     assert r.status == admm.DUAL_INFEASIBLE
+
+
+def test_no_false_certificate_for_large_objective():
+    # max g s.t. x^4 - 3x^2 + x + 2000 - g is SOS: feasible, optimal value
+    # 2000 + min_x (x^4 - 3x^2 + x) against |c| = 1.  Early iterates sit at
+    # tau = 0 with |A^T u_y + v_z| / b^T u_y < 1e-3, so a certificate test at
+    # the residual tolerance 1e-3 would declare the program infeasible; at its
+    # own tolerance (1e-7, taken only while kappa > tau) the solve ends SOLVED
+    # at the value a fine grid gives (univariate nonnegative = SOS).
+    C = 2000.0
+    p = SOSProgram(n=1, w=np.array([-1.0]),
+                   constraints=[Constraint(4, g0={(4,): 1.0, (2,): -3.0, (1,): 1.0, (0,): C},
+                                           g=[{(0,): 1.0}], blocks=[Block(2)])])
+    r = admm.solve(conic.build(p), 1e-3, 20000, k_check=10)
+    assert r.status == admm.SOLVED, (r.status, r.res)
+    assert any(h["pinf"] <= 1e-3 for h in r.history)  # the unguarded test would have fired
+    x = np.linspace(-3, 3, 600001)
+    gamma = C + np.min(x ** 4 - 3 * x ** 2 + x)
+    assert abs(-r.res["pobj"] - gamma) <= 2e-3 * gamma
