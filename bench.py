@@ -246,13 +246,159 @@ def warmstart_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def batched_arm(args):
+    """Batched form: 4096 cubic Lyapunov searches (n uniform in 2..6, Gram
+    blocks 3x3 .. 84x84) advanced together.  One step = one ADMM iteration of
+    every instance.  Mixed form (FP64 iterates, Woodbury and residuals; FP32
+    Jacobi projections with the compensated refinement).  Also reported: time
+    to a 1e-4 residual for the whole batch, the plain FP64 form's rate on the
+    same batch, and the HBM roofline fraction of each memory-bound kernel of
+    the FP64 affine step (timed alone, L2 flushed before each launch)."""
+    import torch
+
+    from instances import workloads as W
+    from paper_1708_04174_gb300 import capi
+
+    count = 4096
+    t0 = time.perf_counter()
+    progs = W.lyapunov_batch(count, 0, 2, 6)
+    t_gen = time.perf_counter() - t0
+    pk, pk_kind = peaks()
+    hbm = float(pk["hbm_gbs"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(solver, fn, reps, flush_each=True):
+        st = torch.cuda.ExternalStream(solver.stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            with torch.cuda.stream(st):
+                if flush_each:
+                    flush.zero_()
+                a.record(st)
+            fn()
+            with torch.cuda.stream(st):
+                b.record(st)
+        solver.sync()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    t0 = time.perf_counter()
+    s = capi.Solver(progs, precision=capi.PREC_MIXED, k_check=10)
+    t_setup = time.perf_counter() - t0
+    s.iterate(args.warmup)
+    s.sync()
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_rank0.csv")
+                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_rank0.csv")
+    torch.cuda.synchronize()
+    with clk:
+        step_ms = timed(s, lambda: s.iterate(1), args.steps)
+    total_ms = float(np.sum(step_ms))
+    ips = args.steps / (total_ms / 1e3)
+    stage_ms = {name: float(np.mean(timed(s, lambda st=st: s.run_stage(st), 5)))
+                for st, name in ((0, "affine"), (1, "psd_small"))}
+    dims = s.dims
+    Ns = []
+    for prog in progs:
+        for con in prog.constraints:
+            for blk in con.blocks:
+                from math import comb
+
+                Ns.append(comb(prog.n + blk.basis_degree, blk.basis_degree))
+    flops = sum(9.0 * N ** 3 for N in Ns)
+    fp32_peak = 69700.0
+    roof = {"kernel": "k_psd_small<double,float> (FP32 Jacobi + compensated refinement, one CTA per block)",
+            "bound": "alu", "achieved": flops / (stage_ms["psd_small"] / 1e3) / 1e9, "peak": fp32_peak,
+            "unit": "GFLOP/s", "frac": flops / (stage_ms["psd_small"] / 1e3) / 1e9 / fp32_peak, "traffic": None,
+            "note": "algorithmic flops 9 N^3 per block over all 8192 blocks; peak = FMA-loop FP32 rate measured "
+                    "on this GB300", "stage_ms": stage_ms,
+            "stage_bytes": {"affine": s.stage_bytes(0), "psd_small": s.stage_bytes(1)}}
+    tuning = s.tuning()
+    launches = s.launches_per_iteration()
+    # end-to-end through the C-ABI with host buffers
+    u0, v0 = s.get_iterate()
+    e2e_steps = 10
+    s.sync()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_iterate(u0, v0)
+        s.iterate(1)
+        u0, v0 = s.get_iterate()
+    e2e_dt = time.perf_counter() - t0
+    nbytes = int(u0.nbytes + v0.nbytes)
+    e2e = {"value": e2e_steps / e2e_dt, "unit": "iter/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    s.close()
+
+    # time to a 1e-4 residual for the whole batch, from the cold start
+    tt = None
+    if not args.no_tt:
+        sm = capi.Solver(progs, precision=capi.PREC_MIXED, k_check=10)
+        t0 = time.perf_counter()
+        res = sm.solve(1e-4, args.max_iter, want_solution=False)
+        t_solve = time.perf_counter() - t0
+        sm.close()
+        st = np.array([r["status"] for r in res])
+        it = np.array([r["iters"] for r in res])
+        tt = {"seconds": t_solve, "per_instance_s": t_solve / count,
+              "status_counts": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
+              "iters": {"median": float(np.median(it)), "p90": float(np.percentile(it, 90)), "max": int(it.max())}}
+
+    # plain FP64 form on the same batch: rate, and the HBM roofline of the
+    # memory-bound kernels of its affine step
+    s64 = capi.Solver(progs, precision=capi.PREC_FP64, k_check=10, solve_mode=1)
+    s64.iterate(3)
+    s64.sync()
+    fp64_ms = float(np.mean(timed(s64, lambda: s64.iterate(1), 10)))
+    names = {4: "k_rows_r", 5: "k_lr_y", 6: "k_woodbury", 7: "k_rows_sigma2", 8: "k_inst_scalar", 9: "k_rows_y"}
+    hbm_kernels = {}
+    for stg, name in names.items():
+        ms = float(np.mean(timed(s64, lambda stg=stg: s64.run_stage(stg), 10)))
+        nb = s64.stage_bytes(stg)
+        gbs = nb / (ms / 1e3) / 1e9
+        hbm_kernels[name] = {"ms": ms, "algorithmic_bytes": nb, "achieved_gbs": gbs, "frac": gbs / hbm}
+    s64.close()
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle, as it stands, on a sample of the batch (one instance at a time)
+        tot_k, tot_t, used = 0, 0.0, 0
+        for prog in progs[::256]:
+            k, dt = run_oracle_iters(prog, seconds=1.0, max_iters=10 ** 9)
+            tot_k += k
+            tot_t += dt
+            used += 1
+        inst_rate = tot_k / tot_t
+        cpu = {"value": inst_rate / count, "unit": "iter/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{used} of the {count} instances (every 256th), about 1 s of oracle iterations each; "
+                         f"batch iterations/s = instance-iterations/s / {count}"}
+
+    line = {"metric": "ADMM iterations/s of the whole batch (one iteration of all 4096 instances)",
+            "value": ips, "unit": "iter/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 iterates, f32 proj", "data": "synthetic",
+            "config": {"workload": "lyapunov_batch4096",
+                       "desc": "4096 cubic Lyapunov searches, n uniform in 2..6, V degree 2..4, eps 1e-3; "
+                               "Gram blocks 3x3 .. 84x84",
+                       "form": "FP64 iterates/Woodbury/residuals, FP32 Jacobi projections + compensated refinement",
+                       "l2": "flushed between steps (256 MB write); working set > L2",
+                       "n_x_total": int(sum(d[0] for d in dims)), "m_total": int(sum(d[1] for d in dims)),
+                       "setup_s": t_setup, "generate_s": t_gen},
+            "instance_iters_per_s": ips * count, "e2e": e2e, "roofline": roof,
+            "hbm_kernels_fp64": {"peak_gbs": hbm, "peak_source": pk_kind, "kernels": hbm_kernels},
+            "fp64_form": {"ms_per_step": fp64_ms, "value": 1e3 / fp64_ms, "unit": "iter/s"},
+            "time_to_1e-4": tt, "tuning": tuning,
+            "gpu_launches": int(launches * args.steps), "clocks": clk.summary(0)}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="ball_pop_n20", choices=sorted(WORKLOADS) + ["parametric_warmstart"])
+    ap.add_argument("--workload", default="ball_pop_n20",
+                    choices=sorted(WORKLOADS) + ["parametric_warmstart", "lyapunov_batch4096"])
     ap.add_argument("--train", type=int, default=20000, help="training members (parametric_warmstart)")
     ap.add_argument("--epochs", type=int, default=200, help="training epochs (parametric_warmstart)")
     ap.add_argument("--max-iter", type=int, default=20000, help="iteration cap of every solve (parametric_warmstart)")
@@ -269,6 +415,8 @@ def main():
         return reference_arm(args, rank)
     if args.workload == "parametric_warmstart":
         return warmstart_arm(args)
+    if args.workload == "lyapunov_batch4096":
+        return batched_arm(args)
 
     import torch
 

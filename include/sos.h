@@ -328,9 +328,19 @@ int sos_launches_per_iteration(const sos_handle* h);
  * on the handle's stream).  sos_stream returns the cudaStream_t in use.
  * sos_run_stage enqueues one stage of one iteration: 0 = affine step (all
  * kernels up to the cone projection), 1 = PSD projection of small blocks,
- * 2 = PSD projection of large blocks, 3 = one full iteration. */
+ * 2 = PSD projection of large blocks, 3 = one full iteration, and single
+ * kernels of the affine step: 4 = row gather r = w2_hat - A w1_hat,
+ * x = P^-1 r (eq. (27b)), 5 = y = A_L^T x, 6 = Woodbury solve
+ * z = L^-T L^-1 y (eq. (28)), 7 = sigma_2 = x - P^-1 A_L z, 8 = per-instance
+ * scalars (eq. (24b), (25)) and free variables, 9 = u_y, v_y and u_hat_2
+ * rows.  Stages 4..9 run out of order leave the iterate meaningless; they
+ * exist to time one kernel.
+ * sos_stage_bytes gives the algorithmic bytes of one launch of a stage:
+ * every array element the stage has to read or write, counted once (the
+ * numerator of an HBM roofline fraction).  Errors: SOS_ERR_INVALID_ARG. */
 void* sos_stream(sos_handle* h);
 int sos_run_stage(sos_handle* h, int32_t stage);
+int sos_stage_bytes(const sos_handle* h, int32_t stage, int64_t* bytes);
 
 #ifdef __cplusplus
 }

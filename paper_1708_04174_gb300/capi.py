@@ -75,6 +75,7 @@ EXPORTS = {
     "sos_psd_project_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sos_psd_project_mixed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sos_run_stage": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sos_stage_bytes": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
     "sos_mlp_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]),
     "sos_mlp_destroy": (None, [C.c_void_p]),
     "sos_mlp_param_count": (C.c_int64, [C.c_void_p]),
@@ -304,6 +305,12 @@ class Solver:
 
     def launches_per_iteration(self) -> int:
         return int(lib().sos_launches_per_iteration(self.h))
+
+    def stage_bytes(self, stage: int) -> int:
+        """Algorithmic bytes of one launch of a profiling stage."""
+        out = C.c_int64()
+        _check(lib().sos_stage_bytes(self.h, stage, C.byref(out)), self.h)
+        return int(out.value)
 
     def run_stage(self, stage: int):
         _check(lib().sos_run_stage(self.h, stage), self.h)

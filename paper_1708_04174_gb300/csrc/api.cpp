@@ -70,6 +70,7 @@ struct sos_handle {
   int64_t iter_count = 0;
   int32_t* blk_sweeps = nullptr;  // device
   int32_t large_grid_best = 0;    // grid chosen for the cooperative Jacobi kernel
+  int64_t stage_bytes[10] = {0};  // algorithmic bytes of each profiling stage
   // persistent batched path
   bool persistent = false;
   int32_t solve_mode = 0;
@@ -216,6 +217,7 @@ template <typename T, typename TC>
 cudaError_t enqueue_stage(sos_handle* h, const DevPlan<T>& p, std::vector<LargeBlock<TC>>& large,
                           const SmallWarm<TC>& wm, int stage) {
   cudaError_t e = cudaSuccess;
+  if (stage >= 4 && stage <= 9) return launch_affine_part<T>(p, h->shape, stage - 4, h->stream);
   if (stage == 0 || stage == 3) {
     e = launch_affine<T>(p, h->shape, h->stream);
     if (e != cudaSuccess) return e;
@@ -428,6 +430,49 @@ int autotune_large(sos_handle* h, std::vector<LargeBlock<TC>>& large) {
   return check_err_word(h);
 }
 
+// Algorithmic bytes of each profiling stage (sos_stage_bytes): every array
+// element the stage has to read or write, counted once.  es is the size of an
+// iterate element, tcs the element size of the stored eigenvectors.
+void compute_stage_bytes(sos_handle* h, const HostPlan& P, const std::vector<int>& large) {
+  const int64_t es = h->precision == SOS_PREC_FP32 ? 4 : 8;
+  const int64_t tcs = h->precision == SOS_PREC_FP64 ? 8 : 4;
+  const int64_t M = P.M, nent = static_cast<int64_t>(P.row_ent.size());
+  const int64_t nnz = static_cast<int64_t>(P.lr_row.size()), TL = P.TL, ni = P.n_inst;
+  int64_t tri = 0, te_sum = 0, t_sum = 0;
+  for (const InstInfo& in : P.inst) {
+    tri += static_cast<int64_t>(in.t_eff) * (in.t_eff + 1) / 2;
+    te_sum += in.t_eff;
+    t_sum += in.t;
+  }
+  int64_t* b = h->stage_bytes;
+  // rows_r: rows (row_inst, u_y, v_y, b, pinv, row_ptr, lrr_ptr, x), plain
+  // entries (row_ent, u, v), A_L rows (lrr_col, lrr_val), low-rank columns
+  // (lr_ent, u, v, lr_c), per instance tau, kappa, active
+  b[4] = M * (4 + 2 * es + 8 + 8 + 4 + 4 + 8) + nent * (4 + 2 * es) + nnz * 12 + TL * (16 + 2 * es) + ni * 20;
+  // lr_y: A_L columns (lr_ptr, lr_inst, y_L), nonzeros (lr_val, lr_row), x
+  b[5] = TL * 16 + nnz * 12 + M * 8 + ni * 4;
+  // woodbury: the lower triangle of L^-1, y_L in, z out
+  b[6] = tri * 8 + te_sum * 16 + ni * static_cast<int64_t>(sizeof(InstInfo));
+  // rows_sigma2: rows (row_inst, lrr_ptr, x, pinv, sigma_2), nonzeros, z
+  b[7] = M * 32 + nnz * 12 + TL * 8;
+  // inst_scalar: b and sigma_2 per row; per free variable lr_c, u, v, z and
+  // the writes of u, v
+  b[8] = M * 16 + t_sum * (8 + 2 * es + 8 + 8 + 2 * es) + ni * 64;
+  // rows_y: rows (row_inst, sigma_2, h_2, v_y in; u_y, v_y, u_hat_2 out)
+  b[9] = M * (4 + 8 + 8 + 4 * es) + ni * 8;
+  b[0] = b[4] + b[5] + b[6] + b[7] + b[8] + b[9];
+  // projections: per packed entry the input (u, ent_row, u_hat_2 / z), the
+  // outputs u and v, and the stored eigenvectors read and written
+  std::vector<char> is_large(P.blocks.size(), 0);
+  for (int bid : large) is_large[bid] = 1;
+  b[1] = b[2] = 0;
+  for (size_t k = 0; k < P.blocks.size(); ++k) {
+    const int64_t N = P.blocks[k].N, L = N * (N + 1) / 2;
+    b[is_large[k] ? 2 : 1] += L * (4 + 3 * es) + 2 * N * N * tcs;
+  }
+  b[3] = b[0] + b[1] + b[2];
+}
+
 int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   HostPlan P;
   std::string err;
@@ -543,6 +588,7 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
     for (int32_t b : cls[k]) cls_n[k] = std::max(cls_n[k], P.blocks[b].N + (P.blocks[b].N & 1));
     max_small = std::max(max_small, cls_n[k]);
   }
+  compute_stage_bytes(h, P, large);
   // eigenvector storage of small blocks (warm start)
   int64_t voff = 0;
   for (int k = 0; k < kClasses; ++k)
@@ -1136,8 +1182,14 @@ int sos_launches_per_iteration(const sos_handle* h) {
 
 void* sos_stream(sos_handle* h) { return h ? static_cast<void*>(h->stream) : nullptr; }
 
+int sos_stage_bytes(const sos_handle* h, int32_t stage, int64_t* bytes) {
+  if (!h || !bytes || stage < 0 || stage > 9) return SOS_ERR_INVALID_ARG;
+  *bytes = h->stage_bytes[stage];
+  return SOS_OK;
+}
+
 int sos_run_stage(sos_handle* h, int32_t stage) {
-  if (!h || stage < 0 || stage > 3) return SOS_ERR_INVALID_ARG;
+  if (!h || stage < 0 || stage > 9) return SOS_ERR_INVALID_ARG;
   cudaError_t e = enqueue_any(h, stage);
   if (e != cudaSuccess) return set_err(h, SOS_ERR_CUDA, std::string("stage launch: ") + cudaGetErrorString(e));
   return SOS_OK;

@@ -1483,6 +1483,37 @@ cudaError_t launch_affine(const DevPlan<T>& p, const LaunchShape& ls, cudaStream
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_affine_part(const DevPlan<T>& p, const LaunchShape& ls, int part, cudaStream_t s) {
+  const int rt = ls.row_threads;
+  switch (part) {
+    case 0:
+      k_rows_r<T><<<grid_for(p.M, rt, ls.sms), rt, 0, s>>>(p);
+      break;
+    case 1:
+      if (p.TL > 0) k_lr_y<T><<<grid_for(static_cast<int64_t>(p.TL) * 32, 256, ls.sms), 256, 0, s>>>(p);
+      break;
+    case 2:
+      if (p.TL > 0) {
+        const size_t wsm = sizeof(double) * 2 * static_cast<size_t>(p.max_teff > 0 ? p.max_teff : 1);
+        k_woodbury<T><<<p.n_inst, 256, wsm, s>>>(p);
+      }
+      break;
+    case 3:
+      k_rows_sigma2<T><<<grid_for(p.M, rt, ls.sms), rt, 0, s>>>(p);
+      break;
+    case 4:
+      k_inst_scalar<T><<<p.n_inst, ls.inst_threads, 0, s>>>(p);
+      break;
+    case 5:
+      k_rows_y<T><<<grid_for(p.M, rt, ls.sms), rt, 0, s>>>(p);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 size_t psd_small_smem_bytes(int maxN, int form) {
   const int Np = maxN + (maxN & 1), ld = Np + 1, H = Np / 2;
   const size_t es = form == kFormFP64 ? 8 : 4;
@@ -1618,6 +1649,7 @@ cudaError_t launch_psd_ns(const DevPlan<T>& p, int bid, int N, const NsScratch& 
 
 #define SOS_INSTANTIATE(T)                                                                       \
   template cudaError_t launch_affine<T>(const DevPlan<T>&, const LaunchShape&, cudaStream_t);    \
+  template cudaError_t launch_affine_part<T>(const DevPlan<T>&, const LaunchShape&, int, cudaStream_t);    \
   template cudaError_t launch_residuals<T>(const DevPlan<T>&, const LaunchShape&, cudaStream_t);             \
   template cudaError_t launch_psd_ns<T>(const DevPlan<T>&, int, int, const NsScratch&, cudaStream_t);
 

@@ -131,6 +131,10 @@ struct LaunchShape {
 
 template <typename T>
 cudaError_t launch_affine(const DevPlan<T>& p, const LaunchShape& ls, cudaStream_t s);
+// one kernel of the affine step: 0 rows_r, 1 lr_y, 2 woodbury, 3 rows_sigma2,
+// 4 inst_scalar, 5 rows_y (profiling)
+template <typename T>
+cudaError_t launch_affine_part(const DevPlan<T>& p, const LaunchShape& ls, int part, cudaStream_t s);
 template <typename T, typename TC>
 cudaError_t launch_psd_small(const DevPlan<T>& p, const int32_t* ids, int count, int maxN, const SmallWarm<TC>& wm,
                              cudaStream_t s);
