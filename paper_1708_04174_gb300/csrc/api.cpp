@@ -136,6 +136,11 @@ struct Common {
   const int32_t *row_inst, *row_ptr, *ent_row, *lr_ptr, *lr_row, *lrr_ptr, *lrr_col, *lr_inst;
   const uint32_t* row_ent;
   const int64_t* lr_ent;
+  const int64_t *ent_sl_off, *lr_sl_off;
+  const uint32_t* ent_sl;
+  const int32_t* lr_sl_col;
+  const double* lr_sl_val;
+  double* wl;
   double *tau, *kappa, *xP, *ylr, *zlr, *sig2, *ra, *atyl;
   int32_t* err;
   int32_t* blk_sweeps;
@@ -171,6 +176,12 @@ int make_devplan(sos_handle* h, const Common& c, int32_t max_teff, DevPlan<T>& p
   p.lr_c = c.lr_c;
   p.lr_g = c.lr_g;
   p.linv = c.linv;
+  p.ent_sl_off = c.ent_sl_off;
+  p.ent_sl = c.ent_sl;
+  p.lr_sl_off = c.lr_sl_off;
+  p.lr_sl_col = c.lr_sl_col;
+  p.lr_sl_val = c.lr_sl_val;
+  p.wl = c.wl;
   p.tau = c.tau;
   p.kappa = c.kappa;
   p.xP = c.xP;
@@ -268,6 +279,11 @@ int check_err_word(sos_handle* h) {
   return SOS_OK;
 }
 
+int init_wl(sos_handle* h) {
+  CK(iter64(h) ? launch_init_wl<double>(h->d64, h->stream) : launch_init_wl<float>(h->d32, h->stream));
+  return SOS_OK;
+}
+
 int cold_start(sos_handle* h) {
   std::vector<double> one(h->n_inst, 1.0);
   CK(cudaMemcpyAsync(h->d64.tau, one.data(), sizeof(double) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
@@ -283,6 +299,7 @@ int cold_start(sos_handle* h) {
     CK(cudaMemsetAsync(h->d32.uy, 0, sizeof(float) * h->M, h->stream));
     CK(cudaMemsetAsync(h->d32.vy, 0, sizeof(float) * h->M, h->stream));
   }
+  TRY(init_wl(h));
   std::fill(h->active_h.begin(), h->active_h.end(), 1);
   CK(cudaMemcpyAsync(h->active, h->active_h.data(), sizeof(int32_t) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
   std::fill(h->iters_h.begin(), h->iters_h.end(), 0);
@@ -541,6 +558,47 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   int64_t* lp;
   TRY(upload(h, P.lr_ent, &lp));
   c.lr_ent = lp;
+  {  // sliced row lists: 32 rows per slice, element k of a row at off + 32 k + lane
+    const int64_t n_sl = (h->M + 31) / 32;
+    std::vector<int64_t> eoff(n_sl + 1, 0), loff(n_sl + 1, 0);
+    for (int64_t sl = 0; sl < n_sl; ++sl) {
+      int we = 0, wlr = 0;
+      for (int64_t a = sl * 32; a < std::min<int64_t>(h->M, sl * 32 + 32); ++a) {
+        we = std::max(we, P.row_ptr[a + 1] - P.row_ptr[a]);
+        wlr = std::max(wlr, P.lrr_ptr[a + 1] - P.lrr_ptr[a]);
+      }
+      eoff[sl + 1] = eoff[sl] + 32 * static_cast<int64_t>(we);
+      loff[sl + 1] = loff[sl] + 32 * static_cast<int64_t>(wlr);
+    }
+    std::vector<uint32_t> esl(std::max<int64_t>(eoff[n_sl], 1), 0u);
+    std::vector<int32_t> lcol(std::max<int64_t>(loff[n_sl], 1), 0);
+    std::vector<double> lval(std::max<int64_t>(loff[n_sl], 1), 0.0);
+    for (int64_t a = 0; a < h->M; ++a) {
+      const int64_t sl = a / 32, lane = a % 32;
+      for (int k = P.row_ptr[a]; k < P.row_ptr[a + 1]; ++k)
+        esl[eoff[sl] + 32 * static_cast<int64_t>(k - P.row_ptr[a]) + lane] = P.row_ent[k];
+      for (int k = P.lrr_ptr[a]; k < P.lrr_ptr[a + 1]; ++k) {
+        const int64_t q = loff[sl] + 32 * static_cast<int64_t>(k - P.lrr_ptr[a]) + lane;
+        lcol[q] = P.lrr_col[k];
+        lval[q] = P.lrr_val[k];
+      }
+    }
+    int64_t* op;
+    TRY(upload(h, eoff, &op));
+    c.ent_sl_off = op;
+    TRY(upload(h, loff, &op));
+    c.lr_sl_off = op;
+    uint32_t* eup;
+    TRY(upload(h, esl, &eup));
+    c.ent_sl = eup;
+    int32_t* cp;
+    TRY(upload(h, lcol, &cp));
+    c.lr_sl_col = cp;
+    double* vp;
+    TRY(upload(h, lval, &vp));
+    c.lr_sl_val = vp;
+  }
+  TRY(alloc(h, std::max<int64_t>(h->TL, 1), &c.wl));
   TRY(alloc(h, h->n_inst, &c.tau));
   TRY(alloc(h, h->n_inst, &c.kappa));
   TRY(alloc(h, h->M, &c.xP));
@@ -1003,6 +1061,7 @@ int sos_set_iterate(sos_handle* h, const double* u, const double* v) {
   if (!h || !u || !v) return SOS_ERR_INVALID_ARG;
   int rc = iter64(h) ? copy_iterate_in(h, h->d64, u, v) : copy_iterate_in(h, h->d32, u, v);
   if (rc != SOS_OK) return rc;
+  TRY(init_wl(h));
   std::fill(h->active_h.begin(), h->active_h.end(), 1);
   std::fill(h->iters_h.begin(), h->iters_h.end(), 0);
   std::fill(h->status_h.begin(), h->status_h.end(), SOS_RUNNING);

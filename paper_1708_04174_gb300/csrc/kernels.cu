@@ -61,6 +61,11 @@ __device__ __forceinline__ double d(T x) {
 // affine step
 // ---------------------------------------------------------------------------
 
+// r = w2_hat - A w1_hat and x = P^-1 r for every row (eq. (27b)).  Rows are
+// walked one per thread through the sliced lists (a warp's 32 rows read
+// element k of each row from 32 consecutive words), and the low-rank part
+// uses w1_hat of each column, stored once per iteration in wl: one FP64
+// multiply-add per A_L nonzero.  The row index must advance in whole warps.
 template <typename T>
 __device__ void d_rows_r(const DevPlan<T>& p, int64_t g0, int64_t stride) {
   for (int64_t a = g0; a < p.M; a += stride) {
@@ -68,19 +73,19 @@ __device__ void d_rows_r(const DevPlan<T>& p, int64_t g0, int64_t stride) {
     if (!p.active[i]) continue;
     const double om3 = p.tau[i] + p.kappa[i];
     double acc = d(p.uy[a]) + d(p.vy[a]) + p.b[a] * om3;  // w2hat
-    const int k1 = p.row_ptr[a + 1];
-    for (int k = p.row_ptr[a]; k < k1; ++k) {
-      const uint32_t v = p.row_ent[k];
+    const int64_t sl = a >> 5;
+    const int lane = static_cast<int>(a & 31);
+    const int ne = p.row_ptr[a + 1] - p.row_ptr[a];
+    const uint32_t* ent = p.ent_sl + p.ent_sl_off[sl] + lane;
+    for (int k = 0; k < ne; ++k) {
+      const uint32_t v = ent[32 * k];
       const uint32_t e = v & ~kOffDiagBit;
       const double w = d(p.ux[e]) + d(p.vx[e]);
       acc -= (v & kOffDiagBit) ? kSqrt2 * w : w;
     }
-    const int l1 = p.lrr_ptr[a + 1];
-    for (int k = p.lrr_ptr[a]; k < l1; ++k) {
-      const int j = p.lrr_col[k];
-      const int64_t e = p.lr_ent[j];
-      acc -= p.lrr_val[k] * (d(p.ux[e]) + d(p.vx[e]) - p.lr_c[j] * om3);
-    }
+    const int nl = p.lrr_ptr[a + 1] - p.lrr_ptr[a];
+    const int64_t lb = p.lr_sl_off[sl] + lane;
+    for (int k = 0; k < nl; ++k) acc -= p.lr_sl_val[lb + 32 * k] * p.wl[p.lr_sl_col[lb + 32 * k]];
     p.xP[a] = acc * p.pinv[a];
   }
 }
@@ -90,16 +95,23 @@ __global__ void k_rows_r(DevPlan<T> p) {
   d_rows_r(p, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, static_cast<int64_t>(gridDim.x) * blockDim.x);
 }
 
+// y = A_L^T x (eq. (28)), eight lanes per column: four columns per warp,
+// lanes striding over a column's nonzeros, a three-step shuffle reduction.
 template <typename T>
 __device__ void d_lr_y(const DevPlan<T>& p, int warp, int nwarps) {
-  const int lane = threadIdx.x & 31;
-  for (int j = warp; j < p.TL; j += nwarps) {
-    if (!p.active[p.lr_inst[j]]) continue;
+  const int lane = threadIdx.x & 31, sub = lane & 7, grp = lane >> 3;
+  for (int j0 = warp * 4; j0 < p.TL; j0 += nwarps * 4) {  // warp-uniform loop
+    const int j = j0 + grp;
+    const bool on = j < p.TL && p.active[p.lr_inst[j]];
     double acc = 0.0;
-    const int k1 = p.lr_ptr[j + 1];
-    for (int k = p.lr_ptr[j] + lane; k < k1; k += 32) acc += p.lr_val[k] * p.xP[p.lr_row[k]];
-    acc = warp_sum(acc);
-    if (lane == 0) p.ylr[j] = acc;
+    if (on) {
+      const int k1 = p.lr_ptr[j + 1];
+      for (int k = p.lr_ptr[j] + sub; k < k1; k += 8) acc += p.lr_val[k] * p.xP[p.lr_row[k]];
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (on && sub == 0) p.ylr[j] = acc;
   }
 }
 
@@ -148,8 +160,9 @@ __device__ void d_rows_sigma2(const DevPlan<T>& p, int64_t g0, int64_t stride) {
   for (int64_t a = g0; a < p.M; a += stride) {
     if (!p.active[p.row_inst[a]]) continue;
     double acc = 0.0;
-    const int l1 = p.lrr_ptr[a + 1];
-    for (int k = p.lrr_ptr[a]; k < l1; ++k) acc += p.lrr_val[k] * p.zlr[p.lrr_col[k]];
+    const int nl = p.lrr_ptr[a + 1] - p.lrr_ptr[a];
+    const int64_t lb = p.lr_sl_off[a >> 5] + (a & 31);  // sliced A_L row (rows advance in whole warps)
+    for (int k = 0; k < nl; ++k) acc += p.lr_sl_val[lb + 32 * k] * p.zlr[p.lr_sl_col[lb + 32 * k]];
     p.sig2[a] = p.xP[a] - acc * p.pinv[a];
   }
 }
@@ -175,25 +188,27 @@ __device__ void d_inst_scalar(const DevPlan<T>& p, int i) {
   for (int j = threadIdx.x; j < in.t; j += blockDim.x) {
     const int jl = in.lr_off + j;
     const double w = p.lr_c[jl];
-    const double w1 = d(p.ux[in.x_off + j]) + d(p.vx[in.x_off + j]) - w * om3;
-    cs += w * (w1 + p.zlr[jl]);  // c^T sigma_1, sigma_1 = w1hat + A^T sigma_2 = w1hat + z
+    cs += w * (p.wl[jl] + p.zlr[jl]);  // c^T sigma_1, sigma_1 = w1hat + A^T sigma_2 = w1hat + z
   }
   const double csig1 = block_sum(cs, sh);
   const double zs = csig1 - bsig2;                 // zeta^T sigma
   const double s = zs / (1.0 + in.zeta_h);         // eq. (25)
   const double uh3 = om3 + zs - s * in.zeta_h;     // eq. (24b): w3 + c^T u1 - b^T u2
+  const double tn = fmax(uh3 - kappa, 0.0);
+  const double kn = kappa - uh3 + tn;
   for (int j = threadIdx.x; j < in.t; j += blockDim.x) {
     const int jl = in.lr_off + j;
     const double w = p.lr_c[jl];
     const int64_t e = in.x_off + j;
     const double wv = d(p.ux[e]) - w * (om3 + s) + p.zlr[jl] - s * p.lr_g[jl];
-    p.ux[e] = static_cast<T>(wv);  // free: projection is the identity
-    p.vx[e] = static_cast<T>(0);   // dual of a free variable is 0
+    const T un = static_cast<T>(wv);
+    p.ux[e] = un;                // free: projection is the identity
+    p.vx[e] = static_cast<T>(0);  // dual of a free variable is 0
+    p.wl[jl] = d(un) - w * (tn + kn);  // w1_hat of the next iteration
   }
   if (threadIdx.x == 0) {
-    const double tn = fmax(uh3 - kappa, 0.0);
     p.tau[i] = tn;
-    p.kappa[i] = kappa - uh3 + tn;
+    p.kappa[i] = kn;
     p.st[i].s = s;
     p.st[i].omega3 = om3;
     p.st[i].cs1 = csig1;
@@ -301,6 +316,14 @@ __device__ __forceinline__ void jacobi_rot(T app, T aqq, T apq, T& c, T& s, T& t
 // they are stored) give B = V^T W V, nearly diagonal after the first
 // iterations, so few sweeps remain.
 // ---------------------------------------------------------------------------
+// Row i >= column j of lower-triangle entry t = i (i + 1) / 2 + j.
+__device__ __forceinline__ void lower_ij(int t, int& i, int& j) {
+  i = static_cast<int>((sqrtf(8.0f * static_cast<float>(t) + 1.0f) - 1.0f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;  // integer correction of the float estimate
+  while (i * (i + 1) / 2 > t) --i;
+  j = t - i * (i + 1) / 2;
+}
+
 // Compensated FP32 dot-product step (Ogita, Rump & Oishi, "Accurate sum and
 // dot product", 2005): s + c accumulates a*b with the product split exactly
 // by an FMA (a*b = p + e) and the sum split exactly by TwoSum (s + p = t + r).
@@ -336,10 +359,12 @@ __device__ __forceinline__ void dot2_step(float a, float b, float& s, float& c) 
 // above (2 N^3 steps of ~10 FP32 operations), not FP64: FP64 runs at under
 // 2% of the FP32 rate on this GPU.  On entry V holds the Jacobi
 // eigenvectors; on exit A holds V'.  The pair copy of W and then W V' live
-// where V and T1 were (2 Np ld floats >= 2 N^2).
+// where V and T1 were (2 Np ld floats >= 2 N^2); M is held in registers
+// until W V' is dead and then written where T1 was, so the refinement needs
+// no shared memory beyond the Jacobi's three buffers.
 template <typename T, typename TC>
 __device__ void psd_small_refine(const DevPlan<T>& p, const BlockDesc& bd, double s_sm, int N, int ld, TC* A, TC* V,
-                                 TC* T1, TC* X4, double* lam64) {
+                                 TC* T1, double* lam64) {
   static_assert(sizeof(TC) == 4, "the refinement works on FP32 data");
   const int tid = threadIdx.x, nt = blockDim.x;
   __syncthreads();
@@ -418,42 +443,65 @@ __device__ void psd_small_refine(const DevPlan<T>& p, const BlockDesc& bd, doubl
     lam64[i] = static_cast<double>(sh) + static_cast<double>(c);
   }
   __syncthreads();
-  for (int q = tid; q < N * N; q += nt) {  // X4 = M
-    const int i = q / N, j = q - i * N;
-    if (i < j) continue;
-    const double li = lam64[i], lj = lam64[j];
-    double m;
-    if (i == j) {
-      m = fmax(li, 0.0);
-    } else {
-      double g;
-      if (li > 0.0 && lj > 0.0)
-        g = 1.0;
-      else if (li <= 0.0 && lj <= 0.0)
-        g = 0.0;
-      else
-        g = (fmax(li, 0.0) - fmax(lj, 0.0)) / (li - lj);  // one of them > 0 >= the other: |li - lj| > 0
-      if (g != 0.0) {
-        float sh = 0.f, c = 0.f;
-        for (int k = 0; k < N; ++k) {
-          const float v = A[k * ld + i];
-          const float2 t2 = W2[k * N + j];
-          dot2_step(v, t2.x, sh, c);
-          c = __fmaf_rn(v, t2.y, c);
-        }
-        m = g * (static_cast<double>(sh) + static_cast<double>(c));
+  // M, one lower-triangle entry t = i (i + 1) / 2 + j per thread and slot,
+  // held in registers until W V' is dead, then written where T1 was
+  constexpr int kMaxLower = 25;  // ceil(112 * 113 / 2 / 256): N <= 112 with 256 threads
+  const int L = N * (N + 1) / 2;
+  if (L > kMaxLower * nt) {  // uniform: the size classes keep N <= 112
+    if (tid == 0) atomicExch(p.err, 3);
+    return;
+  }
+  float mreg[kMaxLower];
+#pragma unroll
+  for (int r = 0; r < kMaxLower; ++r) {
+    const int t = tid + r * nt;
+    mreg[r] = 0.f;
+    if (t < L) {
+      int i, j;
+      lower_ij(t, i, j);
+      const double li = lam64[i], lj = lam64[j];
+      double m;
+      if (i == j) {
+        m = fmax(li, 0.0);
       } else {
+        double g;
+        if (li > 0.0 && lj > 0.0)
+          g = 1.0;
+        else if (li <= 0.0 && lj <= 0.0)
+          g = 0.0;
+        else
+          g = (fmax(li, 0.0) - fmax(lj, 0.0)) / (li - lj);  // one of them > 0 >= the other: |li - lj| > 0
         m = 0.0;
+        if (g != 0.0) {
+          float sh = 0.f, c = 0.f;
+          for (int k = 0; k < N; ++k) {
+            const float v = A[k * ld + i];
+            const float2 t2 = W2[k * N + j];
+            dot2_step(v, t2.x, sh, c);
+            c = __fmaf_rn(v, t2.y, c);
+          }
+          m = g * (static_cast<double>(sh) + static_cast<double>(c));
+        }
       }
+      mreg[r] = static_cast<float>(m);
     }
-    X4[i * ld + j] = static_cast<TC>(m);
-    X4[j * ld + i] = static_cast<TC>(m);
+  }
+  __syncthreads();  // W V' is dead from here
+#pragma unroll
+  for (int r = 0; r < kMaxLower; ++r) {
+    const int t = tid + r * nt;
+    if (t < L) {
+      int i, j;
+      lower_ij(t, i, j);
+      T1[i * ld + j] = mreg[r];
+      T1[j * ld + i] = mreg[r];
+    }
   }
   __syncthreads();
   for (int q = tid; q < N * N; q += nt) {  // V region (as TC) = Y = V' M
     const int i = q / N, j = q - i * N;
     TC acc = 0;
-    for (int k = 0; k < N; ++k) acc += A[i * ld + k] * X4[k * ld + j];
+    for (int k = 0; k < N; ++k) acc += A[i * ld + k] * T1[k * ld + j];
     V[i * ld + j] = acc;
   }
   __syncthreads();
@@ -466,7 +514,9 @@ __device__ void psd_small_refine(const DevPlan<T>& p, const BlockDesc& bd, doubl
     const T w = proj_input(p, bd, kk, i != j, s_sm);
     const T uu = (i != j) ? static_cast<T>(d(u) * kSqrt2) : static_cast<T>(u);
     p.ux[bd.x_off + kk] = uu;
-    p.vx[bd.x_off + kk] = uu - w;
+    const T vv = uu - w;
+    p.vx[bd.x_off + kk] = vv;
+    if (bd.kind == kWeighted) p.wl[bd.lr_first + kk] = d(uu) + d(vv);  // w1_hat of the next iteration (c = 0)
   }
 }
 
@@ -484,8 +534,7 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
   TC* A = reinterpret_cast<TC*>(smraw);
   TC* V = A + Np * ld;
   TC* T1 = V + Np * ld;
-  TC* X4 = T1 + Np * ld;  // refinement only: M of the corrected projection
-  double* lam64 = reinterpret_cast<double*>(X4 + Np * ld);  // refinement only: Ritz values
+  double* lam64 = reinterpret_cast<double*>(T1 + Np * ld);  // refinement only: Ritz values
   TC* rc = kRefine ? reinterpret_cast<TC*>(lam64 + Np) : T1 + Np * ld;
   TC* rs = rc + H;
   TC* rt = rs + H;
@@ -609,7 +658,7 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
 
   if (tid == 0) p.blk_sweeps[bid] = sweeps_done;
   if constexpr (kRefine) {
-    psd_small_refine(p, bd, s_sm, N, ld, A, V, T1, X4, lam64);
+    psd_small_refine(p, bd, s_sm, N, ld, A, V, T1, lam64);
     if (gV) {  // keep the re-orthonormalised V' for the next iteration
       for (int q = tid; q < N * N; q += nt) {
         const int i = q / N, j = q - i * N;
@@ -630,7 +679,9 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
     const T w = proj_input(p, bd, kk, i != j, s_sm);
     const T uu = (i != j) ? static_cast<T>(d(u) * kSqrt2) : static_cast<T>(u);
     p.ux[bd.x_off + kk] = uu;
-    p.vx[bd.x_off + kk] = uu - w;
+    const T vv = uu - w;
+    p.vx[bd.x_off + kk] = vv;
+    if (bd.kind == kWeighted) p.wl[bd.lr_first + kk] = d(uu) + d(vv);  // w1_hat of the next iteration (c = 0)
   }
   if (gV) {  // keep V for the next iteration: V (3 I - V^T V) / 2
     for (int q = tid; q < N * N; q += nt) {
@@ -935,7 +986,9 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
       const T w = proj_input(p, bd, kk, i != j, s_sm);
       const T u = (i != j) ? static_cast<T>(d(acc) * kSqrt2) : static_cast<T>(acc);
       p.ux[bd.x_off + kk] = u;
-      p.vx[bd.x_off + kk] = u - w;
+      const T vv = u - w;
+      p.vx[bd.x_off + kk] = vv;
+      if (bd.kind == kWeighted) p.wl[bd.lr_first + kk] = d(u) + d(vv);  // w1_hat of the next iteration (c = 0)
     }
   }
   if (sizeof(TC) < 8) {  // FP32 eigenvectors: V <- V (3 I - V^T V) / 2 before they are kept
@@ -1233,7 +1286,9 @@ __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch
         const T wv = proj_input(p, bd, kk, row != col, s_sm);
         const T uu = (row != col) ? static_cast<T>(static_cast<double>(u) * kSqrt2) : static_cast<T>(u);
         p.ux[bd.x_off + kk] = uu;
-        p.vx[bd.x_off + kk] = uu - wv;
+        const T vv = uu - wv;
+        p.vx[bd.x_off + kk] = vv;
+        if (bd.kind == kWeighted) p.wl[bd.lr_first + kk] = d(uu) + d(vv);  // w1_hat of the next iteration (c = 0)
       }
     }
   }
@@ -1484,6 +1539,23 @@ cudaError_t launch_affine(const DevPlan<T>& p, const LaunchShape& ls, cudaStream
 }
 
 template <typename T>
+__global__ void k_init_wl(DevPlan<T> p) {
+  for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < p.TL;
+       j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int i = p.lr_inst[j];
+    const int64_t e = p.lr_ent[j];
+    p.wl[j] = d(p.ux[e]) + d(p.vx[e]) - p.lr_c[j] * (p.tau[i] + p.kappa[i]);
+  }
+}
+
+template <typename T>
+cudaError_t launch_init_wl(const DevPlan<T>& p, cudaStream_t s) {
+  if (p.TL == 0) return cudaSuccess;
+  k_init_wl<T><<<static_cast<int>((p.TL + 255) / 256), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_affine_part(const DevPlan<T>& p, const LaunchShape& ls, int part, cudaStream_t s) {
   const int rt = ls.row_threads;
   switch (part) {
@@ -1517,9 +1589,8 @@ cudaError_t launch_affine_part(const DevPlan<T>& p, const LaunchShape& ls, int p
 size_t psd_small_smem_bytes(int maxN, int form) {
   const int Np = maxN + (maxN & 1), ld = Np + 1, H = Np / 2;
   const size_t es = form == kFormFP64 ? 8 : 4;
-  const size_t bufs = form == kFormMixed ? 4 : 3;  // the refinement adds M
-  const size_t lam64 = form == kFormMixed ? sizeof(double) * Np : 0;
-  return es * (bufs * static_cast<size_t>(Np) * ld + 3 * H + Np) + lam64 + sizeof(int) * 2 * H;
+  const size_t lam64 = form == kFormMixed ? sizeof(double) * Np : 0;  // Ritz values of the refinement
+  return es * (3 * static_cast<size_t>(Np) * ld + 3 * H + Np) + lam64 + sizeof(int) * 2 * H;
 }
 
 int psd_small_max_n(int form) { return form == kFormFP64 ? 96 : (form == kFormMixed ? 112 : 128); }
@@ -1650,6 +1721,7 @@ cudaError_t launch_psd_ns(const DevPlan<T>& p, int bid, int N, const NsScratch& 
 #define SOS_INSTANTIATE(T)                                                                       \
   template cudaError_t launch_affine<T>(const DevPlan<T>&, const LaunchShape&, cudaStream_t);    \
   template cudaError_t launch_affine_part<T>(const DevPlan<T>&, const LaunchShape&, int, cudaStream_t);    \
+  template cudaError_t launch_init_wl<T>(const DevPlan<T>&, cudaStream_t);    \
   template cudaError_t launch_residuals<T>(const DevPlan<T>&, const LaunchShape&, cudaStream_t);             \
   template cudaError_t launch_psd_ns<T>(const DevPlan<T>&, int, int, const NsScratch&, cudaStream_t);
 

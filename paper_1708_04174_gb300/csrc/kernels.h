@@ -40,6 +40,14 @@ struct DevPlan {
   const double* lr_c = nullptr;
   const double* lr_g = nullptr;
   const double* linv = nullptr;
+  // sliced copies of the row lists (32 consecutive rows per slice; element k
+  // of row a at off[a / 32] + 32 k + a % 32, so a warp's loads coalesce)
+  const int64_t* ent_sl_off = nullptr;  // plain Gram entries (as row_ent)
+  const uint32_t* ent_sl = nullptr;
+  const int64_t* lr_sl_off = nullptr;   // A_L rows (as lrr_col / lrr_val)
+  const int32_t* lr_sl_col = nullptr;
+  const double* lr_sl_val = nullptr;
+  double* wl = nullptr;  // w1_hat on the low-rank columns: u + v - c (tau + kappa) (TL)
   // iterates
   T* ux = nullptr;
   T* vx = nullptr;
@@ -131,6 +139,10 @@ struct LaunchShape {
 
 template <typename T>
 cudaError_t launch_affine(const DevPlan<T>& p, const LaunchShape& ls, cudaStream_t s);
+// w1_hat on the low-rank columns from the stored iterate (after a start or
+// sos_set_iterate; during the iteration the producers of u and v write it)
+template <typename T>
+cudaError_t launch_init_wl(const DevPlan<T>& p, cudaStream_t s);
 // one kernel of the affine step: 0 rows_r, 1 lr_y, 2 woodbury, 3 rows_sigma2,
 // 4 inst_scalar, 5 rows_y (profiling)
 template <typename T>
