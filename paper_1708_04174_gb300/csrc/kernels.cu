@@ -728,19 +728,22 @@ __device__ __forceinline__ void st_release_u32(unsigned* ptr, unsigned v) {
 
 // Grid-wide barrier.  bar[0] counts arrivals (zeroed before the launch),
 // bar[1] holds the last released generation; the CTA that completes a
-// generation releases it, the others poll bar[1].  Bounded spin: on expiry
-// (or when another CTA already raised the error word) every CTA returns false.
+// generation releases it, the others poll bar[1].  Ordering comes from the
+// atomics themselves, not from full fences: __syncthreads orders the CTA's
+// writes before thread 0's arrival, the arrival is an acquire-release
+// read-modify-write at GPU scope (so the last arriver acquires every earlier
+// arrival), the release is a store-release and the pollers load-acquire it.
+// Bounded spin: on expiry (or when another CTA already raised the error
+// word) every CTA returns false.
 __device__ bool grid_barrier(unsigned* bar, unsigned target, int32_t* err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned G = gridDim.x;
-    const unsigned gen = target / G;
-    __threadfence();
-    const unsigned old = atomicAdd(bar, 1u);
+    const unsigned gen = target / gridDim.x;
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
     int good = 1;
     if (old == target - 1) {
-      __threadfence();  // order the other CTAs' arrivals before the release
       st_release_u32(bar + 1, gen);
     } else {
       const long long t0 = clock64();
@@ -756,7 +759,6 @@ __device__ bool grid_barrier(unsigned* bar, unsigned target, int32_t* err) {
         }
       }
     }
-    __threadfence();
     ok = good;
   }
   __syncthreads();
