@@ -47,6 +47,23 @@ def make_program(name):
     return getattr(W, fn)(n, seed)
 
 
+class L2Flush:
+    """Evicts L2 between timed steps: writes a 256 MB buffer (> 129 MB of L2)
+    and then reads a second one, so L2 holds clean unrelated lines and the
+    write-back of the flush itself is not charged to the next timed step."""
+
+    def __init__(self, torch):
+        n = 256 * 1024 * 1024 // 4
+        self.w = torch.empty(n, dtype=torch.float32, device="cuda")
+        self.r = torch.zeros(n, dtype=torch.float32, device="cuda")
+        self.out = torch.zeros((), dtype=torch.float32, device="cuda")
+        self.torch = torch
+
+    def __call__(self):
+        self.w.zero_()
+        self.torch.sum(self.r, dim=0, out=self.out)
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -265,7 +282,7 @@ def batched_arm(args):
     t_gen = time.perf_counter() - t0
     pk, pk_kind = peaks()
     hbm = float(pk["hbm_gbs"])
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch)
 
     def timed(solver, fn, reps, flush_each=True):
         st = torch.cuda.ExternalStream(solver.stream)
@@ -273,7 +290,7 @@ def batched_arm(args):
         for a, b in ev:
             with torch.cuda.stream(st):
                 if flush_each:
-                    flush.zero_()
+                    flush()
                 a.record(st)
             fn()
             with torch.cuda.stream(st):
@@ -378,7 +395,7 @@ def batched_arm(args):
                        "desc": "4096 cubic Lyapunov searches, n uniform in 2..6, V degree 2..4, eps 1e-3; "
                                "Gram blocks 3x3 .. 84x84",
                        "form": "FP64 iterates/Woodbury/residuals, FP32 Jacobi projections + compensated refinement",
-                       "l2": "flushed between steps (256 MB write); working set > L2",
+                       "l2": "flushed between steps (256 MB write, then 256 MB read); working set > L2",
                        "n_x_total": int(sum(d[0] for d in dims)), "m_total": int(sum(d[1] for d in dims)),
                        "setup_s": t_setup, "generate_s": t_gen},
             "instance_iters_per_s": ips * count, "e2e": e2e, "roofline": roof,
@@ -434,7 +451,7 @@ def main():
     prec = {"fp64": capi.PREC_FP64, "mixed": capi.PREC_MIXED, "fp32": capi.PREC_FP32}[args.precision]
     solver = capi.Solver(prog, precision=prec, k_check=10)
     stream = torch.cuda.ExternalStream(solver.stream)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch)
 
     # warm-up
     solver.iterate(args.warmup)
@@ -454,7 +471,7 @@ def main():
         t_wall0 = time.perf_counter()
         for k in range(args.steps):
             with torch.cuda.stream(stream):
-                flush.zero_()  # L2 flush (256 MB > 129 MB L2) between steps, outside the step's events
+                flush()  # L2 flush between steps, outside the step's events
                 starts[k].record(stream)
             solver.iterate(1)
             with torch.cuda.stream(stream):
@@ -512,16 +529,20 @@ def main():
                 "note": "algorithmic flops 9 N^3 per block; peak = FMA-loop rate measured on this GB300"}
     roof["stage_ms"] = stage_ms
 
-    # end-to-end through the C-ABI with host buffers
-    u0, v0 = solver.get_iterate()
-    e2e_steps = max(5, args.steps // 4)
-    solver.sync()
+    # end-to-end through the C-ABI with host buffers, on a fresh handle over
+    # the same iteration range as the timed steps (warm-up, then the steps)
+    se = capi.Solver(prog, precision=prec, k_check=10)
+    se.iterate(args.warmup)
+    se.sync()
+    u0, v0 = se.get_iterate()
+    e2e_steps = args.steps
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        solver.set_iterate(u0, v0)
-        solver.iterate(1)
-        u0, v0 = solver.get_iterate()
+        se.set_iterate(u0, v0)
+        se.iterate(1)
+        u0, v0 = se.get_iterate()
     e2e_dt = time.perf_counter() - t0
+    se.close()
     esz = 8 if prec == capi.PREC_FP64 else 4
     nbytes = 2 * ((d[0] + d[1]) * esz + 8)
     e2e = {"value": world * e2e_steps / e2e_dt, "unit": "iter/s", "h2d_bytes_per_step": nbytes,
@@ -533,7 +554,7 @@ def main():
            "vs_baseline": None, "dtype": "f64" if prec == capi.PREC_FP64 else "f32", "data": "synthetic",
            "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
                       "form": "plain FP64" if prec == capi.PREC_FP64 else "FP32 projections, FP64 Woodbury",
-                      "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
+                      "l2": "flushed between steps (256 MB write, then 256 MB read)", "parallelism": "replicas" if world > 1 else "1 GPU",
                       "n_x": d[0], "m": d[1], "t_eff": d[3]},
            "wall_s": t_wall, "e2e": e2e, "roofline": roof,
            "gpu_launches": None}
@@ -551,7 +572,7 @@ def main():
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         for a0, a1 in ev:
             with torch.cuda.stream(stm):
-                flush.zero_()
+                flush()
                 a0.record(stm)
             sm.iterate(1)
             with torch.cuda.stream(stm):

@@ -132,11 +132,12 @@ struct Common {
   InstState* st;
   InstResid* resid;
   const BlockDesc* blocks;
-  const double *b, *pinv, *h2, *lr_val, *lrr_val, *lr_c, *lr_g, *linv;
+  const double *b, *pinv, *h2, *lr_val, *lrr_val, *lr_c, *lr_g, *linv, *linv_t;
   const int32_t *row_inst, *row_ptr, *ent_row, *lr_ptr, *lr_row, *lrr_ptr, *lrr_col, *lr_inst;
   const uint32_t* row_ent;
   const int64_t* lr_ent;
   const int64_t *ent_sl_off, *lr_sl_off;
+  const int32_t *row_perm, *col_perm;
   const uint32_t* ent_sl;
   const int32_t* lr_sl_col;
   const double* lr_sl_val;
@@ -176,6 +177,9 @@ int make_devplan(sos_handle* h, const Common& c, int32_t max_teff, DevPlan<T>& p
   p.lr_c = c.lr_c;
   p.lr_g = c.lr_g;
   p.linv = c.linv;
+  p.linv_t = c.linv_t;
+  p.row_perm = c.row_perm;
+  p.col_perm = c.col_perm;
   p.ent_sl_off = c.ent_sl_off;
   p.ent_sl = c.ent_sl;
   p.lr_sl_off = c.lr_sl_off;
@@ -535,6 +539,18 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   c.lr_g = dp;
   TRY(upload(h, P.linv, &dp));
   c.linv = dp;
+  {  // column-major copy of every L^-1
+    std::vector<double> lt(P.linv.size(), 0.0);
+    for (const InstInfo& in : P.inst) {
+      const int64_t te = in.t_eff;
+      const double* src = P.linv.data() + in.linv_off;
+      double* dst = lt.data() + in.linv_off;
+      for (int64_t r = 0; r < te; ++r)
+        for (int64_t k = 0; k <= r; ++k) dst[k * te + r] = src[r * te + k];
+    }
+    TRY(upload(h, lt, &dp));
+    c.linv_t = dp;
+  }
   int32_t* ip;
   TRY(upload(h, P.row_inst, &ip));
   c.row_inst = ip;
@@ -558,12 +574,27 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   int64_t* lp;
   TRY(upload(h, P.lr_ent, &lp));
   c.lr_ent = lp;
-  {  // sliced row lists: 32 rows per slice, element k of a row at off + 32 k + lane
+  {  // sliced row lists (SELL-32-sigma): within each instance the rows are
+     // ordered by decreasing length (A_L nonzeros, then plain entries), 32
+     // consecutive slots form a slice, element k of the row in slot q lies at
+     // off[q / 32] + 32 k + q % 32.  Rows of a slice then have similar
+     // lengths, so a warp's 32 lanes stay busy for the same number of steps.
     const int64_t n_sl = (h->M + 31) / 32;
+    std::vector<int32_t> perm(h->M);
+    for (int64_t a = 0; a < h->M; ++a) perm[a] = static_cast<int32_t>(a);
+    for (const InstInfo& in : P.inst) {
+      auto first = perm.begin() + in.y_off, last = first + in.m;
+      std::stable_sort(first, last, [&](int32_t x, int32_t y) {
+        const int lx = P.lrr_ptr[x + 1] - P.lrr_ptr[x], ly = P.lrr_ptr[y + 1] - P.lrr_ptr[y];
+        if (lx != ly) return lx > ly;
+        return P.row_ptr[x + 1] - P.row_ptr[x] > P.row_ptr[y + 1] - P.row_ptr[y];
+      });
+    }
     std::vector<int64_t> eoff(n_sl + 1, 0), loff(n_sl + 1, 0);
     for (int64_t sl = 0; sl < n_sl; ++sl) {
       int we = 0, wlr = 0;
-      for (int64_t a = sl * 32; a < std::min<int64_t>(h->M, sl * 32 + 32); ++a) {
+      for (int64_t q = sl * 32; q < std::min<int64_t>(h->M, sl * 32 + 32); ++q) {
+        const int32_t a = perm[q];
         we = std::max(we, P.row_ptr[a + 1] - P.row_ptr[a]);
         wlr = std::max(wlr, P.lrr_ptr[a + 1] - P.lrr_ptr[a]);
       }
@@ -573,8 +604,9 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
     std::vector<uint32_t> esl(std::max<int64_t>(eoff[n_sl], 1), 0u);
     std::vector<int32_t> lcol(std::max<int64_t>(loff[n_sl], 1), 0);
     std::vector<double> lval(std::max<int64_t>(loff[n_sl], 1), 0.0);
-    for (int64_t a = 0; a < h->M; ++a) {
-      const int64_t sl = a / 32, lane = a % 32;
+    for (int64_t q = 0; q < h->M; ++q) {
+      const int64_t a = perm[q];
+      const int64_t sl = q / 32, lane = q % 32;
       for (int k = P.row_ptr[a]; k < P.row_ptr[a + 1]; ++k)
         esl[eoff[sl] + 32 * static_cast<int64_t>(k - P.row_ptr[a]) + lane] = P.row_ent[k];
       for (int k = P.lrr_ptr[a]; k < P.lrr_ptr[a + 1]; ++k) {
@@ -591,6 +623,21 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
     uint32_t* eup;
     TRY(upload(h, esl, &eup));
     c.ent_sl = eup;
+    int32_t* pp;
+    TRY(upload(h, perm, &pp));
+    c.row_perm = pp;
+    // columns of A_L (CSC) ordered by decreasing length within each instance,
+    // so the four columns a warp takes together have similar lengths
+    std::vector<int32_t> cperm(std::max<int32_t>(h->TL, 1), 0);
+    for (int32_t j = 0; j < h->TL; ++j) cperm[j] = j;
+    for (const InstInfo& in : P.inst) {
+      auto first = cperm.begin() + in.lr_off, last = first + in.t_eff;
+      std::stable_sort(first, last, [&](int32_t x, int32_t y) {
+        return P.lr_ptr[x + 1] - P.lr_ptr[x] > P.lr_ptr[y + 1] - P.lr_ptr[y];
+      });
+    }
+    TRY(upload(h, cperm, &pp));
+    c.col_perm = pp;
     int32_t* cp;
     TRY(upload(h, lcol, &cp));
     c.lr_sl_col = cp;

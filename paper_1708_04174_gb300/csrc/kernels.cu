@@ -68,15 +68,17 @@ __device__ __forceinline__ double d(T x) {
 // multiply-add per A_L nonzero.  The row index must advance in whole warps.
 template <typename T>
 __device__ void d_rows_r(const DevPlan<T>& p, int64_t g0, int64_t stride) {
-  for (int64_t a = g0; a < p.M; a += stride) {
+  for (int64_t q = g0; q < p.M; q += stride) {  // q: slot, a: row
+    const int64_t a = p.row_perm[q];
     const int i = p.row_inst[a];
     if (!p.active[i]) continue;
     const double om3 = p.tau[i] + p.kappa[i];
     double acc = d(p.uy[a]) + d(p.vy[a]) + p.b[a] * om3;  // w2hat
-    const int64_t sl = a >> 5;
-    const int lane = static_cast<int>(a & 31);
+    const int64_t sl = q >> 5;
+    const int lane = static_cast<int>(q & 31);
     const int ne = p.row_ptr[a + 1] - p.row_ptr[a];
     const uint32_t* ent = p.ent_sl + p.ent_sl_off[sl] + lane;
+#pragma unroll 4
     for (int k = 0; k < ne; ++k) {
       const uint32_t v = ent[32 * k];
       const uint32_t e = v & ~kOffDiagBit;
@@ -85,6 +87,7 @@ __device__ void d_rows_r(const DevPlan<T>& p, int64_t g0, int64_t stride) {
     }
     const int nl = p.lrr_ptr[a + 1] - p.lrr_ptr[a];
     const int64_t lb = p.lr_sl_off[sl] + lane;
+#pragma unroll 4
     for (int k = 0; k < nl; ++k) acc -= p.lr_sl_val[lb + 32 * k] * p.wl[p.lr_sl_col[lb + 32 * k]];
     p.xP[a] = acc * p.pinv[a];
   }
@@ -101,11 +104,13 @@ template <typename T>
 __device__ void d_lr_y(const DevPlan<T>& p, int warp, int nwarps) {
   const int lane = threadIdx.x & 31, sub = lane & 7, grp = lane >> 3;
   for (int j0 = warp * 4; j0 < p.TL; j0 += nwarps * 4) {  // warp-uniform loop
-    const int j = j0 + grp;
-    const bool on = j < p.TL && p.active[p.lr_inst[j]];
+    const int jq = j0 + grp;
+    const int j = jq < p.TL ? p.col_perm[jq] : 0;  // columns of similar length share a warp
+    const bool on = jq < p.TL && p.active[p.lr_inst[j]];
     double acc = 0.0;
     if (on) {
       const int k1 = p.lr_ptr[j + 1];
+#pragma unroll 4
       for (int k = p.lr_ptr[j] + sub; k < k1; k += 8) acc += p.lr_val[k] * p.xP[p.lr_row[k]];
     }
     acc += __shfl_xor_sync(0xffffffffu, acc, 4);
@@ -132,16 +137,16 @@ __device__ void d_woodbury(const DevPlan<T>& p, int i, double* sh) {
   const double* Li = p.linv + in.linv_off;
   for (int k = threadIdx.x; k < te; k += blockDim.x) y[k] = p.ylr[in.lr_off + k];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = warp; r < te; r += nw) {  // q = L^{-1} y, one warp per row
+  const double* Lt = p.linv_t + in.linv_off;  // the same matrix, column-major
+  for (int r = threadIdx.x; r < te; r += blockDim.x) {  // q = L^{-1} y, one thread per row
     double acc = 0.0;
-    for (int k = lane; k <= r; k += 32) acc += Li[static_cast<int64_t>(r) * te + k] * y[k];
-    acc = warp_sum(acc);
-    if (lane == 0) q[r] = acc;
+#pragma unroll 4
+    for (int k = 0; k <= r; ++k) acc += Lt[static_cast<int64_t>(k) * te + r] * y[k];  // coalesced across rows
+    q[r] = acc;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < te + 31; j += blockDim.x) {  // z = L^{-T} q, one thread per column
-    const int r0 = j & ~31;
+  for (int j = threadIdx.x; j < te + 31; j += blockDim.x) {  // z = L^{-T} q, one thread per column;
+    const int r0 = j & ~31;  // the lanes of a warp walk the same rows together (coalesced row reads)
     double acc = 0.0;
     for (int r = r0; r < te; ++r)
       if (j < te && r >= j) acc += Li[static_cast<int64_t>(r) * te + j] * q[r];
@@ -157,11 +162,13 @@ __global__ void k_woodbury(DevPlan<T> p) {
 
 template <typename T>
 __device__ void d_rows_sigma2(const DevPlan<T>& p, int64_t g0, int64_t stride) {
-  for (int64_t a = g0; a < p.M; a += stride) {
+  for (int64_t q = g0; q < p.M; q += stride) {  // q: slot, a: row (slots advance in whole warps)
+    const int64_t a = p.row_perm[q];
     if (!p.active[p.row_inst[a]]) continue;
     double acc = 0.0;
     const int nl = p.lrr_ptr[a + 1] - p.lrr_ptr[a];
-    const int64_t lb = p.lr_sl_off[a >> 5] + (a & 31);  // sliced A_L row (rows advance in whole warps)
+    const int64_t lb = p.lr_sl_off[q >> 5] + (q & 31);
+#pragma unroll 4
     for (int k = 0; k < nl; ++k) acc += p.lr_sl_val[lb + 32 * k] * p.zlr[p.lr_sl_col[lb + 32 * k]];
     p.sig2[a] = p.xP[a] - acc * p.pinv[a];
   }
@@ -260,6 +267,20 @@ __device__ __forceinline__ int64_t packed_index(int i, int j, int N) {  // i >= 
 }
 
 // Round-robin (circle method) pairing: pair k of round r, for Np even.
+// q = x / d, r = x % d for 0 <= x < 2^24 without an integer division: the
+// float estimate is off by at most one and is corrected exactly.
+__device__ __forceinline__ void divmod_small(int x, int d, float invd, int& q, int& r) {
+  q = __float2int_rz(static_cast<float>(x) * invd);
+  r = x - q * d;
+  if (r >= d) {
+    ++q;
+    r -= d;
+  } else if (r < 0) {
+    --q;
+    r += d;
+  }
+}
+
 __device__ __forceinline__ void rr_pair(int k, int r, int Np, int& a, int& b) {
   const int m1 = Np - 1;
   a = (k == 0) ? 0 : 1 + (k - 1 + r) % m1;
@@ -583,6 +604,7 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
 
   int sweeps_done = 0;
   int round_id = 0;
+  const float invH = 1.0f / static_cast<float>(H);
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
     bool rotated = false;
     sweeps_done = sweep + 1;
@@ -610,7 +632,8 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
       const int nblk = H * H;
       for (int task = tid; task < nblk + N * H; task += nt) {
         if (task < nblk) {
-          const int k1 = task / H, k2 = task - k1 * H;
+          int k1, k2;
+          divmod_small(task, H, invH, k1, k2);
           if (k1 > k2) continue;
           const int p1 = rp[k1], q1 = rq[k1], p2 = rp[k2], q2 = rq[k2];
           const TC c1 = rc[k1], s1 = rs[k1];
@@ -640,8 +663,8 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
           A[p2 * ld + q1] = z21;
           A[q2 * ld + q1] = z22;
         } else {
-          const int t2 = task - nblk;
-          const int row = t2 / H, k = t2 - row * H;
+          int row, k;
+          divmod_small(task - nblk, H, invH, row, k);
           const TC s = rs[k];
           if (s == static_cast<TC>(0)) continue;
           const TC c = rc[k];
@@ -703,7 +726,7 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
 }
 
 template <typename T, typename TC>
-__global__ void __launch_bounds__(256) k_psd_small(DevPlan<T> p, const int32_t* ids, SmallWarm<TC> wm) {
+__global__ void __launch_bounds__(512) k_psd_small(DevPlan<T> p, const int32_t* ids, SmallWarm<TC> wm) {
   extern __shared__ __align__(16) unsigned char smraw[];
   d_psd_small(p, ids[blockIdx.x], wm, smraw);
 }
@@ -1602,7 +1625,8 @@ cudaError_t launch_psd_small(const DevPlan<T>& p, const int32_t* ids, int count,
                              cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   const size_t sm = psd_small_smem_bytes(maxN, form_of<T, TC>());
-  k_psd_small<T, TC><<<count, 256, sm, s>>>(p, ids, wm);
+  const int threads = maxN > 64 ? 512 : 256;  // more warps per SM where blocks are large
+  k_psd_small<T, TC><<<count, threads, sm, s>>>(p, ids, wm);
   return cudaGetLastError();
 }
 
