@@ -71,6 +71,7 @@ struct sos_handle {
   int32_t* blk_sweeps = nullptr;  // device
   int32_t large_grid_best = 0;    // grid chosen for the cooperative Jacobi kernel
   int64_t stage_bytes[10] = {0};  // algorithmic bytes of each profiling stage
+  std::vector<int32_t> row_perm;  // device row q holds the constraint row row_perm[q]
   // persistent batched path
   bool persistent = false;
   int32_t solve_mode = 0;
@@ -137,7 +138,7 @@ struct Common {
   const uint32_t* row_ent;
   const int64_t* lr_ent;
   const int64_t *ent_sl_off, *lr_sl_off;
-  const int32_t *row_perm, *col_perm;
+  const int32_t* col_perm;
   const uint32_t* ent_sl;
   const int32_t* lr_sl_col;
   const double* lr_sl_val;
@@ -178,7 +179,6 @@ int make_devplan(sos_handle* h, const Common& c, int32_t max_teff, DevPlan<T>& p
   p.lr_g = c.lr_g;
   p.linv = c.linv;
   p.linv_t = c.linv_t;
-  p.row_perm = c.row_perm;
   p.col_perm = c.col_perm;
   p.ent_sl_off = c.ent_sl_off;
   p.ent_sl = c.ent_sl;
@@ -451,6 +451,68 @@ int autotune_large(sos_handle* h, std::vector<LargeBlock<TC>>& large) {
   return check_err_word(h);
 }
 
+// Renumbers the rows of each instance in order of decreasing length (A_L
+// nonzeros, then plain Gram entries) so that 32 consecutive rows have similar
+// lengths: a warp of the row kernels then keeps its lanes busy, and every
+// row-indexed array is read and written contiguously.  perm[new] = old; the
+// host converts the y part of iterates and results with it.
+void renumber_rows(HostPlan& P, std::vector<int32_t>& perm) {
+  const int64_t M = P.M;
+  perm.resize(M);
+  for (int64_t a = 0; a < M; ++a) perm[a] = static_cast<int32_t>(a);
+  for (const InstInfo& in : P.inst) {
+    auto first = perm.begin() + in.y_off, last = first + in.m;
+    std::stable_sort(first, last, [&](int32_t x, int32_t y) {
+      const int lx = P.lrr_ptr[x + 1] - P.lrr_ptr[x], ly = P.lrr_ptr[y + 1] - P.lrr_ptr[y];
+      if (lx != ly) return lx > ly;
+      return P.row_ptr[x + 1] - P.row_ptr[x] > P.row_ptr[y + 1] - P.row_ptr[y];
+    });
+  }
+  std::vector<int32_t> inv(M);
+  for (int64_t q = 0; q < M; ++q) inv[perm[q]] = static_cast<int32_t>(q);
+  auto permute = [&](auto& v) {
+    auto w = v;
+    for (int64_t q = 0; q < M; ++q) w[q] = v[perm[q]];
+    v.swap(w);
+  };
+  permute(P.b);
+  permute(P.pinv);
+  permute(P.h2);
+  permute(P.row_inst);
+  {  // plain entries per row
+    std::vector<int32_t> ptr(M + 1, 0);
+    std::vector<uint32_t> ent;
+    ent.reserve(P.row_ent.size());
+    for (int64_t q = 0; q < M; ++q) {
+      const int32_t a = perm[q];
+      for (int k = P.row_ptr[a]; k < P.row_ptr[a + 1]; ++k) ent.push_back(P.row_ent[k]);
+      ptr[q + 1] = static_cast<int32_t>(ent.size());
+    }
+    P.row_ptr.swap(ptr);
+    P.row_ent.swap(ent);
+  }
+  {  // A_L rows
+    std::vector<int32_t> ptr(M + 1, 0), col;
+    std::vector<double> val;
+    col.reserve(P.lrr_col.size());
+    val.reserve(P.lrr_val.size());
+    for (int64_t q = 0; q < M; ++q) {
+      const int32_t a = perm[q];
+      for (int k = P.lrr_ptr[a]; k < P.lrr_ptr[a + 1]; ++k) {
+        col.push_back(P.lrr_col[k]);
+        val.push_back(P.lrr_val[k]);
+      }
+      ptr[q + 1] = static_cast<int32_t>(col.size());
+    }
+    P.lrr_ptr.swap(ptr);
+    P.lrr_col.swap(col);
+    P.lrr_val.swap(val);
+  }
+  for (auto& r : P.ent_row)  // row of each plain entry (flag bit kept)
+    if (r >= 0) r = inv[r & ~kEntOffBit] | (r & kEntOffBit);
+  for (auto& r : P.lr_row) r = inv[r];  // rows of the A_L columns
+}
+
 // Algorithmic bytes of each profiling stage (sos_stage_bytes): every array
 // element the stage has to read or write, counted once.  es is the size of an
 // iterate element, tcs the element size of the stored eigenvectors.
@@ -499,6 +561,7 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   std::string err;
   int rc = build_plan(progs, n_progs, P, err);
   if (rc != SOS_OK) return set_err(h, rc, err);
+  renumber_rows(P, h->row_perm);
   h->n_inst = P.n_inst;
   h->NX = P.NX;
   h->M = P.M;
@@ -574,27 +637,14 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   int64_t* lp;
   TRY(upload(h, P.lr_ent, &lp));
   c.lr_ent = lp;
-  {  // sliced row lists (SELL-32-sigma): within each instance the rows are
-     // ordered by decreasing length (A_L nonzeros, then plain entries), 32
-     // consecutive slots form a slice, element k of the row in slot q lies at
-     // off[q / 32] + 32 k + q % 32.  Rows of a slice then have similar
-     // lengths, so a warp's 32 lanes stay busy for the same number of steps.
+  {  // sliced row lists: 32 consecutive rows (already ordered by length by
+     // renumber_rows) form a slice, element k of row a lies at
+     // off[a / 32] + 32 k + a % 32
     const int64_t n_sl = (h->M + 31) / 32;
-    std::vector<int32_t> perm(h->M);
-    for (int64_t a = 0; a < h->M; ++a) perm[a] = static_cast<int32_t>(a);
-    for (const InstInfo& in : P.inst) {
-      auto first = perm.begin() + in.y_off, last = first + in.m;
-      std::stable_sort(first, last, [&](int32_t x, int32_t y) {
-        const int lx = P.lrr_ptr[x + 1] - P.lrr_ptr[x], ly = P.lrr_ptr[y + 1] - P.lrr_ptr[y];
-        if (lx != ly) return lx > ly;
-        return P.row_ptr[x + 1] - P.row_ptr[x] > P.row_ptr[y + 1] - P.row_ptr[y];
-      });
-    }
     std::vector<int64_t> eoff(n_sl + 1, 0), loff(n_sl + 1, 0);
     for (int64_t sl = 0; sl < n_sl; ++sl) {
       int we = 0, wlr = 0;
-      for (int64_t q = sl * 32; q < std::min<int64_t>(h->M, sl * 32 + 32); ++q) {
-        const int32_t a = perm[q];
+      for (int64_t a = sl * 32; a < std::min<int64_t>(h->M, sl * 32 + 32); ++a) {
         we = std::max(we, P.row_ptr[a + 1] - P.row_ptr[a]);
         wlr = std::max(wlr, P.lrr_ptr[a + 1] - P.lrr_ptr[a]);
       }
@@ -604,9 +654,8 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
     std::vector<uint32_t> esl(std::max<int64_t>(eoff[n_sl], 1), 0u);
     std::vector<int32_t> lcol(std::max<int64_t>(loff[n_sl], 1), 0);
     std::vector<double> lval(std::max<int64_t>(loff[n_sl], 1), 0.0);
-    for (int64_t q = 0; q < h->M; ++q) {
-      const int64_t a = perm[q];
-      const int64_t sl = q / 32, lane = q % 32;
+    for (int64_t a = 0; a < h->M; ++a) {
+      const int64_t sl = a / 32, lane = a % 32;
       for (int k = P.row_ptr[a]; k < P.row_ptr[a + 1]; ++k)
         esl[eoff[sl] + 32 * static_cast<int64_t>(k - P.row_ptr[a]) + lane] = P.row_ent[k];
       for (int k = P.lrr_ptr[a]; k < P.lrr_ptr[a + 1]; ++k) {
@@ -624,8 +673,6 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
     TRY(upload(h, esl, &eup));
     c.ent_sl = eup;
     int32_t* pp;
-    TRY(upload(h, perm, &pp));
-    c.row_perm = pp;
     // columns of A_L (CSC) ordered by decreasing length within each instance,
     // so the four columns a warp takes together have similar lengths
     std::vector<int32_t> cperm(std::max<int32_t>(h->TL, 1), 0);
@@ -804,8 +851,12 @@ int copy_iterate_out(sos_handle* h, const DevPlan<T>& p, std::vector<double>& ux
   CK(cudaStreamSynchronize(h->stream));
   ux.assign(a.begin(), a.end());
   vx.assign(b.begin(), b.end());
-  uy.assign(c.begin(), c.end());
-  vy.assign(dd.begin(), dd.end());
+  uy.resize(h->M);
+  vy.resize(h->M);
+  for (int64_t q = 0; q < h->M; ++q) {  // back to the order of the constraint rows
+    uy[h->row_perm[q]] = c[q];
+    vy[h->row_perm[q]] = dd[q];
+  }
   return SOS_OK;
 }
 
@@ -836,10 +887,15 @@ int copy_iterate_in(sos_handle* h, const DevPlan<T>& p, const double* u, const d
     kappa[i] = v[pos];
     pos += 1;
   }
+  std::vector<T> cq(h->M), dq(h->M);
+  for (int64_t q = 0; q < h->M; ++q) {  // device rows are ordered by length
+    cq[q] = c[h->row_perm[q]];
+    dq[q] = dd[h->row_perm[q]];
+  }
   CK(cudaMemcpyAsync(p.ux, a.data(), sizeof(T) * h->NX, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(p.vx, b.data(), sizeof(T) * h->NX, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(p.uy, c.data(), sizeof(T) * h->M, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(p.vy, dd.data(), sizeof(T) * h->M, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(p.uy, cq.data(), sizeof(T) * h->M, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(p.vy, dq.data(), sizeof(T) * h->M, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->d64.tau, tau.data(), sizeof(double) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->d64.kappa, kappa.data(), sizeof(double) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));

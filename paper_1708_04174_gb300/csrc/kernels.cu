@@ -68,14 +68,13 @@ __device__ __forceinline__ double d(T x) {
 // multiply-add per A_L nonzero.  The row index must advance in whole warps.
 template <typename T>
 __device__ void d_rows_r(const DevPlan<T>& p, int64_t g0, int64_t stride) {
-  for (int64_t q = g0; q < p.M; q += stride) {  // q: slot, a: row
-    const int64_t a = p.row_perm[q];
+  for (int64_t a = g0; a < p.M; a += stride) {
     const int i = p.row_inst[a];
     if (!p.active[i]) continue;
     const double om3 = p.tau[i] + p.kappa[i];
     double acc = d(p.uy[a]) + d(p.vy[a]) + p.b[a] * om3;  // w2hat
-    const int64_t sl = q >> 5;
-    const int lane = static_cast<int>(q & 31);
+    const int64_t sl = a >> 5;
+    const int lane = static_cast<int>(a & 31);
     const int ne = p.row_ptr[a + 1] - p.row_ptr[a];
     const uint32_t* ent = p.ent_sl + p.ent_sl_off[sl] + lane;
 #pragma unroll 4
@@ -83,7 +82,8 @@ __device__ void d_rows_r(const DevPlan<T>& p, int64_t g0, int64_t stride) {
       const uint32_t v = ent[32 * k];
       const uint32_t e = v & ~kOffDiagBit;
       const double w = d(p.ux[e]) + d(p.vx[e]);
-      acc -= (v & kOffDiagBit) ? kSqrt2 * w : w;
+      const double wt = (v & kOffDiagBit) ? kSqrt2 : 1.0;  // selected, not multiplied
+      acc = fma(-wt, w, acc);                              // two FP64 operations per entry
     }
     const int nl = p.lrr_ptr[a + 1] - p.lrr_ptr[a];
     const int64_t lb = p.lr_sl_off[sl] + lane;
@@ -162,12 +162,11 @@ __global__ void k_woodbury(DevPlan<T> p) {
 
 template <typename T>
 __device__ void d_rows_sigma2(const DevPlan<T>& p, int64_t g0, int64_t stride) {
-  for (int64_t q = g0; q < p.M; q += stride) {  // q: slot, a: row (slots advance in whole warps)
-    const int64_t a = p.row_perm[q];
+  for (int64_t a = g0; a < p.M; a += stride) {  // rows advance in whole warps
     if (!p.active[p.row_inst[a]]) continue;
     double acc = 0.0;
     const int nl = p.lrr_ptr[a + 1] - p.lrr_ptr[a];
-    const int64_t lb = p.lr_sl_off[q >> 5] + (q & 31);
+    const int64_t lb = p.lr_sl_off[a >> 5] + (a & 31);
 #pragma unroll 4
     for (int k = 0; k < nl; ++k) acc += p.lr_sl_val[lb + 32 * k] * p.zlr[p.lr_sl_col[lb + 32 * k]];
     p.sig2[a] = p.xP[a] - acc * p.pinv[a];

@@ -41,11 +41,10 @@ struct DevPlan {
   const double* lr_g = nullptr;
   const double* linv = nullptr;
   const double* linv_t = nullptr;  // L^-1 of each instance, column-major (first triangular pass)
-  // sliced copies of the row lists: row_perm[q] is the row in slot q (rows
-  // of an instance ordered by decreasing length), 32 consecutive slots per
-  // slice, element k of slot q at off[q / 32] + 32 k + q % 32, so a warp's
-  // loads coalesce and its lanes run similar lengths
-  const int32_t* row_perm = nullptr;
+  // sliced copies of the row lists: rows are numbered in order of decreasing
+  // length within each instance, 32 consecutive rows per slice, element k of
+  // row a at off[a / 32] + 32 k + a % 32, so a warp's loads coalesce and its
+  // lanes run similar lengths
   const int32_t* col_perm = nullptr;  // A_L columns by decreasing length within each instance
   const int64_t* ent_sl_off = nullptr;  // plain Gram entries (as row_ent)
   const uint32_t* ent_sl = nullptr;
