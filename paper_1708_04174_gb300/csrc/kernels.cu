@@ -628,8 +628,12 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
       __syncthreads();
       if (last_rot != round_id) continue;  // no rotation this round (uniform)
       rotated = true;
+      // A <- J^T A J as 2x2-block tasks; V <- V J as (pair, row group)
+      // tasks: each loads its rotation once and walks the rows g, g + G, ...
+      // (consecutive threads on consecutive rows: odd ld, no bank conflicts)
       const int nblk = H * H;
-      for (int task = tid; task < nblk + N * H; task += nt) {
+      const int G = nt / H > 1 ? nt / H : 1;  // row groups per pair
+      for (int task = tid; task < nblk + G * H; task += nt) {
         if (task < nblk) {
           int k1, k2;
           divmod_small(task, H, invH, k1, k2);
@@ -662,15 +666,17 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
           A[p2 * ld + q1] = z21;
           A[q2 * ld + q1] = z22;
         } else {
-          int row, k;
-          divmod_small(task - nblk, H, invH, row, k);
+          int k, g;
+          divmod_small(task - nblk, G, 1.0f / static_cast<float>(G), k, g);
           const TC s = rs[k];
           if (s == static_cast<TC>(0)) continue;
           const TC c = rc[k];
           const int pp = rp[k], qq = rq[k];
-          const TC vp = V[row * ld + pp], vq = V[row * ld + qq];
-          V[row * ld + pp] = c * vp - s * vq;
-          V[row * ld + qq] = s * vp + c * vq;
+          for (int row = g; row < N; row += G) {
+            const TC vp = V[row * ld + pp], vq = V[row * ld + qq];
+            V[row * ld + pp] = c * vp - s * vq;
+            V[row * ld + qq] = s * vp + c * vq;
+          }
         }
       }
       __syncthreads();
