@@ -603,7 +603,7 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
 
   int sweeps_done = 0;
   int round_id = 0;
-  const float invH = 1.0f / static_cast<float>(H);
+  const float invH1 = 1.0f / static_cast<float>(H + 1);
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
     bool rotated = false;
     sweeps_done = sweep + 1;
@@ -631,13 +631,21 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
       // A <- J^T A J as 2x2-block tasks; V <- V J as (pair, row group)
       // tasks: each loads its rotation once and walks the rows g, g + G, ...
       // (consecutive threads on consecutive rows: odd ld, no bank conflicts)
-      const int nblk = H * H;
+      // the H (H + 1) / 2 pair combinations k1 <= k2 are enumerated with
+      // rows r and H - 1 - r paired (H + 1 combinations per paired row)
+      const int nblk = H * (H + 1) / 2;
       const int G = nt / H > 1 ? nt / H : 1;  // row groups per pair
       for (int task = tid; task < nblk + G * H; task += nt) {
         if (task < nblk) {
-          int k1, k2;
-          divmod_small(task, H, invH, k1, k2);
-          if (k1 > k2) continue;
+          int rr, cc, k1, k2;
+          divmod_small(task, H + 1, invH1, rr, cc);
+          if (cc < H - rr) {
+            k1 = rr;
+            k2 = rr + cc;
+          } else {
+            k1 = H - 1 - rr;
+            k2 = k1 + cc - (H - rr);
+          }
           const int p1 = rp[k1], q1 = rq[k1], p2 = rp[k2], q2 = rq[k2];
           const TC c1 = rc[k1], s1 = rs[k1];
           if (k1 == k2) {

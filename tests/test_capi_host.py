@@ -91,3 +91,12 @@ def test_setup_rejects_bad_input(capi):
     bad = SOSProgram(n=1, w=np.array([1.0]), constraints=[Constraint(2, {(0,): 1.0}, [{(0,): 1.0}], [Block(2)])])
     with pytest.raises(RuntimeError, match="not among"):
         capi.host_plan(bad)
+
+
+@pytest.mark.parametrize("kw,msg", [(dict(warm_restart=-1), "warm_restart"), (dict(infeas_tol=-1.0), "infeas_tol"),
+                                    (dict(precision=7), "precision"), (dict(solve_mode=3), "solve_mode"),
+                                    (dict(large_method=5), "large_method")])
+def test_setup_rejects_bad_options(capi, kw, msg):
+    # option checks run before any CUDA call, so they need no GPU
+    with pytest.raises(RuntimeError, match=msg):
+        capi.Solver(W.quartic_pop(3, 0), **kw)
