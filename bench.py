@@ -324,7 +324,10 @@ def batched_arm(args):
     fp32_peak = 69700.0
     roof = {"kernel": "k_psd_small<double,float> (FP32 Jacobi + compensated refinement, one CTA per block)",
             "bound": "alu", "achieved": flops / (stage_ms["psd_small"] / 1e3) / 1e9, "peak": fp32_peak,
-            "unit": "GFLOP/s", "frac": flops / (stage_ms["psd_small"] / 1e3) / 1e9 / fp32_peak, "traffic": None,
+            "unit": "GFLOP/s", "frac": flops / (stage_ms["psd_small"] / 1e3) / 1e9 / fp32_peak,
+            # DRAM bytes of the stage's five class launches of one iteration (ncu
+            # capture summarised in profiles/lyapunov_batch4096_launches_and_kernels.md)
+            "traffic": 6534400 + 18487040 + 12453888 + (28714240 + 616448) + (68750848 + 19795456),
             "note": "algorithmic flops 9 N^3 per block over all 8192 blocks; peak = FMA-loop FP32 rate measured "
                     "on this GB300", "stage_ms": stage_ms,
             "stage_bytes": {"affine": s.stage_bytes(0), "psd_small": s.stage_bytes(1)}}
@@ -513,9 +516,12 @@ def main():
         flops = sum(9.0 * N ** 3 for N in big)
         dom_ms = stage_ms["psd_large"]
         fp64_peak = 1190.0 if prec == capi.PREC_FP64 else 69700.0
+        # DRAM bytes of one launch, from the ncu capture summarised in
+        # profiles/k_psd_large_fp64_ball_pop_n20.md (FP64 kernel only)
+        traffic = 465152 + 421632 if prec == capi.PREC_FP64 and args.workload == "ball_pop_n20" else None
         roof = {"kernel": "k_psd_large (grid Jacobi eigen-projection)", "bound": "alu",
                 "achieved": flops / (dom_ms / 1e3) / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
-                "frac": flops / (dom_ms / 1e3) / 1e9 / fp64_peak, "traffic": None,
+                "frac": flops / (dom_ms / 1e3) / 1e9 / fp64_peak, "traffic": traffic,
                 "note": f"algorithmic flops 9 N^3 per N x N eigen-projection (N={big}); peak = FMA-loop "
                         f"{'FP64' if prec == capi.PREC_FP64 else 'FP32'} rate measured on this GB300"}
     else:
