@@ -581,7 +581,10 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
     A[i * ld + j] = a;
     A[j * ld + i] = a;
   }
-  const TC thr = static_cast<TC>(sqrt(block_sum(nrm, red))) * teps<TC>();
+  // FP64: sweeps stop below 1e-10 |W|_F and the reconstruction corrects
+  // for the remaining off-diagonal to first order; FP32: to the roundoff
+  // (the mixed form's refinement then corrects it).
+  const TC thr = static_cast<TC>(sqrt(block_sum(nrm, red))) * (sizeof(TC) == 8 ? static_cast<TC>(1e-10) : teps<TC>());
   if (warm) {
     for (int q = tid; q < N * N; q += nt) {  // T1 = W V
       const int i = q / N, j = q - i * N;
@@ -703,14 +706,47 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
       if (tid == 0) wm.count[bid] = warm ? wc + 1 : 1;
     }
   } else {
-  // P_S+(W) = V max(Lambda, 0) V^T; v = u - W (in the storage type)
+  // P_S+(W) = V max(Lambda, 0) V^T; v = u - W (in the storage type).  FP64:
+  // V M V^T with M = diag(max(b_kk, 0)) + G o offdiag(B), the first-order
+  // projection of the nearly diagonal B (T1 = V M first).
   for (int k = tid; k < N; k += nt) lam[k] = fmax(A[k * ld + k], static_cast<TC>(0));
   __syncthreads();
+  if constexpr (sizeof(TC) == 8) {
+    TC* bdiag = rc;  // rc, rs, rt are contiguous: 3 H >= N entries, free after the sweeps
+    for (int k = tid; k < N; k += nt) bdiag[k] = A[k * ld + k];
+    __syncthreads();
+    for (int q = tid; q < N * N; q += nt) {  // A <- M in place (each entry from itself and the diagonal)
+      const int l = q / N, k = q - l * N;
+      const TC bl = bdiag[l], bk = bdiag[k];
+      TC m;
+      if (l == k)
+        m = lam[k];
+      else if (bl > 0 && bk > 0)
+        m = A[l * ld + k];
+      else if (bl <= 0 && bk <= 0)
+        m = 0;
+      else
+        m = (lam[l] - lam[k]) / (bl - bk) * A[l * ld + k];  // |bl - bk| > 0 here
+      A[l * ld + k] = m;
+    }
+    __syncthreads();
+    for (int q = tid; q < N * N; q += nt) {  // T1 = V M
+      const int i = q / N, k = q - i * N;
+      TC acc = 0;
+      for (int l = 0; l < N; ++l) acc += V[i * ld + l] * A[l * ld + k];
+      T1[i * ld + k] = acc;
+    }
+    __syncthreads();
+  }
   for (int q = tid; q < N * N; q += nt) {
     const int i = q / N, j = q - i * N;
     if (i < j) continue;
     TC u = 0;
-    for (int k = 0; k < N; ++k) u += V[i * ld + k] * lam[k] * V[j * ld + k];
+    if constexpr (sizeof(TC) == 8) {
+      for (int k = 0; k < N; ++k) u += T1[i * ld + k] * V[j * ld + k];
+    } else {
+      for (int k = 0; k < N; ++k) u += V[i * ld + k] * lam[k] * V[j * ld + k];
+    }
     const int64_t kk = packed_index(i, j, N);
     const T w = proj_input(p, bd, kk, i != j, s_sm);
     const T uu = (i != j) ? static_cast<T>(d(u) * kSqrt2) : static_cast<T>(u);
@@ -720,6 +756,7 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
     if (bd.kind == kWeighted) p.wl[bd.lr_first + kk] = d(uu) + d(vv);  // w1_hat of the next iteration (c = 0)
   }
   if (gV) {  // keep V for the next iteration: V (3 I - V^T V) / 2
+    __syncthreads();  // T1 may still be read by the reconstruction above
     for (int q = tid; q < N * N; q += nt) {
       const int i = q / N, j = q - i * N;
       TC acc = 0;
@@ -874,7 +911,11 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
   if (!grid_barrier(L.bar, (++gen) * G, err)) return;
   double tot = 0.0;
   for (unsigned c = 0; c < G; ++c) tot += __ldcg(L.partial + c);
-  const TC thr = static_cast<TC>(sqrt(tot)) * teps<TC>();
+  // FP64: the sweeps stop once every off-diagonal entry is below
+  // 1e-10 |W|_F and the reconstruction corrects for the rest to first order
+  // (second-order error <= |E|^2 / gap, and never above |E|); FP32 sweeps run
+  // to the unit roundoff.
+  const TC thr = static_cast<TC>(sqrt(tot)) * (sizeof(TC) == 8 ? static_cast<TC>(1e-10) : teps<TC>());
 
   const int nt = (Np + 15) / 16;
   TC* cur = Wf;
@@ -999,8 +1040,39 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
     if (!sweep_rot) break;
   }
 
-  // U = V max(diag B, 0) V^T on lower tiles; write u and v = u - W
   const int ntl = (N + 15) / 16;
+  if constexpr (sizeof(TC) == 8) {
+    // U = V M V^T with M = diag(max(b_kk, 0)) + G o offdiag(B): the first-order
+    // projection of the nearly diagonal B (the derivative of the eigenvalue
+    // map max(., 0) at diag(B); g_lk = 1 when both diagonal entries are
+    // positive, 0 when neither is, in (0, 1) across zero).  M into B1 (free
+    // in FP64), then T1 = V M.
+    for (int64_t q = gt; q < static_cast<int64_t>(Np) * Np; q += gs) {
+      const int l = static_cast<int>(q / Np), k = static_cast<int>(q - static_cast<int64_t>(l) * Np);
+      TC m = 0;
+      if (l < N && k < N) {
+        const TC bl = ldg_cg(cur + static_cast<int64_t>(l) * Np + l), bk = ldg_cg(cur + static_cast<int64_t>(k) * Np + k);
+        if (l == k)
+          m = fmax(bl, static_cast<TC>(0));
+        else if (bl > 0 && bk > 0)
+          m = ldg_cg(cur + q);
+        else if (bl <= 0 && bk <= 0)
+          m = 0;
+        else
+          m = (fmax(bl, static_cast<TC>(0)) - fmax(bk, static_cast<TC>(0))) / (bl - bk) * ldg_cg(cur + q);  // |bl - bk| > 0
+      }
+      L.B1[q] = m;
+    }
+    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    for (int tile = blockIdx.x; tile < nt * nt; tile += G) {
+      const int ti = tile / nt, tj = tile - ti * nt;
+      const TC v = tile_mm(V, L.B1, Np, ti, tj, 0, sA, sB);
+      const int i = ti * 16 + (threadIdx.x >> 4), j = tj * 16 + (threadIdx.x & 15);
+      if (i < Np && j < Np) L.T1[static_cast<int64_t>(i) * Np + j] = v;
+    }
+    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+  }
+  // U = (V M or V max(diag B, 0)) V^T on lower tiles; write u and v = u - W
   for (int tile = blockIdx.x; tile < ntl * ntl; tile += G) {
     const int ti = tile / ntl, tj = tile - ti * ntl;
     if (ti < tj) continue;
@@ -1010,9 +1082,13 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
     for (int k0 = 0; k0 < N; k0 += 16) {
       const int gk = k0 + tx;
       const int ri = ti * 16 + ty, rj = tj * 16 + ty;
-      TC lk = 0;
-      if (gk < N) lk = fmax(ldg_cg(cur + static_cast<int64_t>(gk) * Np + gk), static_cast<TC>(0));
-      sA[ty * 17 + tx] = (ri < N && gk < N) ? ldg_cg(V + static_cast<int64_t>(ri) * Np + gk) * lk : static_cast<TC>(0);
+      if constexpr (sizeof(TC) == 8) {
+        sA[ty * 17 + tx] = (ri < N && gk < N) ? ldg_cg(L.T1 + static_cast<int64_t>(ri) * Np + gk) : static_cast<TC>(0);
+      } else {
+        TC lk = 0;
+        if (gk < N) lk = fmax(ldg_cg(cur + static_cast<int64_t>(gk) * Np + gk), static_cast<TC>(0));
+        sA[ty * 17 + tx] = (ri < N && gk < N) ? ldg_cg(V + static_cast<int64_t>(ri) * Np + gk) * lk : static_cast<TC>(0);
+      }
       sB[ty * 17 + tx] = (rj < N && gk < N) ? ldg_cg(V + static_cast<int64_t>(rj) * Np + gk) : static_cast<TC>(0);
       __syncthreads();
 #pragma unroll
