@@ -582,9 +582,12 @@ __device__ void d_psd_small(const DevPlan<T>& p, int bid, const SmallWarm<TC>& w
     A[j * ld + i] = a;
   }
   // FP64: sweeps stop below 1e-10 |W|_F and the reconstruction corrects
-  // for the remaining off-diagonal to first order; FP32: to the roundoff
-  // (the mixed form's refinement then corrects it).
-  const TC thr = static_cast<TC>(sqrt(block_sum(nrm, red))) * (sizeof(TC) == 8 ? static_cast<TC>(1e-10) : teps<TC>());
+  // for the remaining off-diagonal to first order.  FP32 with the refinement
+  // (mixed form): stop below 4 eps |W|_F, the refinement's first-order
+  // correction absorbs the rest (same ~1e-7 |W| result, one sweep fewer);
+  // plain FP32: to the roundoff.
+  const TC thr = static_cast<TC>(sqrt(block_sum(nrm, red))) *
+                 (sizeof(TC) == 8 ? static_cast<TC>(1e-10) : (kRefine ? 4 * teps<TC>() : teps<TC>()));
   if (warm) {
     for (int q = tid; q < N * N; q += nt) {  // T1 = W V
       const int i = q / N, j = q - i * N;
