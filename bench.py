@@ -47,6 +47,16 @@ def make_program(name):
     return getattr(W, fn)(n, seed)
 
 
+def clock_dir() -> str:
+    """Where the nvidia-smi clock samples of the timed region are written
+    (SOS_CLOCKS_DIR, else the system's temporary directory)."""
+    import tempfile
+
+    d = os.environ.get("SOS_CLOCKS_DIR") or tempfile.gettempdir()
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
 class L2Flush:
     """Evicts L2 between timed steps: writes a 256 MB buffer (> 129 MB of L2)
     and then reads a second one, so L2 holds clean unrelated lines and the
@@ -303,8 +313,7 @@ def batched_arm(args):
     t_setup = time.perf_counter() - t0
     s.iterate(args.warmup)
     s.sync()
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_rank0.csv")
-                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_rank0.csv")
+    clk = ClockSampler(os.path.join(clock_dir(), "clocks_rank0.csv"))
     torch.cuda.synchronize()
     with clk:
         step_ms = timed(s, lambda: s.iterate(1), args.steps)
@@ -467,8 +476,7 @@ def main():
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    clk = ClockSampler(os.path.join(clock_dir(), f"clocks_rank{rank}.csv"))
     barrier()
     with clk:
         t_wall0 = time.perf_counter()
