@@ -12,7 +12,7 @@ roofline of the dominant kernel, the CPU oracle as a bounded baseline,
 time to a 1e-4 residual for the plain FP64 form and the FP32 form, and SM
 clocks sampled during the timed region.
 
-``--impl reference`` times the CPU oracle (the reference arm of this build)
+``--impl reference`` times the CPU oracle (the reference arm)
 on the same workload and metric.
 """
 
@@ -338,7 +338,7 @@ def batched_arm(args):
             # capture summarised in profiles/lyapunov_batch4096_launches_and_kernels.md)
             "traffic": 6534400 + 18487040 + 12453888 + (28714240 + 616448) + (68750848 + 19795456),
             "note": "algorithmic flops 9 N^3 per block over all 8192 blocks; peak = FMA-loop FP32 rate measured "
-                    "on this GB300", "stage_ms": stage_ms,
+                    "on GB300", "stage_ms": stage_ms,
             "stage_bytes": {"affine": s.stage_bytes(0), "psd_small": s.stage_bytes(1)}}
     tuning = s.tuning()
     launches = s.launches_per_iteration()
@@ -531,7 +531,7 @@ def main():
                 "achieved": flops / (dom_ms / 1e3) / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
                 "frac": flops / (dom_ms / 1e3) / 1e9 / fp64_peak, "traffic": traffic,
                 "note": f"algorithmic flops 9 N^3 per N x N eigen-projection (N={big}); peak = FMA-loop "
-                        f"{'FP64' if prec == capi.PREC_FP64 else 'FP32'} rate measured on this GB300"}
+                        f"{'FP64' if prec == capi.PREC_FP64 else 'FP32'} rate measured on GB300"}
     else:
         small = [N for N in blocks if N not in big]
         flops = sum(9.0 * N ** 3 for N in small)
@@ -540,7 +540,7 @@ def main():
         roof = {"kernel": "k_psd_small (shared-memory Jacobi eigen-projection)", "bound": "alu",
                 "achieved": flops / (dom_ms / 1e3) / 1e9, "peak": peak, "unit": "GFLOP/s",
                 "frac": flops / (dom_ms / 1e3) / 1e9 / peak, "traffic": None,
-                "note": "algorithmic flops 9 N^3 per block; peak = FMA-loop rate measured on this GB300"}
+                "note": "algorithmic flops 9 N^3 per block; peak = FMA-loop rate measured on GB300"}
     roof["stage_ms"] = stage_ms
 
     # end-to-end through the C-ABI with host buffers, on a fresh handle over
@@ -573,7 +573,7 @@ def main():
            "wall_s": t_wall, "e2e": e2e, "roofline": roof,
            "gpu_launches": None}
     out["gpu_launches"] = int(solver.launches_per_iteration() * args.steps)
-    out["roofline"]["peak_source"] = "FMA-loop probe on this GB300 (FP64 1.19 TFLOP/s, FP32 69.7 TFLOP/s)"
+    out["roofline"]["peak_source"] = "FMA-loop probe on GB300 (FP64 1.19 TFLOP/s, FP32 69.7 TFLOP/s)"
     out["clocks"] = clk.summary(local)
 
     # the FP32-projection form (tensor-core Newton-Schulz for the large block)

@@ -377,7 +377,7 @@ __device__ __forceinline__ void dot2_step(float a, float b, float& s, float& c) 
 // Ritz values are positive, 0 when neither is, and in (0, 1) across zero).
 // The products that need more than FP32 use the compensated dot product
 // above (2 N^3 steps of ~10 FP32 operations), not FP64: FP64 runs at under
-// 2% of the FP32 rate on this GPU.  On entry V holds the Jacobi
+// 2% of the FP32 rate on GB300.  On entry V holds the Jacobi
 // eigenvectors; on exit A holds V'.  The pair copy of W and then W V' live
 // where V and T1 were (2 Np ld floats >= 2 N^2); M is held in registers
 // until W V' is dead and then written where T1 was, so the refinement needs
