@@ -1208,48 +1208,67 @@ __device__ __forceinline__ void ns_stage(const float* M, int Np, int r0, int k0,
 }
 
 struct NsState {
-  uint64_t* mbar;
+  uint64_t* mbar;      // two barriers, one per operand buffer
   uint32_t tmem;
-  uint32_t phase;
+  uint32_t phase[2];   // phase awaited next on each barrier
+  int pending[2];      // a commit on that barrier not yet waited for
   bool ok;
 };
 
-constexpr size_t kNsSmem = 3 * (kNsTM + kNsTN) * kNsKC * 2;  // three parts of both operand chunks
+constexpr size_t kNsSmem = 3 * (kNsTM + kNsTN) * kNsKC * 2;  // three parts of both operand chunks (one buffer)
 
 // acc[128 x 64] (TMEM) = A[m0.., :] * B[n0.., :]^T over k in [0, Np), with the
 // six products of the three-part split whose exponent sum is at most 2^-16.
+// Two operand buffers: the chunk k + 1 is loaded, split and stored while the
+// MMAs of chunk k run; a buffer is rewritten only after the MMAs that read it
+// (two chunks earlier) have completed.
 __device__ void ns_gemm(const float* A, const float* B, int Np, int m0, int n0, unsigned char* smem, NsState& st) {
-  unsigned char* a[3];
-  unsigned char* b[3];
-  for (int q = 0; q < 3; ++q) a[q] = smem + q * kNsTM * kNsKC * 2;
-  for (int q = 0; q < 3; ++q) b[q] = smem + 3 * kNsTM * kNsKC * 2 + q * kNsTN * kNsKC * 2;
   constexpr uint32_t LBO = 128, SBO = (kNsKC / 8) * 128;
   constexpr uint32_t idesc = tc::idesc_bf16(kNsTM, kNsTN);
   const int pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
-  for (int k0 = 0; k0 < Np; k0 += kNsKC) {
+  auto wait_buf = [&](int b) {  // uniform: every thread waits for the commit on barrier b
+    if (!st.pending[b]) return;
+    const bool good = st.ok ? tc::wait(st.mbar + b, st.phase[b]) : false;
+    if (good) {
+      st.phase[b] ^= 1u;
+      st.pending[b] = 0;
+    } else {
+      st.ok = false;  // left pending: the kernel's cleanup waits for it once more
+    }
+    tc::fence_after();
+  };
+  const int nk = Np / kNsKC;
+  for (int kc = 0; kc < nk; ++kc) {
+    const int b = kc & 1;
+    wait_buf(b);
+    unsigned char* base = smem + b * kNsSmem;
+    unsigned char* a[3];
+    unsigned char* bb[3];
+    for (int q = 0; q < 3; ++q) a[q] = base + q * kNsTM * kNsKC * 2;
+    for (int q = 0; q < 3; ++q) bb[q] = base + 3 * kNsTM * kNsKC * 2 + q * kNsTN * kNsKC * 2;
+    const int k0 = kc * kNsKC;
     ns_stage<kNsTM>(A, Np, m0, k0, a[0], a[1], a[2]);
-    ns_stage<kNsTN>(B, Np, n0, k0, b[0], b[1], b[2]);
+    ns_stage<kNsTN>(B, Np, n0, k0, bb[0], bb[1], bb[2]);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (threadIdx.x == 0 && st.ok) {
+    const bool issue = st.ok;
+    if (threadIdx.x == 0 && issue) {
       for (int s = 0; s < kNsKC / 16; ++s) {
         const uint32_t so = s * 2 * LBO;
         for (int q = 0; q < 6; ++q) {
           const uint32_t acc = (k0 > 0 || s > 0 || q > 0) ? 1u : 0u;
-          tc::mma(st.tmem, tc::desc(tc::smem_u32(a[pa[q]]) + so, LBO, SBO), tc::desc(tc::smem_u32(b[pb[q]]) + so, LBO, SBO),
+          tc::mma(st.tmem, tc::desc(tc::smem_u32(a[pa[q]]) + so, LBO, SBO), tc::desc(tc::smem_u32(bb[pb[q]]) + so, LBO, SBO),
                   idesc, acc);
         }
       }
-      tc::commit(st.mbar);
+      tc::commit(st.mbar + b);
     }
-    // every thread waits for the MMAs before the chunk buffers are rewritten
-    const bool good = st.ok ? tc::wait(st.mbar, st.phase) : false;
-    st.phase ^= 1u;
-    if (!good) st.ok = false;
-    tc::fence_after();
+    if (issue) st.pending[b] = 1;
   }
+  wait_buf(nk & 1);        // older of the last two commits first
+  wait_buf((nk + 1) & 1);
 }
 
 
@@ -1262,7 +1281,7 @@ __host__ __device__ __forceinline__ int ns_tiles(int N) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch S) {
   extern __shared__ __align__(1024) unsigned char nsm[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   __shared__ double red[40];
   const BlockDesc bd = p.blocks[bid];
@@ -1283,11 +1302,13 @@ __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch
   const int m0 = ti * kNsTM, n0 = rem * kNsTN;
 
   NsState st;
-  st.mbar = &mbar;
-  st.phase = 0;
+  st.mbar = mbar;
+  st.phase[0] = st.phase[1] = 0;
+  st.pending[0] = st.pending[1] = 0;
   st.ok = true;
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar[1])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (threadIdx.x < 32) {
@@ -1413,7 +1434,9 @@ __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch
 #undef NS_SYNC
   // cleanup on every path: MMAs still in flight after a failed wait get one
   // more bounded wait, then the tensor memory is released
-  if (!st.ok) tc::wait(st.mbar, st.phase ^ 1u);
+  if (!st.ok)
+    for (int b = 0; b < 2; ++b)
+      if (st.pending[b]) tc::wait(st.mbar + b, st.phase[b]);
   tc::fence_before();
   __syncthreads();
   if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(st.tmem), "r"(kNsTN));
@@ -1815,18 +1838,18 @@ cudaError_t launch_persistent(const DevPlan<T>& p, const PersistArgs<TC>& a, int
 
 int ns_grid(int N) { return ns_tiles(N); }
 int ns_padded(int N) { return ns_np(N); }
-size_t ns_smem_bytes() { return kNsSmem; }
+size_t ns_smem_bytes() { return 2 * kNsSmem; }
 
 template <typename T>
 cudaError_t launch_psd_ns(const DevPlan<T>& p, int bid, int N, const NsScratch& S, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_psd_ns<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kNsSmem));
+  cudaError_t e = cudaFuncSetAttribute(k_psd_ns<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(2 * kNsSmem));
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(S.bar, 0, 2 * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ns_tiles(N));
   cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = kNsSmem;
+  cfg.dynamicSmemBytes = 2 * kNsSmem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
