@@ -245,7 +245,8 @@ def warmstart_arm(args):
     per_plain = t_plain / len(sample)
     per_warm = t_warm / 1024
     obj_err = np.array([abs(a["obj_primal"] - b["obj_primal"]) / max(1.0, abs(b["obj_primal"]))
-                        for a, b in zip(warm, cold)])
+                        for a, b in zip(warm, cold)
+                        if a["status"] == capi.SOLVED and b["status"] == capi.SOLVED])  # members solved by both
     line = {"metric": "time to a 1e-4 residual per instance (learned warm start + FP32 projections + batched)",
             "value": per_warm, "unit": "s/instance", "n_gpus": 1, "steps": 1, "warmup": 0,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64 iterates, f32 proj",
