@@ -79,7 +79,7 @@ __device__ void d_rows_r(const DevPlan<T>& p, int64_t g0, int64_t stride) {
     const uint32_t* ent = p.ent_sl + p.ent_sl_off[sl] + lane;
 #pragma unroll 4
     for (int k = 0; k < ne; ++k) {
-      const uint32_t v = ent[32 * k];
+      const uint32_t v = __ldcs(ent + 32 * k);  // read once: streaming load
       const uint32_t e = v & ~kOffDiagBit;
       const double w = d(p.ux[e]) + d(p.vx[e]);
       const double wt = (v & kOffDiagBit) ? kSqrt2 : 1.0;  // selected, not multiplied
@@ -88,7 +88,7 @@ __device__ void d_rows_r(const DevPlan<T>& p, int64_t g0, int64_t stride) {
     const int nl = p.lrr_ptr[a + 1] - p.lrr_ptr[a];
     const int64_t lb = p.lr_sl_off[sl] + lane;
 #pragma unroll 4
-    for (int k = 0; k < nl; ++k) acc -= p.lr_sl_val[lb + 32 * k] * p.wl[p.lr_sl_col[lb + 32 * k]];
+    for (int k = 0; k < nl; ++k) acc -= __ldcs(p.lr_sl_val + lb + 32 * k) * p.wl[__ldcs(p.lr_sl_col + lb + 32 * k)];
     p.xP[a] = acc * p.pinv[a];
   }
 }
@@ -111,7 +111,7 @@ __device__ void d_lr_y(const DevPlan<T>& p, int warp, int nwarps) {
     if (on) {
       const int k1 = p.lr_ptr[j + 1];
 #pragma unroll 4
-      for (int k = p.lr_ptr[j] + sub; k < k1; k += 8) acc += p.lr_val[k] * p.xP[p.lr_row[k]];
+      for (int k = p.lr_ptr[j] + sub; k < k1; k += 8) acc += __ldcs(p.lr_val + k) * p.xP[__ldcs(p.lr_row + k)];
     }
     acc += __shfl_xor_sync(0xffffffffu, acc, 4);
     acc += __shfl_xor_sync(0xffffffffu, acc, 2);
@@ -168,7 +168,7 @@ __device__ void d_rows_sigma2(const DevPlan<T>& p, int64_t g0, int64_t stride) {
     const int nl = p.lrr_ptr[a + 1] - p.lrr_ptr[a];
     const int64_t lb = p.lr_sl_off[a >> 5] + (a & 31);
 #pragma unroll 4
-    for (int k = 0; k < nl; ++k) acc += p.lr_sl_val[lb + 32 * k] * p.zlr[p.lr_sl_col[lb + 32 * k]];
+    for (int k = 0; k < nl; ++k) acc += __ldcs(p.lr_sl_val + lb + 32 * k) * p.zlr[__ldcs(p.lr_sl_col + lb + 32 * k)];
     p.sig2[a] = p.xP[a] - acc * p.pinv[a];
   }
 }
