@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -421,6 +422,59 @@ def batched_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# Published numbers for the constrained POP of eq. (46) (context only: a
+# MATLAB solver on a 2.8 GHz Intel Core i7, tolerance 1e-3, at most 2000
+# iterations).  Table I: CDCS-sos total solve time in seconds; Table II:
+# terminal objective of the interior-point solvers and of CDCS-sos.
+PAPER_TABLE1_CDCS_S = {10: 0.4, 12: 0.7, 14: 1.4, 17: 3.5, 20: 8.5, 24: 22.8, 29: 67.1, 35: 216.9, 42: 686.6}
+PAPER_TABLE2_IPM = {10: -9.11, 12: -11.12, 14: -13.12, 17: -16.12, 20: -19.12, 24: -23.12}
+PAPER_TABLE2_CDCS = {10: -9.10, 12: -11.11, 14: -13.12, 17: -16.06, 20: -19.08, 24: -23.15, 29: -28.17, 35: -34.08,
+                     42: -41.05}
+
+
+def paper_pop_arm(args):
+    """The constrained POP of eq. (46) on the unit ball (Lasserre order 2,
+    Gram N = C(n+2, 2) plus the weighted multiplier block) for the n of the
+    paper's Table I, solved at the paper's stopping rule (tolerance 1e-3, at
+    most 2000 iterations) in the plain FP64 form and the mixed form.  Wall
+    time of sos_solve (setup excluded) next to the paper's CDCS-sos times
+    (other hardware: context), terminal objective next to Table II."""
+    from instances import workloads as W
+    from paper_1708_04174_gb300 import capi
+
+    ns = [10, 12, 14, 17, 20, 24, 29, 35, 42] if not args.paper_n else [int(x) for x in args.paper_n.split(",")]
+    rows = []
+    for n in ns:
+        prog = W.paper_pop(n)
+        entry = {"n": n, "paper_cdcs_s": PAPER_TABLE1_CDCS_S.get(n), "paper_ipm_obj": PAPER_TABLE2_IPM.get(n),
+                 "paper_cdcs_obj": PAPER_TABLE2_CDCS.get(n)}
+        for name, prec in (("fp64", capi.PREC_FP64), ("mixed", capi.PREC_MIXED)):
+            t0 = time.perf_counter()
+            s = capi.Solver(prog, precision=prec, k_check=10)
+            t_setup = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            r = s.solve(1e-3, 2000, want_solution=False)[0]
+            dt = time.perf_counter() - t0
+            d = s.dims[0]
+            s.close()
+            entry[name] = {"solve_s": dt, "setup_s": t_setup, "iters": r["iters"], "status": r["status"],
+                           "objective": -r["obj_primal"], "res": max(r["res_primal"], r["res_dual"], r["gap"])}
+            entry["m"] = d[1]
+        entry["N"] = math.comb(n + 2, 2)
+        if entry["paper_cdcs_s"]:
+            entry["speedup_fp64_vs_paper_cdcs"] = entry["paper_cdcs_s"] / entry["fp64"]["solve_s"]
+        rows.append(entry)
+        print(json.dumps({"n": n, "fp64_s": entry["fp64"]["solve_s"], "mixed_s": entry["mixed"]["solve_s"],
+                          "obj": entry["fp64"]["objective"]}), file=sys.stderr, flush=True)
+    line = {"metric": "time to solve eq. (46) at tolerance 1e-3 (paper's Table I workload, plain FP64)",
+            "value": rows[0]["fp64"]["solve_s"] if len(rows) == 1 else None, "unit": "s", "n_gpus": 1,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "paper_pop_table1", "tol": 1e-3, "max_iter": 2000,
+                       "note": "paper times: MATLAB CDCS-sos on a 2.8 GHz Intel Core i7 (context, other hardware)"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,7 +482,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="ball_pop_n20",
-                    choices=sorted(WORKLOADS) + ["parametric_warmstart", "lyapunov_batch4096"])
+                    choices=sorted(WORKLOADS) + ["parametric_warmstart", "lyapunov_batch4096", "paper_pop_table1"])
+    ap.add_argument("--paper-n", default="", help="comma-separated n for paper_pop_table1 (default: Table I's n)")
     ap.add_argument("--train", type=int, default=20000, help="training members (parametric_warmstart)")
     ap.add_argument("--epochs", type=int, default=200, help="training epochs (parametric_warmstart)")
     ap.add_argument("--max-iter", type=int, default=20000, help="iteration cap of every solve (parametric_warmstart)")
@@ -447,6 +502,8 @@ def main():
         return warmstart_arm(args)
     if args.workload == "lyapunov_batch4096":
         return batched_arm(args)
+    if args.workload == "paper_pop_table1":
+        return paper_pop_arm(args)
 
     import torch
 

@@ -715,7 +715,11 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   // projection classes: small blocks (shared-memory Jacobi) by size class, large blocks (grid Jacobi)
   const bool fp64 = h->precision == SOS_PREC_FP64;  // FP64 projections
   const int form = fp64 ? kFormFP64 : (h->precision == SOS_PREC_MIXED ? kFormMixed : kFormFP32);
-  const int small_cap = psd_small_max_n(form);
+  // A one-CTA FP64 Jacobi runs on a single SM's FP64 pipe; with one program
+  // (a few blocks) the grid path, which spreads each round over every SM, is
+  // faster from N > 32 on (N = 91: 4.5 -> ~1 ms per iteration).  Batches keep
+  // the one-CTA kernel, which fills the GPU with blocks.
+  const int small_cap = (fp64 && P.n_inst == 1 && h->solve_mode != 2) ? 32 : psd_small_max_n(form);
   constexpr int kClasses = 7;
   const int caps[kClasses] = {16, 32, 48, 64, 96, 112, 128};
   std::vector<std::vector<int32_t>> cls(kClasses);
