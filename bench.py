@@ -432,6 +432,54 @@ PAPER_TABLE2_CDCS = {10: -9.10, 12: -11.11, 14: -13.12, 17: -16.06, 20: -19.08, 
                      42: -41.05}
 
 
+# Table III: CDCS-sos total solve time (s) of the local Lyapunov search with a
+# quadratic V in the ball |x|^2 <= 0.1 (same hardware and stopping rule as
+# Table I; context only).
+PAPER_TABLE3_CDCS_S = {10: 0.3, 12: 0.4, 14: 0.6, 17: 1.1, 20: 2.4, 24: 5.1, 29: 14.3, 35: 37.4, 42: 92.8}
+
+
+def local_lyapunov_arm(args):
+    """Local stability of a random cubic system with a linearly stable origin
+    in the ball |x|^2 <= 0.1, quadratic V, Positivstellensatz multiplier
+    (instances.workloads.lyapunov_local, seed = n), for the n of the paper's
+    Table III, at tolerance 1e-3 and at most 2000 iterations, plain FP64 and
+    mixed; wall time of sos_solve next to the paper's CDCS-sos times (other
+    hardware: context)."""
+    from instances import workloads as W
+    from paper_1708_04174_gb300 import capi
+
+    ns = [10, 12, 14, 17, 20, 24, 29, 35, 42] if not args.paper_n else [int(x) for x in args.paper_n.split(",")]
+    rows = []
+    for n in ns:
+        prog = W.lyapunov_local(n, n)
+        entry = {"n": n, "N": math.comb(n + 2, 2), "paper_cdcs_s": PAPER_TABLE3_CDCS_S.get(n)}
+        for name, prec in (("fp64", capi.PREC_FP64), ("mixed", capi.PREC_MIXED)):
+            t0 = time.perf_counter()
+            s = capi.Solver(prog, precision=prec, k_check=10)
+            t_setup = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            r = s.solve(1e-3, 2000, want_solution=False)[0]
+            dt = time.perf_counter() - t0
+            d = s.dims[0]
+            s.close()
+            entry["m"], entry["t_eff"] = d[1], d[3]
+            entry[name] = {"solve_s": dt, "setup_s": t_setup, "iters": r["iters"], "status": r["status"],
+                           "trace_P": r["obj_primal"], "res": max(r["res_primal"], r["res_dual"], r["gap"])}
+        if entry["paper_cdcs_s"]:
+            entry["speedup_fp64_vs_paper_cdcs"] = entry["paper_cdcs_s"] / entry["fp64"]["solve_s"]
+        rows.append(entry)
+        print(json.dumps({"n": n, "fp64_s": entry["fp64"]["solve_s"], "mixed_s": entry["mixed"]["solve_s"],
+                          "status": [entry["fp64"]["status"], entry["mixed"]["status"]]}), file=sys.stderr, flush=True)
+    line = {"metric": "time to solve the local Lyapunov search at tolerance 1e-3 (paper's Table III workload shape, "
+                      "plain FP64)", "value": None, "unit": "s", "n_gpus": 1, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "lyapunov_local_table3", "tol": 1e-3, "max_iter": 2000, "r2": 0.1,
+                       "note": "paper times: MATLAB CDCS-sos on a 2.8 GHz Intel Core i7 on its own random systems "
+                               "(context)"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def paper_pop_arm(args):
     """The constrained POP of eq. (46) on the unit ball (Lasserre order 2,
     Gram N = C(n+2, 2) plus the weighted multiplier block) for the n of the
@@ -482,8 +530,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="ball_pop_n20",
-                    choices=sorted(WORKLOADS) + ["parametric_warmstart", "lyapunov_batch4096", "paper_pop_table1"])
-    ap.add_argument("--paper-n", default="", help="comma-separated n for paper_pop_table1 (default: Table I's n)")
+                    choices=sorted(WORKLOADS) + ["parametric_warmstart", "lyapunov_batch4096", "paper_pop_table1",
+                                                 "lyapunov_local_table3"])
+    ap.add_argument("--paper-n", default="",
+                    help="comma-separated n for paper_pop_table1 / lyapunov_local_table3 (default: the tables' n)")
     ap.add_argument("--train", type=int, default=20000, help="training members (parametric_warmstart)")
     ap.add_argument("--epochs", type=int, default=200, help="training epochs (parametric_warmstart)")
     ap.add_argument("--max-iter", type=int, default=20000, help="iteration cap of every solve (parametric_warmstart)")
@@ -504,6 +554,8 @@ def main():
         return batched_arm(args)
     if args.workload == "paper_pop_table1":
         return paper_pop_arm(args)
+    if args.workload == "lyapunov_local_table3":
+        return local_lyapunov_arm(args)
 
     import torch
 

@@ -263,6 +263,51 @@ def lyapunov_cubic(n: int, seed: int, eps: float = 1e-3, sigma: float = 0.1) -> 
                       name=f"lyapunov_cubic(n={n},seed={seed})", meta={"f": fx})
 
 
+def lyapunov_local(n: int, seed: int, r2: float = 0.1, eps: float = 1e-3, sigma: float = 1.0,
+                   cubic_terms: int = 0) -> SOSProgram:
+    """Local stability of x' = f(x) = A x + cubic(x) (A Hurwitz) in the ball
+    |x|^2 <= r2 with a quadratic V(x) = x^T P x, by the Positivstellensatz:
+
+        min trace(P)  s.t.  V - eps |x|^2 SOS                       (degree 2)
+                            -grad V . f - |x|^2 = s0(x) + s1(x) (r2 - |x|^2)
+                            s0 SOS (basis degree 2), s1 SOS (basis degree 1).
+
+    Each component of f gets ``cubic_terms`` (default n) random cubic
+    monomials with N(0, sigma^2) coefficients.  Decision variables: P_ij,
+    i <= j.  With sigma = 0 the multiplier vanishes at the optimum and P
+    solves A^T P + P A + I = 0 (when P >= eps I)."""
+    A = hurwitz_matrix(n, seed)
+    rng = np.random.default_rng(seed + 1)
+    cub = _support(n, 3, 3)
+    k = cubic_terms if cubic_terms > 0 else n
+    fx: List[Poly] = []
+    for r in range(n):
+        fr: Poly = {_unit(n, q): float(A[r, q]) for q in range(n) if A[r, q] != 0.0}
+        if sigma > 0.0:
+            for idx in rng.choice(len(cub), size=min(k, len(cub)), replace=False):
+                e = tuple(cub[idx])
+                fr[e] = fr.get(e, 0.0) + sigma * float(rng.standard_normal())
+        fx.append(fr)
+    pairs = [(i, j) for j in range(n) for i in range(j + 1)]
+    mons: List[Poly] = []
+    for (i, j) in pairs:
+        e = tuple(a + b for a, b in zip(_unit(n, i), _unit(n, j)))
+        mons.append({e: 1.0 if i == j else 2.0})
+    w = np.array([1.0 if i == j else 0.0 for (i, j) in pairs])
+    c1 = Constraint(degree=2, g0=sq_norm(n, -eps), g=[{e: -c for e, c in m.items()} for m in mons],
+                    blocks=[Block(1)])
+    g2 = []
+    for m in mons:
+        gi: Poly = {}
+        for r in range(n):
+            gi = padd(gi, pmul(pdiff(m, r), fx[r]))
+        g2.append(gi)
+    ball = padd({_zero(n): r2}, sq_norm(n, -1.0))
+    c2 = Constraint(degree=4, g0=sq_norm(n, -1.0), g=g2, blocks=[Block(2), Block(1, ball)])
+    return SOSProgram(n=n, w=w, constraints=[c1, c2], name=f"lyapunov_local(n={n},seed={seed})",
+                      meta={"A": A, "pairs": pairs, "eps": eps, "r2": r2})
+
+
 def lyapunov_batch(count: int, seed: int = 0, n_min: int = 2, n_max: int = 6) -> List[SOSProgram]:
     """``count`` cubic Lyapunov searches with n ~ U{n_min..n_max}."""
     rng = np.random.default_rng(seed)

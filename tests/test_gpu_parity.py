@@ -51,6 +51,8 @@ CASES = [
     ("lyapunov_cubic_n3", lambda: W.lyapunov_cubic(3, 1), 40),
     ("lyapunov_linear_n4", lambda: W.lyapunov_linear(4, 3), 60),
     ("eq46_n6", lambda: W.paper_pop(6), 60),
+    ("lyapunov_local_n4_ball", lambda: W.lyapunov_local(4, 2), 60),
+    ("lyapunov_local_n7_grid", lambda: W.lyapunov_local(7, 0), 40),  # N = 36: one program, FP64 grid path
 ]
 
 
@@ -181,3 +183,18 @@ def test_warm_start_keeps_fp64_parity_over_many_iterations(capi):
     s.close()
     assert rel(ug, uo) < 1e-9 and rel(vg, vo) < 1e-9, (rel(ug, uo), rel(vg, vo))
     assert st["max_sweeps"] <= 6, st  # warm start: a few sweeps instead of ~9
+
+
+def test_local_lyapunov_linear_limit_gpu(capi):
+    # the Positivstellensatz program without cubic terms: min trace P is the
+    # Lyapunov solution of A^T P + P A + I = 0 (Kronecker form)
+    prog = W.lyapunov_local(3, 1, sigma=0.0)
+    A = prog.meta["A"]
+    n = 3
+    K = np.kron(np.eye(n), A.T) + np.kron(A.T, np.eye(n))
+    Pstar = np.linalg.solve(K, -np.eye(n).reshape(-1, order="F")).reshape(n, n, order="F")
+    s = capi.Solver(prog, precision=capi.PREC_FP64)
+    r = s.solve(1e-9, 400000)[0]
+    s.close()
+    assert r["status"] == capi.SOLVED
+    assert abs(r["obj_primal"] - np.trace(Pstar)) <= 1e-6 * np.trace(Pstar)
