@@ -330,7 +330,7 @@ def batched_arm(args):
             for blk in con.blocks:
                 from math import comb
 
-                Ns.append(comb(prog.n + blk.basis_degree, blk.basis_degree))
+                Ns.append(blk.size(prog.n))
     flops = sum(9.0 * N ** 3 for N in Ns)
     fp32_peak = 69700.0
     roof = {"kernel": "k_psd_small<double,float> (FP32 Jacobi + compensated refinement, one CTA per block)",
@@ -452,7 +452,8 @@ def local_lyapunov_arm(args):
     rows = []
     for n in ns:
         prog = W.lyapunov_local(n, n)
-        entry = {"n": n, "N": math.comb(n + 2, 2), "paper_cdcs_s": PAPER_TABLE3_CDCS_S.get(n)}
+        entry = {"n": n, "N": max(b.size(n) for c in prog.constraints for b in c.blocks),
+                 "paper_cdcs_s": PAPER_TABLE3_CDCS_S.get(n)}
         for name, prec in (("fp64", capi.PREC_FP64), ("mixed", capi.PREC_MIXED)):
             t0 = time.perf_counter()
             s = capi.Solver(prog, precision=prec, k_check=10)
@@ -627,7 +628,7 @@ def main():
         for blk in con.blocks:
             from math import comb
 
-            blocks.append(comb(prog.n + blk.basis_degree, blk.basis_degree))
+            blocks.append(blk.size(prog.n))
     big = [N for N in blocks if N > (96 if prec == capi.PREC_FP64 else 160)]
     pk, pk_kind = peaks()
     if big and stage_ms["psd_large"] >= stage_ms["psd_small"]:

@@ -9,12 +9,13 @@ polynomial identities
 one per constraint ``j``.  Each Gram block ``X_b`` (PSD) belongs to exactly one
 constraint; ``p_b`` is 1 for a plain SOS block and a fixed polynomial for a
 weighted block (Section VI).  Coefficients are matched for every monomial of
-degree <= ``Constraint.degree``.
+degree ``Constraint.min_degree`` .. ``Constraint.degree``.
 """
 
 from __future__ import annotations
 
 from dataclasses import dataclass, field
+from math import comb
 from typing import Dict, List, Optional, Tuple
 
 import numpy as np
@@ -25,13 +26,23 @@ Poly = Dict[Exp, float]
 
 @dataclass
 class Block:
-    """One Gram block: basis = all monomials of degree <= ``basis_degree``.
+    """One Gram block: basis = all monomials of degree ``min_degree`` ..
+    ``basis_degree`` in the order of eq. (4) (``min_degree`` 0: the full
+    basis v_d).  A smaller basis drops monomials that cannot appear, e.g. the
+    constant when the polynomial vanishes to second order at the origin; the
+    row structure of Prop. 1 holds for any basis.
 
     ``weight`` is None for an ordinary SOS block, else the sparse polynomial
     multiplying the Gram form (eq. (38))."""
 
     basis_degree: int
     weight: Optional[Poly] = None
+    min_degree: int = 0
+
+    def size(self, n: int) -> int:
+        """N, the number of basis monomials in n variables."""
+        low = comb(n + self.min_degree - 1, self.min_degree - 1) if self.min_degree > 0 else 0
+        return comb(n + self.basis_degree, self.basis_degree) - low
 
 
 class Constraint:
@@ -43,8 +54,9 @@ class Constraint:
     is then built on first access."""
 
     def __init__(self, degree: int, g0: Optional[Poly] = None, g: Optional[List[Poly]] = None,
-                 blocks: Optional[List[Block]] = None, term_arrays=None, g0_arrays=None):
-        self.degree = degree  # rows: all monomials of degree <= degree
+                 blocks: Optional[List[Block]] = None, term_arrays=None, g0_arrays=None, min_degree: int = 0):
+        self.degree = degree  # rows: all monomials of degree min_degree .. degree
+        self.min_degree = min_degree
         self._g0 = g0
         self._g = g
         self.blocks = list(blocks or [])

@@ -194,7 +194,7 @@ def lyapunov_linear(n: int, seed: int, eps: float = 1e-3) -> SOSProgram:
     w = np.array([1.0 if i == j else 0.0 for (i, j) in pairs])
     # s1 = V - eps|x|^2 = g0 - sum u_i g_i with g_i = -m_i
     c1 = Constraint(degree=2, g0=sq_norm(n, -eps), g=[{e: -c for e, c in m.items()} for m in mons],
-                    blocks=[Block(1)])
+                    blocks=[Block(1, min_degree=1)], min_degree=2)
     # s2 = -grad V . f - |x|^2 = g0 - sum u_i g_i with g_i = grad m_i . f
     g2 = []
     for m in mons:
@@ -270,7 +270,16 @@ def lyapunov_local(n: int, seed: int, r2: float = 0.1, eps: float = 1e-3, sigma:
 
         min trace(P)  s.t.  V - eps |x|^2 SOS                       (degree 2)
                             -grad V . f - |x|^2 = s0(x) + s1(x) (r2 - |x|^2)
-                            s0 SOS (basis degree 2), s1 SOS (basis degree 1).
+                            s0 SOS, s1 SOS.
+
+    Every polynomial here vanishes to second order at the origin (f(0) = 0,
+    V quadratic), so the bases leave out the constant: s0 on the monomials of
+    degree 1..2 (N = C(n+2,2) - 1), s1 and the Gram form of V - eps|x|^2 on
+    x_1..x_n, and coefficients are matched on the monomials of degree >= 2.
+    With the constant kept, its row would force a zero row and column in the
+    Gram matrices of s0 and s1, and the SDP would have no strictly feasible
+    point.  The low-rank width (the P entries plus the s1 Gram entries) is
+    then n(n+1), the size of the factorized matrix in Table III.
 
     Each component of f gets ``cubic_terms`` (default n) random cubic
     monomials with N(0, sigma^2) coefficients.  Decision variables: P_ij,
@@ -295,7 +304,7 @@ def lyapunov_local(n: int, seed: int, r2: float = 0.1, eps: float = 1e-3, sigma:
         mons.append({e: 1.0 if i == j else 2.0})
     w = np.array([1.0 if i == j else 0.0 for (i, j) in pairs])
     c1 = Constraint(degree=2, g0=sq_norm(n, -eps), g=[{e: -c for e, c in m.items()} for m in mons],
-                    blocks=[Block(1)])
+                    blocks=[Block(1, min_degree=1)], min_degree=2)
     g2 = []
     for m in mons:
         gi: Poly = {}
@@ -303,7 +312,8 @@ def lyapunov_local(n: int, seed: int, r2: float = 0.1, eps: float = 1e-3, sigma:
             gi = padd(gi, pmul(pdiff(m, r), fx[r]))
         g2.append(gi)
     ball = padd({_zero(n): r2}, sq_norm(n, -1.0))
-    c2 = Constraint(degree=4, g0=sq_norm(n, -1.0), g=g2, blocks=[Block(2), Block(1, ball)])
+    c2 = Constraint(degree=4, g0=sq_norm(n, -1.0), g=g2,
+                    blocks=[Block(2, min_degree=1), Block(1, ball, min_degree=1)], min_degree=2)
     return SOSProgram(n=n, w=w, constraints=[c1, c2], name=f"lyapunov_local(n={n},seed={seed})",
                       meta={"A": A, "pairs": pairs, "eps": eps, "r2": r2})
 

@@ -31,3 +31,11 @@ def monomials(n: int, d: int) -> List[Exp]:
         out.extend(_level(deg, n))
     assert len(out) == comb(n + d, d)
     return out
+
+
+def monomials_range(n: int, lo: int, d: int) -> List[Exp]:
+    """The monomials of v_d(x) with degree >= lo, in the same order: v_d
+    without its first C(n+lo-1, lo-1) entries."""
+    out = monomials(n, d)[comb(n + lo - 1, lo - 1) if lo > 0 else 0:]
+    assert all(sum(e) >= lo for e in out)
+    return out

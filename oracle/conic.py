@@ -73,7 +73,7 @@ def build(prog) -> ConicData:
     row_offsets: List[int] = []
     m = 0
     for con in prog.constraints:
-        r = basis.monomials(n, con.degree)
+        r = basis.monomials_range(n, getattr(con, "min_degree", 0), con.degree)
         rows.append(r)
         row_index.append({e: m + k for k, e in enumerate(r)})
         row_offsets.append(m)
@@ -99,7 +99,7 @@ def build(prog) -> ConicData:
     diag: List[int] = []
     for j, con in enumerate(prog.constraints):
         for blk in con.blocks:
-            bas = basis.monomials(n, blk.basis_degree)
+            bas = basis.monomials_range(n, getattr(blk, "min_degree", 0), blk.basis_degree)
             N = len(bas)
             weighted = blk.weight is not None
             blocks.append(BlockInfo(col, N, weighted, j, bas))

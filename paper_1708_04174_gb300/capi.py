@@ -135,16 +135,18 @@ class _Marshalled:
         self.progs = (sos_program * len(progs))()
         cache = {}
 
-        def mono(n, d):
-            if (n, d) not in cache:
-                cache[(n, d)] = monomials(n, d)
-            return cache[(n, d)]
+        def mono(n, d, lo=0):
+            # v_d without its monomials of degree < lo (same order)
+            if (n, d, lo) not in cache:
+                full = monomials(n, d)
+                cache[(n, d, lo)] = np.ascontiguousarray(full[full.sum(axis=1) >= lo])
+            return cache[(n, d, lo)]
 
         for pi, pg in enumerate(progs):
             n = pg.n
             cons = (sos_constraint * len(pg.constraints))()
             for ci, con in enumerate(pg.constraints):
-                rows = mono(n, con.degree)
+                rows = mono(n, con.degree, getattr(con, "min_degree", 0))
                 tp, te, tc = [], [], []
                 arrays = getattr(con, "term_arrays", None)
                 g0a = getattr(con, "g0_arrays", None)
@@ -172,7 +174,7 @@ class _Marshalled:
                 tc = np.ascontiguousarray(tc)
                 blks = (sos_block * len(con.blocks))()
                 for bi, blk in enumerate(con.blocks):
-                    bas = mono(n, blk.basis_degree)
+                    bas = mono(n, blk.basis_degree, getattr(blk, "min_degree", 0))
                     blks[bi].N = bas.shape[0]
                     blks[bi].basis_exps = _ptr(bas, C.c_int32)
                     if blk.weight is not None:

@@ -49,6 +49,8 @@ PROGS = [
     lambda: W.lyapunov_linear(3, 0),
     lambda: W.paper_pop(5),
     lambda: W.univariate_pop(6, 2),
+    lambda: W.lyapunov_local(4, 2),  # reduced bases and rows
+    lambda: W.lyapunov_local(10, 10),
 ]
 
 
@@ -78,6 +80,14 @@ def test_index_map_bit_exact(capi, make):
     assert np.array_equal(hp["p_diag"], hs.P)  # 1 + n_alpha, exact small integers
     assert np.array_equal(hp["b"], cd.b)
     assert abs(hp["zeta_h"] - hs.zeta @ hs.h) <= 1e-12 * max(1.0, abs(hs.zeta @ hs.h))
+
+
+def test_local_lyapunov_matches_table3_shape(capi):
+    # n = 10: largest cone N = 65 and factorized width t = n (n + 1) = 110,
+    # as in Table III (m differs by the rows this formulation leaves out)
+    hp = capi.host_plan(W.lyapunov_local(10, 10))
+    nx, m, t, teff, nb, nent = hp["dims"]
+    assert teff == 110 and t == 55 and m == 1045
 
 
 def test_setup_rejects_bad_input(capi):

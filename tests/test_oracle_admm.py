@@ -187,11 +187,33 @@ def test_local_lyapunov_cubic_needs_more():
     # with cubic terms the local certificate exists (linearly stable origin,
     # small ball) and cannot beat the linear optimum: the extra terms only
     # tighten the second identity on the ball
-    # (the cubic instance converges slowly, so both run to 1e-4: the
-    # objectives are then good to ~1e-3 relative)
     prog = W.lyapunov_local(3, 1, sigma=1.0)
     lin = W.lyapunov_local(3, 1, sigma=0.0)
-    r = admm.solve(conic.build(prog), 1e-4, 200000, k_check=10)
-    rl = admm.solve(conic.build(lin), 1e-4, 200000, k_check=10)
+    r = admm.solve(conic.build(prog), 1e-8, 400000, k_check=10)
+    rl = admm.solve(conic.build(lin), 1e-8, 400000, k_check=10)
     assert r.status == admm.SOLVED and rl.status == admm.SOLVED
-    assert r.res["pobj"] >= rl.res["pobj"] * (1 - 1e-3)
+    assert r.res["pobj"] >= rl.res["pobj"] * (1 - 1e-6)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_binary_quartic_form_reduced_basis(seed):
+    # A nonnegative binary form is a sum of squares of forms (Hilbert), so
+    # max gamma s.t. p - gamma (x^2 + y^2)^2 SOS, with the Gram basis
+    # [x^2, xy, y^2] (degree 2 only) and coefficients matched on the quartic
+    # monomials only, is the minimum of p on the unit circle.  This pins the
+    # reduced bases (no constant or linear monomials) against brute force.
+    rng = np.random.default_rng(seed)
+    p = {(4 - k, k): float(v) for k, v in enumerate(rng.standard_normal(5))}
+    p[(4, 0)] += 3.0
+    p[(0, 4)] += 3.0
+    circ = {(4, 0): 1.0, (2, 2): 2.0, (0, 4): 1.0}
+    prog = SOSProgram(n=2, w=np.array([-1.0]),
+                      constraints=[Constraint(degree=4, g0=p, g=[circ], blocks=[Block(2, min_degree=2)],
+                                              min_degree=4)])
+    cd = conic.build(prog)
+    assert cd.A.shape == (5, 1 + 9) and cd.blocks[0].N == 3
+    r = admm.solve(cd, 1e-10, 200000, k_check=10)
+    assert r.status == admm.SOLVED
+    th = np.linspace(0.0, np.pi, 2000001)  # p is even: half the circle suffices
+    gmin = np.min(sum(c * np.cos(th) ** e[0] * np.sin(th) ** e[1] for e, c in p.items()))
+    assert abs(-r.res["pobj"] - gmin) <= 1e-6 * max(1.0, abs(gmin))

@@ -28,6 +28,18 @@ def test_basis_eq4_prefix_and_size():
         assert set(v) == brute
 
 
+@pytest.mark.parametrize("n,lo,d", [(2, 1, 2), (3, 2, 4), (4, 1, 1), (5, 0, 3), (3, 3, 3)])
+def test_basis_range(n, lo, d):
+    # the reduced basis is v_d restricted to degrees lo..d, in v_d's order
+    from instances.program import Block
+
+    v = basis.monomials_range(n, lo, d)
+    brute = {e for e in itertools.product(range(d + 1), repeat=n) if lo <= sum(e) <= d}
+    assert set(v) == brute and len(v) == len(brute) == Block(d, min_degree=lo).size(n)
+    full = basis.monomials(n, d)
+    assert v == [e for e in full if sum(e) >= lo]
+
+
 def _pair_counts(bas):
     cnt = {}
     for b1 in bas:
