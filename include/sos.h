@@ -93,6 +93,19 @@ typedef struct {
   const sos_block* blocks;     /* [n_blocks] */
 } sos_constraint;
 
+/* Matrix-valued constraints (Section V, eq. (47)-(48)):
+ *   P_0(x) - sum_h u_h P_h(x) = (I_r (x) v(x))^T Y (I_r (x) v(x)),  Y PSD,
+ * use the same struct in the variables (x_1..x_n, y_1..y_R), R >= r extra
+ * variables per program.  The basis of the single block lists y_i x^a for
+ * i = 1..r (block-major, the order of I_r (x) v); the rows list
+ * y_i y_j x^alpha for the pairs i <= j, one per triple (alpha, i, j) of
+ * Prop. 2; a term c x^e of entry (i, j), i <= j, of P_h becomes the term
+ * c' x^e y_i y_j with c' = c for i == j and 2 c otherwise (the coefficient
+ * of y_i y_j x^e in y^T P_h(x) y).  Entry (p, q) of Y then lands on row
+ * (alpha_p + alpha_q, i_p, i_q) by the same exponent lookup as a scalar
+ * block, and the rows of its Gram part stay orthogonal (Prop. 2).  Scalar
+ * constraints of the same program carry zero exponents in y. */
+
 /* min w^T u subject to the constraints (eq. (7), eq. (15)). */
 typedef struct {
   int32_t n_vars;

@@ -84,6 +84,34 @@ class Constraint:
         return self._g
 
 
+class MatrixConstraint:
+    """One matrix-valued SOS identity (Section V, eq. (47)-(48)):
+
+        P_0(x) - sum_h u_h P_h(x) = (I_r (x) v(x))^T Y (I_r (x) v(x)),   Y PSD,
+
+    Y of size r N, v the basis of ``block`` (plain, unweighted).  ``P0`` and
+    each of the t entries of ``P`` are r x r nested lists of sparse
+    polynomials; the matrices are symmetric and only entries [i][j] with
+    i <= j are read.  Coefficients are matched for every triple
+    (alpha, i, j), i <= j, alpha of degree ``min_degree`` .. ``degree``; the
+    rows are ordered by the pairs (i, j) row-major, then alpha in the order
+    of eq. (4).  Y's rows and columns are ordered block-major: index
+    i N + a is basis monomial a of block row i."""
+
+    def __init__(self, r: int, degree: int, P0, P, block: Block, min_degree: int = 0):
+        self.r = r
+        self.degree = degree
+        self.min_degree = min_degree
+        self.P0 = P0
+        self.P = list(P)
+        self.block = block
+        assert block.weight is None
+
+    @property
+    def pairs(self) -> List[Tuple[int, int]]:
+        return [(i, j) for i in range(self.r) for j in range(i, self.r)]
+
+
 @dataclass
 class SOSProgram:
     n: int

@@ -26,7 +26,7 @@ from typing import Dict, List, Sequence, Tuple
 
 import numpy as np
 
-from .program import Block, Constraint, SOSProgram
+from .program import Block, Constraint, MatrixConstraint, SOSProgram
 
 Exp = Tuple[int, ...]
 Poly = Dict[Exp, float]
@@ -133,6 +133,33 @@ def ball_pop(n: int, seed: int = 0) -> SOSProgram:
     """Quartic POP on the unit ball, order-2 Lasserre relaxation as a weighted
     SOS constraint: p - g = s0 + s1 (1 - |x|^2), s0 deg 4, s1 deg 2."""
     return _pop_program(n, quartic_poly(n, seed), f"ball_pop(n={n},seed={seed})", ball=True)
+
+
+def matrix_poly(n: int, r: int, seed: int) -> List[List[Poly]]:
+    """Symmetric r x r quartic matrix polynomial
+    P(x) = (sum x_i^2)^2 I_r + sum_{|a|<=3} C_a x^a, the entries of C_a ~ N(0,1)
+    drawn for i <= j (pairs row-major), then a in graded order."""
+    rng = np.random.default_rng(seed)
+    s = sq_norm(n)
+    lead = pmul(s, s)
+    P: List[List[Poly]] = [[{} for _ in range(r)] for _ in range(r)]
+    for i in range(r):
+        for j in range(i, r):
+            low = _random_low_part(n, rng)
+            P[i][j] = padd(lead, low) if i == j else low
+            P[j][i] = P[i][j]
+    return P
+
+
+def matrix_pop(n: int, r: int, seed: int = 0) -> SOSProgram:
+    """Lower bound on min_x lambda_min(P(x)) for the matrix polynomial of
+    ``matrix_poly``: max g s.t. P(x) - g I_r is an SOS matrix (Section V,
+    eq. (47)-(48)) with the basis I_r (x) v_2(x); Y is r C(n+2,2) square."""
+    P = matrix_poly(n, r, seed)
+    eye = [[({_zero(n): 1.0} if i == j else {}) for j in range(r)] for i in range(r)]
+    con = MatrixConstraint(r=r, degree=4, P0=P, P=[eye], block=Block(2))
+    return SOSProgram(n=n, w=np.array([-1.0]), constraints=[con], name=f"matrix_pop(n={n},r={r},seed={seed})",
+                      meta={"P": P})
 
 
 def paper_pop_poly(n: int) -> Poly:

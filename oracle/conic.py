@@ -11,6 +11,11 @@ Follows the paper's construction literally, with full ``vec`` Gram columns:
 * Several SOS constraints each own their rows and Gram blocks (eq. (7), remark
   after eq. (13)); a weighted block p(x) v v^T contributes the coefficients of
   p(x) x^(beta+gamma) (Section VI, eq. (38)-(40)).
+* A matrix-valued constraint (Section V) has one row per triple
+  (alpha, i, j): <E_i^T Y E_j, B_alpha> = (C_alpha)_ij (eq. (49)-(50)), Y of
+  size r N.  Y is symmetric, so the triples (alpha, i, j) and (alpha, j, i)
+  state one equation; the row is kept once, for i <= j, and for i < j it
+  collects both blocks Y_ij and Y_ji, with right side 2 (C_alpha)_ij.
 
 Column classes (Prop. 1 and Prop. 3): columns of unweighted Gram blocks form
 the orthogonal part (each has exactly one nonzero, so its rows' products are
@@ -25,6 +30,8 @@ from typing import Dict, List, Tuple
 
 import numpy as np
 import scipy.sparse as sp
+
+from instances.program import MatrixConstraint
 
 from . import basis
 
@@ -73,7 +80,11 @@ def build(prog) -> ConicData:
     row_offsets: List[int] = []
     m = 0
     for con in prog.constraints:
-        r = basis.monomials_range(n, getattr(con, "min_degree", 0), con.degree)
+        if isinstance(con, MatrixConstraint):
+            al = basis.monomials_range(n, con.min_degree, con.degree)
+            r = [(a, i, j) for i in range(con.r) for j in range(i, con.r) for a in al]
+        else:
+            r = basis.monomials_range(n, getattr(con, "min_degree", 0), con.degree)
         rows.append(r)
         row_index.append({e: m + k for k, e in enumerate(r)})
         row_offsets.append(m)
@@ -84,6 +95,18 @@ def build(prog) -> ConicData:
     V: List[float] = []
     b = np.zeros(m)
     for j, con in enumerate(prog.constraints):
+        if isinstance(con, MatrixConstraint):
+            assert len(con.P) == t
+            for (i1, i2) in con.pairs:
+                sym = 1.0 if i1 == i2 else 2.0  # (C_alpha)_ij + (C_alpha)_ji
+                for e, coef in con.P0[i1][i2].items():
+                    b[row_index[j][(e, i1, i2)]] += sym * coef
+                for h, Ph in enumerate(con.P):
+                    for e, coef in Ph[i1][i2].items():
+                        I.append(row_index[j][(e, i1, i2)])
+                        J.append(h)
+                        V.append(sym * coef)
+            continue
         for e, coef in con.g0.items():
             b[row_index[j][e]] += coef
         assert len(con.g) == t
@@ -98,6 +121,22 @@ def build(prog) -> ConicData:
     lowrank = list(range(t))
     diag: List[int] = []
     for j, con in enumerate(prog.constraints):
+        if isinstance(con, MatrixConstraint):
+            bas = basis.monomials_range(n, con.block.min_degree, con.block.basis_degree)
+            N = len(bas)
+            L = con.r * N
+            blocks.append(BlockInfo(col, L, False, j, [(i, e) for i in range(con.r) for e in bas]))
+            for kk in range(L):
+                bk, ek = divmod(kk, N)  # block column, basis monomial
+                for ii in range(L):
+                    bi, ei = divmod(ii, N)
+                    cidx = col + ii + kk * L
+                    I.append(row_index[j][(_add(bas[ei], bas[ek]), min(bi, bk), max(bi, bk))])
+                    J.append(cidx)
+                    V.append(1.0)
+                    diag.append(cidx)
+            col += L * L
+            continue
         for blk in con.blocks:
             bas = basis.monomials_range(n, getattr(blk, "min_degree", 0), blk.basis_degree)
             N = len(bas)

@@ -144,9 +144,28 @@ class _Marshalled:
 
         for pi, pg in enumerate(progs):
             n = pg.n
+            # a matrix-valued constraint of size r is passed as a scalar one in
+            # the variables (x, y_1..y_R): the basis entry (i, a) of I_r (x) v
+            # is y_i x^a and the row triple (alpha, i, j) is y_i y_j x^alpha,
+            # so the library's exponent lookup finds the triple of every Gram
+            # entry; scalar constraints get zero y-exponents
+            R = max([c.r for c in pg.constraints if hasattr(c, "r")] + [0])
+            nv = n + R
+
+            def pad(e, extra=None):
+                e = np.asarray(e, dtype=np.int32).reshape(-1, n)
+                out = np.zeros((e.shape[0], nv), dtype=np.int32)
+                out[:, :n] = e
+                if extra is not None:
+                    out[:, n:] = extra
+                return np.ascontiguousarray(out)
+
             cons = (sos_constraint * len(pg.constraints))()
             for ci, con in enumerate(pg.constraints):
-                rows = mono(n, con.degree, getattr(con, "min_degree", 0))
+                if hasattr(con, "r"):
+                    self._matrix(cons[ci], con, n, R, pad, mono)
+                    continue
+                rows = pad(mono(n, con.degree, getattr(con, "min_degree", 0)))
                 tp, te, tc = [], [], []
                 arrays = getattr(con, "term_arrays", None)
                 g0a = getattr(con, "g0_arrays", None)
@@ -170,15 +189,15 @@ class _Marshalled:
                     te = np.concatenate([te, np.asarray(exps, dtype=np.int32).reshape(-1, n)])
                     tc = np.concatenate([tc, np.asarray(coef, dtype=np.float64)])
                 tp = np.ascontiguousarray(tp)
-                te = np.ascontiguousarray(te)
+                te = pad(te) if R else np.ascontiguousarray(te)
                 tc = np.ascontiguousarray(tc)
                 blks = (sos_block * len(con.blocks))()
                 for bi, blk in enumerate(con.blocks):
-                    bas = mono(n, blk.basis_degree, getattr(blk, "min_degree", 0))
+                    bas = pad(mono(n, blk.basis_degree, getattr(blk, "min_degree", 0)))
                     blks[bi].N = bas.shape[0]
                     blks[bi].basis_exps = _ptr(bas, C.c_int32)
                     if blk.weight is not None:
-                        we = np.ascontiguousarray(np.array(list(blk.weight.keys()), dtype=np.int32).reshape(-1, n))
+                        we = pad(np.array(list(blk.weight.keys()), dtype=np.int32))
                         wc = np.ascontiguousarray(list(blk.weight.values()), dtype=np.float64)
                         blks[bi].n_weight_terms = len(wc)
                         blks[bi].weight_exps = _ptr(we, C.c_int32)
@@ -197,12 +216,55 @@ class _Marshalled:
                 cons[ci].blocks = blks
                 self.keep += [rows, tp, te, tc, blks]
             w = np.ascontiguousarray(pg.w, dtype=np.float64)
-            self.progs[pi].n_vars = n
+            self.progs[pi].n_vars = nv
             self.progs[pi].t = len(w)
             self.progs[pi].w = _ptr(w, C.c_double)
             self.progs[pi].n_constraints = len(pg.constraints)
             self.progs[pi].constraints = cons
             self.keep += [w, cons]
+
+
+    def _matrix(self, out, con, n, R, pad, mono):
+        """sos_constraint of a matrix-valued constraint (Section V) in the
+        variables (x, y): rows y_i y_j x^alpha for the pairs i <= j row-major,
+        then alpha; terms of P_h[i][j] (h = 0 for P_0) times 2 off the
+        diagonal, the coefficient of y_i y_j x^alpha in y^T P_h(x) y; basis
+        y_i x^a block-major."""
+        r = con.r
+        al = mono(n, con.degree, con.min_degree)
+        yy = []
+        for (i, j) in con.pairs:
+            e = np.zeros(R, dtype=np.int32)
+            e[i] += 1
+            e[j] += 1
+            yy.append(e)
+        rows = np.concatenate([pad(al, e) for e in yy])
+        tp, te, tc = [], [], []
+        for h, Ph in enumerate([con.P0] + list(con.P)):
+            for (i, j), e_y in zip(con.pairs, yy):
+                sym = 1.0 if i == j else 2.0
+                for e, cval in Ph[i][j].items():
+                    tp.append(h)
+                    te.append(list(e) + list(e_y))
+                    tc.append(sym * cval)
+        tp = np.ascontiguousarray(tp, dtype=np.int32)
+        te = np.ascontiguousarray(np.array(te, dtype=np.int32).reshape(-1, n + R))
+        tc = np.ascontiguousarray(tc, dtype=np.float64)
+        bas1 = mono(n, con.block.basis_degree, con.block.min_degree)
+        bas = np.concatenate([pad(bas1, np.eye(R, dtype=np.int32)[i]) for i in range(r)])
+        blks = (sos_block * 1)()
+        blks[0].N = bas.shape[0]
+        blks[0].basis_exps = _ptr(bas, C.c_int32)
+        blks[0].n_weight_terms = 0
+        out.n_rows = rows.shape[0]
+        out.row_exps = _ptr(rows, C.c_int32)
+        out.n_terms = len(tp)
+        out.term_poly = _ptr(tp, C.c_int32)
+        out.term_exps = _ptr(te, C.c_int32)
+        out.term_coef = _ptr(tc, C.c_double)
+        out.n_blocks = 1
+        out.blocks = blks
+        self.keep += [rows, tp, te, tc, bas, blks]
 
 
 def psd_project(in_ptr: int, out_ptr: int, N: int, stream: int = 0):

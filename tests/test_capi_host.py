@@ -51,7 +51,21 @@ PROGS = [
     lambda: W.univariate_pop(6, 2),
     lambda: W.lyapunov_local(4, 2),  # reduced bases and rows
     lambda: W.lyapunov_local(10, 10),
+    lambda: W.matrix_pop(2, 2, 0),  # matrix-valued (Section V)
+    lambda: W.matrix_pop(3, 3, 1),
+    lambda: W.matrix_pop(1, 4, 2),
+    lambda: _scalar_and_matrix(),
 ]
+
+
+def _scalar_and_matrix():
+    # one u shared by a scalar and a matrix-valued constraint (the scalar one's
+    # exponents are padded with the matrix encoding's extra variables)
+    from instances.program import Block, Constraint, SOSProgram
+
+    mp = W.matrix_pop(2, 2, 3)
+    sc = Constraint(degree=4, g0=W.quartic_poly(2, 3), g=[{(0, 0): 1.0}], blocks=[Block(2), Block(1, {(0, 0): 1.0, (2, 0): -1.0})])
+    return SOSProgram(n=2, w=np.array([-1.0]), constraints=[sc, mp.constraints[0]])
 
 
 @pytest.mark.parametrize("make", PROGS)

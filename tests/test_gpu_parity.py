@@ -53,7 +53,20 @@ CASES = [
     ("eq46_n6", lambda: W.paper_pop(6), 60),
     ("lyapunov_local_n4_ball", lambda: W.lyapunov_local(4, 2), 60),
     ("lyapunov_local_n7_grid", lambda: W.lyapunov_local(7, 0), 40),  # N = 36: one program, FP64 grid path
+    ("matrix_n2_r2", lambda: W.matrix_pop(2, 2, 0), 60),  # matrix-valued (Section V): Y 12 x 12
+    ("matrix_n3_r3", lambda: W.matrix_pop(3, 3, 1), 60),
+    ("matrix_n6_r3_grid", lambda: W.matrix_pop(6, 3, 0), 40),  # Y 84 x 84: FP64 grid path
+    ("scalar_and_matrix", lambda: _scalar_and_matrix(), 60),
 ]
+
+
+def _scalar_and_matrix():
+    from instances.program import Block, Constraint, SOSProgram
+
+    mp = W.matrix_pop(2, 2, 3)
+    sc = Constraint(degree=4, g0=W.quartic_poly(2, 3), g=[{(0, 0): 1.0}],
+                    blocks=[Block(2), Block(1, {(0, 0): 1.0, (2, 0): -1.0})])
+    return SOSProgram(n=2, w=np.array([-1.0]), constraints=[sc, mp.constraints[0]])
 
 
 @pytest.mark.parametrize("name,make,iters", CASES, ids=[c[0] for c in CASES])
@@ -198,3 +211,24 @@ def test_local_lyapunov_linear_limit_gpu(capi):
     s.close()
     assert r["status"] == capi.SOLVED
     assert abs(r["obj_primal"] - np.trace(Pstar)) <= 1e-6 * np.trace(Pstar)
+
+
+@pytest.mark.parametrize("precision,make,tol", [
+    ("fp64", lambda: W.matrix_pop(1, 3, 2), 1e-6),
+    ("mixed", lambda: W.matrix_pop(6, 3, 0), 1e-3),   # Y 84: FP32 Jacobi + refinement
+    ("mixed", lambda: W.matrix_pop(8, 3, 0), 1e-3),   # Y 135: tensor-core Newton-Schulz
+])
+def test_matrix_valued_objective_vs_oracle(capi, precision, make, tol):
+    """Matrix-valued SOS (Section V): the plain form solved to 1e-8 gives the
+    oracle's objective within 1e-6 (same iteration count); the mixed form
+    solved to 1e-4 within 1e-3 (the termination rule's own slack)."""
+    prog = make()
+    ro = admm.solve(conic.build(prog), 1e-7 if precision == "mixed" else 1e-8, 50000, k_check=10)
+    prec = capi.PREC_FP64 if precision == "fp64" else capi.PREC_MIXED
+    s = capi.Solver(prog, precision=prec, k_check=10)
+    r = s.solve(1e-8 if precision == "fp64" else 1e-4, 50000)[0]
+    s.close()
+    assert r["status"] == capi.SOLVED and ro.status == admm.SOLVED
+    assert abs(r["obj_primal"] - ro.res["pobj"]) <= tol * abs(ro.res["pobj"])
+    if precision == "fp64":
+        assert r["iters"] == ro.iters
