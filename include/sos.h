@@ -140,7 +140,18 @@ typedef struct {
                              iteration's eigenvectors and restart from the
                              identity after this many warm iterations;
                              0 = 1024, 1 = every iteration cold */
-  int32_t reserved0;      /* must be zero */
+  int32_t weighted_form;  /* weighted blocks (eq. (37)): 0 auto, per program by
+                             eq. (42) -- directly while the Woodbury core
+                             t + sum N_i (N_i + 1) / 2 over weighted blocks is
+                             smaller than m, else with extra polynomials;
+                             1 always directly; 2 always with extra
+                             polynomials: p s becomes p r with r free (its
+                             coefficients r_beta, one per monomial of v v^T
+                             in the order of eq. (4), follow the t variables)
+                             and a new identity r = v^T X v (after the
+                             program's constraints) holds X as a plain block.
+                             sos_dims, the iterate and the solution then
+                             describe that program. */
   double infeas_tol;      /* tolerance of the infeasibility certificates of
                              sos_solve, independent of its tol; 0 = 1e-7 */
   int32_t reserved[2];    /* must be zero */
@@ -234,9 +245,9 @@ int sos_monomials(int32_t n_vars, int32_t degree, int32_t* out, int64_t capacity
  * for a plain Gram entry (eq. (8)) or -1 for a low-rank entry (free variable
  * or weighted block), p_diag[m] the diagonal of P = I + A_D A_D^T (Prop. 1),
  * b[m] the coefficients of g_0, and *zeta_h the scalar zeta^T M^{-1} zeta of
- * eq. (25).  Errors as sos_setup. */
-int sos_host_plan(const sos_program* prog, int64_t dims[6], int32_t* ent_row, double* p_diag, double* b,
-                  double* zeta_h);
+ * eq. (25); weighted_form as in sos_options.  Errors as sos_setup. */
+int sos_host_plan(const sos_program* prog, int32_t weighted_form, int64_t dims[6], int32_t* ent_row, double* p_diag,
+                  double* b, double* zeta_h);
 
 /* Projection onto the PSD cone of ONE symmetric N x N matrix (the Gram-block
  * part of the cone projection of eq. (20b)): out = svec(P_S+(smat(in))),

@@ -135,6 +135,19 @@ def ball_pop(n: int, seed: int = 0) -> SOSProgram:
     return _pop_program(n, quartic_poly(n, seed), f"ball_pop(n={n},seed={seed})", ball=True)
 
 
+def interval_pop(deg: int, seed: int = 0) -> SOSProgram:
+    """min of a random univariate polynomial of even degree ``deg``
+    (coefficients N(0,1), drawn from x^0 up) on [-1, 1]:
+    max g s.t. p - g = s0 + (1 - x^2) s1, s0 with basis v_{deg/2}, s1 with
+    basis v_{deg/2 - 1} (a weighted block, eq. (37))."""
+    rng = np.random.default_rng(seed)
+    p = {(k,): float(c) for k, c in enumerate(rng.standard_normal(deg + 1))}
+    con = Constraint(degree=deg, g0=p, g=[{(0,): 1.0}],
+                     blocks=[Block(deg // 2), Block(deg // 2 - 1, {(0,): 1.0, (2,): -1.0})])
+    return SOSProgram(n=1, w=np.array([-1.0]), constraints=[con], name=f"interval_pop(deg={deg},seed={seed})",
+                      meta={"p": p})
+
+
 def matrix_poly(n: int, r: int, seed: int) -> List[List[Poly]]:
     """Symmetric r x r quartic matrix polynomial
     P(x) = (sum x_i^2)^2 I_r + sum_{|a|<=3} C_a x^a, the entries of C_a ~ N(0,1)

@@ -46,7 +46,7 @@ class sos_program(C.Structure):
 class sos_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("k_check", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("solve_mode", C.c_int32), ("large_method", C.c_int32), ("warm_restart", C.c_int32),
-                ("reserved0", C.c_int32), ("infeas_tol", C.c_double), ("reserved", C.c_int32 * 2)]
+                ("weighted_form", C.c_int32), ("infeas_tol", C.c_double), ("reserved", C.c_int32 * 2)]
 
 
 class sos_result(C.Structure):
@@ -66,7 +66,8 @@ EXPORTS = {
     "sos_get_iterate": (C.c_int, [C.c_void_p, _f64p, _f64p]),
     "sos_set_iterate": (C.c_int, [C.c_void_p, _f64p, _f64p]),
     "sos_monomials": (C.c_int, [C.c_int32, C.c_int32, _i32p, C.c_int64, C.POINTER(C.c_int64)]),
-    "sos_host_plan": (C.c_int, [C.POINTER(sos_program), C.POINTER(C.c_int64), _i32p, _f64p, _f64p, _f64p]),
+    "sos_host_plan": (C.c_int, [C.POINTER(sos_program), C.c_int32, C.POINTER(C.c_int64), _i32p, _f64p, _f64p,
+                                _f64p]),
     "sos_stream": (C.c_void_p, [C.c_void_p]),
     "sos_launches_per_iteration": (C.c_int, [C.c_void_p]),
     "sos_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
@@ -291,18 +292,18 @@ def psd_project_noalloc(in_ptr: int, out_ptr: int, N: int, stream: int = 0):
                                          C.c_void_p(stream) if stream else None))
 
 
-def host_plan(prog):
+def host_plan(prog, weighted_form: int = 0):
     """Index map of one program as built by libsos's host setup (no GPU)."""
     m = _Marshalled([prog])
     dims = (C.c_int64 * 6)()
-    _check(lib().sos_host_plan(m.progs, dims, None, None, None, None))
+    _check(lib().sos_host_plan(m.progs, weighted_form, dims, None, None, None, None))
     nx, mm = dims[0], dims[1]
     ent = np.zeros(nx, dtype=np.int32)
     pd = np.zeros(mm)
     b = np.zeros(mm)
     zh = C.c_double(0)
-    _check(lib().sos_host_plan(m.progs, dims, _ptr(ent, C.c_int32), _ptr(pd, C.c_double), _ptr(b, C.c_double),
-                               C.byref(zh)))
+    _check(lib().sos_host_plan(m.progs, weighted_form, dims, _ptr(ent, C.c_int32), _ptr(pd, C.c_double),
+                               _ptr(b, C.c_double), C.byref(zh)))
     return {"dims": tuple(dims), "ent_row": ent, "p_diag": pd, "b": b, "zeta_h": zh.value}
 
 
@@ -310,7 +311,7 @@ class Solver:
     """One libsos handle over a batch of SOS programs (instances)."""
 
     def __init__(self, progs, precision: int = PREC_FP64, k_check: int = 10, stream=None, solve_mode: int = 0,
-                 large_method: int = 0, warm_restart: int = 0, infeas_tol: float = 0.0):
+                 large_method: int = 0, warm_restart: int = 0, infeas_tol: float = 0.0, weighted_form: int = 0):
         if not isinstance(progs, (list, tuple)):
             progs = [progs]
         self.n_inst = len(progs)
@@ -323,6 +324,7 @@ class Solver:
         opts.large_method = large_method
         opts.warm_restart = warm_restart
         opts.infeas_tol = infeas_tol
+        opts.weighted_form = weighted_form
         h = C.c_void_p()
         _check(lib().sos_setup(m.progs, len(progs), C.byref(opts), C.byref(h)))
         self.h = h

@@ -75,6 +75,7 @@ struct sos_handle {
   // persistent batched path
   bool persistent = false;
   int32_t solve_mode = 0;
+  int32_t weighted_form = 0;  // 0 eq. (42), 1 direct, 2 extra polynomials
   int32_t p_grid = 0, p_dynamic = 0, p_tried = 0, p_max_small = 0, p_max_teff = 0;
   float p_best_ms = 0.f;
   uint32_t *p_bar = nullptr, *p_queue = nullptr;
@@ -559,7 +560,7 @@ void compute_stage_bytes(sos_handle* h, const HostPlan& P, const std::vector<int
 int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   HostPlan P;
   std::string err;
-  int rc = build_plan(progs, n_progs, P, err);
+  int rc = build_plan(progs, n_progs, P, err, h->weighted_form);
   if (rc != SOS_OK) return set_err(h, rc, err);
   renumber_rows(P, h->row_perm);
   h->n_inst = P.n_inst;
@@ -936,10 +937,15 @@ int sos_setup(const sos_program* progs, int32_t n_progs, const sos_options* opts
       g_setup_error = "warm_restart must be >= 0";
       return SOS_ERR_INVALID_ARG;
     }
-    if (opts->infeas_tol < 0 || opts->reserved0 != 0) {
-      g_setup_error = "infeas_tol must be >= 0 and reserved fields zero";
+    if (opts->infeas_tol < 0) {
+      g_setup_error = "infeas_tol must be >= 0";
       return SOS_ERR_INVALID_ARG;
     }
+    if (opts->weighted_form < 0 || opts->weighted_form > 2) {
+      g_setup_error = "unknown weighted_form";
+      return SOS_ERR_INVALID_ARG;
+    }
+    h->weighted_form = opts->weighted_form;
     if (opts->infeas_tol > 0) h->infeas_tol = opts->infeas_tol;
     if (opts->warm_restart > 0)
       h->warm64.limit = h->warm32.limit = opts->warm_restart;
@@ -1183,12 +1189,12 @@ int sos_monomials(int32_t n_vars, int32_t degree, int32_t* out, int64_t capacity
   return SOS_OK;
 }
 
-int sos_host_plan(const sos_program* prog, int64_t dims[6], int32_t* ent_row, double* p_diag, double* b,
-                  double* zeta_h) {
-  if (!prog || !dims) return SOS_ERR_INVALID_ARG;
+int sos_host_plan(const sos_program* prog, int32_t weighted_form, int64_t dims[6], int32_t* ent_row, double* p_diag,
+                  double* b, double* zeta_h) {
+  if (!prog || !dims || weighted_form < 0 || weighted_form > 2) return SOS_ERR_INVALID_ARG;
   HostPlan P;
   std::string err;
-  const int rc = build_plan(prog, 1, P, err);
+  const int rc = build_plan(prog, 1, P, err, weighted_form);
   if (rc != SOS_OK) {
     g_setup_error = err;
     return rc;

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <thread>
 
@@ -86,6 +87,7 @@ struct Local {
   std::vector<std::vector<uint32_t>> row_plain; // per row: entries | offdiag bit
   std::vector<LocalBlock> blocks;
   double zeta_h = 0, norm_b = 0, norm_c = 0;
+  int extra_form = 0;  // 1: weighted blocks rewritten with extra polynomials
   int code = SOS_OK;
   std::string err;
 };
@@ -127,6 +129,150 @@ std::vector<double> tri_inverse(const std::vector<double>& Lm, int n) {
     }
   }
   return X;
+}
+
+// ---------------------------------------------------------------------------
+// Extra-polynomial form of weighted SOS constraints (end of Section II): a
+// weighted term p(x) s(x), s = v^T X v, becomes p(x) r(x) with r a free
+// polynomial r = sum_beta r_beta x^beta over the monomials beta of v v^T,
+// plus a new identity r(x) = v^T X v in which X is a plain Gram block.  The
+// coefficients r_beta follow the original t variables (weighted blocks in
+// program order, beta in the order of eq. (4)); each new identity follows the
+// original constraints (same order) and owns its block, which leaves the
+// weighted term's constraint.  Every Gram block of the result is plain, and
+// the low-rank part holds only free variables.
+// ---------------------------------------------------------------------------
+struct ExtraForm {
+  std::vector<double> w;
+  std::vector<sos_constraint> cons;
+  std::deque<std::vector<sos_block>> blocks;
+  std::deque<std::vector<int32_t>> i32;
+  std::deque<std::vector<double>> f64;
+  sos_program prog{};
+};
+
+bool has_weighted(const sos_program& pg) {
+  for (int j = 0; j < pg.n_constraints; ++j)
+    for (int k = 0; k < pg.constraints[j].n_blocks; ++k)
+      if (pg.constraints[j].blocks[k].n_weight_terms > 0) return true;
+  return false;
+}
+
+// eq. (42) with packed Gram blocks: the direct form pays off while the
+// Woodbury core, t + sum N_i (N_i + 1) / 2 for the weighted blocks, stays
+// smaller than m.
+bool choose_extra_form(const sos_program& pg, int form) {
+  if (form == 1 || !has_weighted(pg)) return false;
+  if (form == 2) return true;
+  int64_t width = pg.t, m = 0;
+  for (int j = 0; j < pg.n_constraints; ++j) {
+    const sos_constraint& c = pg.constraints[j];
+    m += c.n_rows;
+    for (int k = 0; k < c.n_blocks; ++k)
+      if (c.blocks[k].n_weight_terms > 0) width += static_cast<int64_t>(c.blocks[k].N) * (c.blocks[k].N + 1) / 2;
+  }
+  return width >= m;
+}
+
+void to_extra_form(const sos_program& pg, ExtraForm& F) {
+  const int nv = pg.n_vars;
+  struct Weighted {
+    int j, k;
+    int32_t first;                          // index of r_beta for the first beta
+    std::vector<std::vector<int32_t>> beta;  // monomials of v v^T, eq. (4) order
+  };
+  std::vector<Weighted> ws;
+  int32_t t2 = pg.t;
+  for (int j = 0; j < pg.n_constraints; ++j)
+    for (int k = 0; k < pg.constraints[j].n_blocks; ++k) {
+      const sos_block& bk = pg.constraints[j].blocks[k];
+      if (bk.n_weight_terms <= 0) continue;
+      std::vector<std::vector<int32_t>> bs;
+      for (int jj = 0; jj < bk.N; ++jj)
+        for (int ii = jj; ii < bk.N; ++ii) {
+          std::vector<int32_t> e(nv);
+          for (int q = 0; q < nv; ++q)
+            e[q] = bk.basis_exps[static_cast<int64_t>(ii) * nv + q] + bk.basis_exps[static_cast<int64_t>(jj) * nv + q];
+          bs.push_back(std::move(e));
+        }
+      auto degree = [](const std::vector<int32_t>& e) {
+        int64_t d = 0;
+        for (int32_t v : e) d += v;
+        return d;
+      };
+      std::sort(bs.begin(), bs.end(), [&](const std::vector<int32_t>& a, const std::vector<int32_t>& b) {
+        const int64_t da = degree(a), db = degree(b);
+        return da != db ? da < db : a > b;  // graded, then x1-major descending
+      });
+      bs.erase(std::unique(bs.begin(), bs.end()), bs.end());
+      ws.push_back({j, k, t2, std::move(bs)});
+      t2 += static_cast<int32_t>(ws.back().beta.size());
+    }
+  F.w.assign(pg.w, pg.w + pg.t);
+  F.w.resize(t2, 0.0);
+  size_t wi = 0;
+  for (int j = 0; j < pg.n_constraints; ++j) {
+    const sos_constraint& c = pg.constraints[j];
+    auto& tp = F.i32.emplace_back(c.term_poly, c.term_poly + c.n_terms);
+    auto& te = F.i32.emplace_back(c.term_exps, c.term_exps + c.n_terms * nv);
+    auto& tc = F.f64.emplace_back(c.term_coef, c.term_coef + c.n_terms);
+    auto& bl = F.blocks.emplace_back();
+    for (int k = 0; k < c.n_blocks; ++k) {
+      const sos_block& bk = c.blocks[k];
+      if (bk.n_weight_terms <= 0) {
+        bl.push_back(bk);
+        continue;
+      }
+      const Weighted& W = ws[wi++];
+      // g_beta = p(x) x^beta on the identity's left side
+      for (size_t q = 0; q < W.beta.size(); ++q)
+        for (int d = 0; d < bk.n_weight_terms; ++d) {
+          tp.push_back(W.first + static_cast<int32_t>(q) + 1);
+          for (int v = 0; v < nv; ++v) te.push_back(W.beta[q][v] + bk.weight_exps[static_cast<int64_t>(d) * nv + v]);
+          tc.push_back(bk.weight_coef[d]);
+        }
+    }
+    sos_constraint nc = c;
+    nc.n_terms = static_cast<int64_t>(tp.size());
+    nc.term_poly = tp.data();
+    nc.term_exps = te.data();
+    nc.term_coef = tc.data();
+    nc.n_blocks = static_cast<int32_t>(bl.size());
+    nc.blocks = bl.data();
+    F.cons.push_back(nc);
+  }
+  for (const Weighted& W : ws) {
+    const sos_block& bk = pg.constraints[W.j].blocks[W.k];
+    auto& rows = F.i32.emplace_back();
+    auto& tp = F.i32.emplace_back();
+    auto& tc = F.f64.emplace_back();
+    for (size_t q = 0; q < W.beta.size(); ++q) {
+      rows.insert(rows.end(), W.beta[q].begin(), W.beta[q].end());
+      tp.push_back(W.first + static_cast<int32_t>(q) + 1);
+      tc.push_back(-1.0);  // 0 - sum_beta r_beta (-x^beta) = v^T X v
+    }
+    auto& bl = F.blocks.emplace_back();
+    sos_block plain = bk;
+    plain.n_weight_terms = 0;
+    plain.weight_exps = nullptr;
+    plain.weight_coef = nullptr;
+    bl.push_back(plain);
+    sos_constraint nc{};
+    nc.n_rows = static_cast<int32_t>(W.beta.size());
+    nc.row_exps = rows.data();
+    nc.n_terms = static_cast<int64_t>(tp.size());
+    nc.term_poly = tp.data();
+    nc.term_exps = rows.data();  // term q is x^beta_q, the q-th row
+    nc.term_coef = tc.data();
+    nc.n_blocks = 1;
+    nc.blocks = bl.data();
+    F.cons.push_back(nc);
+  }
+  F.prog = pg;
+  F.prog.t = t2;
+  F.prog.w = F.w.data();
+  F.prog.n_constraints = static_cast<int32_t>(F.cons.size());
+  F.prog.constraints = F.cons.data();
 }
 
 int build_instance(const sos_program& pg, Local& L) {
@@ -343,7 +489,7 @@ int64_t enumerate_monomials(int32_t n_vars, int32_t degree, int32_t* out, int64_
   return count;
 }
 
-int build_plan(const sos_program* progs, int32_t n_progs, HostPlan& P, std::string& err) {
+int build_plan(const sos_program* progs, int32_t n_progs, HostPlan& P, std::string& err, int weighted_form) {
   if (!progs || n_progs < 1) {
     err = "need at least one program";
     return SOS_ERR_INVALID_ARG;
@@ -354,7 +500,16 @@ int build_plan(const sos_program* progs, int32_t n_progs, HostPlan& P, std::stri
   std::vector<std::thread> pool;
   for (unsigned w = 0; w < nth; ++w)
     pool.emplace_back([&, w]() {
-      for (int32_t i = static_cast<int32_t>(w); i < n_progs; i += static_cast<int32_t>(nth)) build_instance(progs[i], loc[i]);
+      for (int32_t i = static_cast<int32_t>(w); i < n_progs; i += static_cast<int32_t>(nth)) {
+        if (progs[i].n_constraints >= 1 && progs[i].constraints && choose_extra_form(progs[i], weighted_form)) {
+          ExtraForm F;
+          to_extra_form(progs[i], F);
+          build_instance(F.prog, loc[i]);
+          loc[i].extra_form = 1;
+        } else {
+          build_instance(progs[i], loc[i]);
+        }
+      }
     });
   for (auto& th : pool) th.join();
   for (int32_t i = 0; i < n_progs; ++i)
@@ -408,6 +563,7 @@ int build_plan(const sos_program* progs, int32_t n_progs, HostPlan& P, std::stri
     in.t = L.t;
     in.t_eff = L.t_eff;
     in.lr_off = lroff;
+    in.extra_form = L.extra_form;
     in.linv_off = loff;
     in.zeta_h = L.zeta_h;
     in.norm_b = L.norm_b;

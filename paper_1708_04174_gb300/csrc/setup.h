@@ -38,7 +38,9 @@ struct HostPlan {
 };
 
 // Builds the plan; returns SOS_OK or an SOS_ERR_* code with a message.
-int build_plan(const sos_program* progs, int32_t n_progs, HostPlan& plan, std::string& err);
+// weighted_form: 0 choose per program by eq. (42), 1 weighted blocks directly,
+// 2 extra polynomials (end of Section II).
+int build_plan(const sos_program* progs, int32_t n_progs, HostPlan& plan, std::string& err, int weighted_form = 0);
 
 // Message returned by sos_last_error(NULL) (shared by every entry point
 // that has no handle).

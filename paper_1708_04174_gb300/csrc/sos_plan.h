@@ -27,7 +27,7 @@ struct InstInfo {
   int32_t nx, m;
   int32_t t, t_eff;
   int32_t lr_off;     // first low-rank column
-  int32_t pad0;
+  int32_t extra_form; // 1: weighted blocks rewritten with extra polynomials
   int64_t linv_off;   // dense t_eff x t_eff lower-triangular L^{-1}, row-major
   double zeta_h;      // zeta^T h with h = M^{-1} zeta (eq. (25))
   double norm_b, norm_c;

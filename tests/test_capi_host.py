@@ -71,8 +71,32 @@ def _scalar_and_matrix():
 @pytest.mark.parametrize("make", PROGS)
 def test_index_map_bit_exact(capi, make):
     prog = make()
-    hp = capi.host_plan(prog)
-    cd = conic.build(prog)
+    _check_index_map(capi.host_plan(prog, weighted_form=1), conic.build(prog))
+
+
+@pytest.mark.parametrize("make", [lambda: W.ball_pop(2, 1), lambda: W.ball_pop(4, 2), lambda: W.lyapunov_local(4, 2),
+                                  lambda: W.interval_pop(8, 0), lambda: _scalar_and_matrix()])
+def test_extra_form_index_map_bit_exact(capi, make):
+    # weighted blocks rewritten with extra polynomials (end of Section II): the
+    # library's own rewrite against the oracle's, entry by entry
+    from oracle import extra_form
+
+    prog = make()
+    _check_index_map(capi.host_plan(prog, weighted_form=2), conic.build(extra_form.extra_form(prog)))
+
+
+@pytest.mark.parametrize("make", [lambda: W.interval_pop(4, 0), lambda: W.interval_pop(8, 0),
+                                  lambda: W.interval_pop(12, 1), lambda: W.ball_pop(3, 0), lambda: W.quartic_pop(3, 0)])
+def test_eq42_choice(capi, make):
+    # the automatic choice follows eq. (42) as the oracle states it
+    from oracle import extra_form
+
+    prog = make()
+    want = conic.build(extra_form.extra_form(prog) if extra_form.prefers_extra(prog) else prog)
+    assert capi.host_plan(prog)["dims"][2] == want.t
+
+
+def _check_index_map(hp, cd):
     hs = admm.HSDE(cd)
     nx, m, t, teff, nb, nent = hp["dims"]
     assert (m, t, nb) == (cd.m, cd.t, len(cd.blocks))
@@ -118,6 +142,7 @@ def test_setup_rejects_bad_input(capi):
 
 
 @pytest.mark.parametrize("kw,msg", [(dict(warm_restart=-1), "warm_restart"), (dict(infeas_tol=-1.0), "infeas_tol"),
+                                    (dict(weighted_form=3), "weighted_form"),
                                     (dict(precision=7), "precision"), (dict(solve_mode=3), "solve_mode"),
                                     (dict(large_method=5), "large_method")])
 def test_setup_rejects_bad_options(capi, kw, msg):

@@ -232,3 +232,37 @@ def test_matrix_valued_objective_vs_oracle(capi, precision, make, tol):
     assert abs(r["obj_primal"] - ro.res["pobj"]) <= tol * abs(ro.res["pobj"])
     if precision == "fp64":
         assert r["iters"] == ro.iters
+
+
+@pytest.mark.parametrize("make,iters", [(lambda: W.ball_pop(4, 2), 60), (lambda: W.lyapunov_local(4, 2), 60),
+                                        (lambda: W.interval_pop(8, 0), 80)])
+def test_extra_form_iterates_match_oracle(capi, make, iters):
+    """Weighted blocks rewritten with extra polynomials (end of Section II) by
+    the library's setup: FP64 iterates within 1e-9 of the oracle run on its
+    own rewrite of the program."""
+    from oracle import extra_form
+
+    prog = make()
+    uo, vo = oracle_packed(extra_form.extra_form(prog), iters)
+    s = capi.Solver(prog, precision=capi.PREC_FP64, weighted_form=2)
+    s.iterate(iters)
+    s.sync()
+    ug, vg = s.get_iterate()
+    s.close()
+    assert rel(ug, uo) < 1e-9, rel(ug, uo)
+    assert rel(vg, vo) < 1e-9, rel(vg, vo)
+
+
+@pytest.mark.parametrize("deg,seed", [(8, 1), (12, 4)])
+def test_interval_minimum_by_eq42_choice(capi, deg, seed):
+    """The automatic choice takes the extra form here (eq. (42) fails) and the
+    solve reaches the exact minimum on [-1, 1] (Markov-Lukacs)."""
+    prog = W.interval_pop(deg, seed)
+    s = capi.Solver(prog, precision=capi.PREC_FP64, k_check=10)
+    assert s.dims[0][2] > prog.t  # the extra coefficients joined u
+    r = s.solve(1e-10, 200000)[0]
+    s.close()
+    assert r["status"] == capi.SOLVED
+    x = np.linspace(-1.0, 1.0, 2000001)
+    pmin = np.min(sum(c * x ** e[0] for e, c in prog.meta["p"].items()))
+    assert abs(-r["obj_primal"] - pmin) <= 1e-7 * max(1.0, abs(pmin))
