@@ -234,6 +234,16 @@ int sos_sync(sos_handle* h);
 int sos_get_iterate(sos_handle* h, double* u, double* v);
 int sos_set_iterate(sos_handle* h, const double* u, const double* v);
 
+/* The same exchange with DEVICE buffers of sum_i (n_x + m + 1) doubles each
+ * (same layout and row order as above), for callers whose data already
+ * lives on the GPU (a warm-start predictor, a pipeline of solves).  The copy
+ * runs on the handle's stream and the call returns without waiting: the
+ * caller orders its own producers and consumers of u, v with that stream
+ * (sos_stream).  The first call builds a position map on the device
+ * (8 bytes per element).  set marks every instance as running. */
+int sos_get_iterate_device(sos_handle* h, double* u, double* v);
+int sos_set_iterate_device(sos_handle* h, const double* u, const double* v);
+
 /* Exponents of all monomials of degree <= degree in n_vars variables in the
  * graded order of eq. (4) (x1 > x2 > ... within a degree).  Writes at most
  * capacity rows to out (may be NULL) and the total count to *count. */

@@ -65,6 +65,8 @@ EXPORTS = {
     "sos_sync": (C.c_int, [C.c_void_p]),
     "sos_get_iterate": (C.c_int, [C.c_void_p, _f64p, _f64p]),
     "sos_set_iterate": (C.c_int, [C.c_void_p, _f64p, _f64p]),
+    "sos_get_iterate_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sos_set_iterate_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sos_monomials": (C.c_int, [C.c_int32, C.c_int32, _i32p, C.c_int64, C.POINTER(C.c_int64)]),
     "sos_host_plan": (C.c_int, [C.POINTER(sos_program), C.c_int32, C.POINTER(C.c_int64), _i32p, _f64p, _f64p,
                                 _f64p]),
@@ -392,6 +394,16 @@ class Solver:
         v = np.ascontiguousarray(v, dtype=np.float64)
         assert u.shape == (self.total,) and v.shape == (self.total,)
         _check(lib().sos_set_iterate(self.h, _ptr(u, C.c_double), _ptr(v, C.c_double)), self.h)
+
+    def get_iterate_device(self, u_ptr: int, v_ptr: int):
+        """sos_get_iterate_device: u_ptr, v_ptr are device addresses of
+        ``self.total`` doubles each; asynchronous on ``self.stream``."""
+        _check(lib().sos_get_iterate_device(self.h, C.c_void_p(u_ptr), C.c_void_p(v_ptr)), self.h)
+
+    def set_iterate_device(self, u_ptr: int, v_ptr: int):
+        """sos_set_iterate_device: device addresses as above; asynchronous on
+        ``self.stream``."""
+        _check(lib().sos_set_iterate_device(self.h, C.c_void_p(u_ptr), C.c_void_p(v_ptr)), self.h)
 
     def split(self, vec: np.ndarray):
         """Per-instance (xi, y, tau) slices of a concatenated iterate."""

@@ -72,6 +72,8 @@ struct sos_handle {
   int32_t large_grid_best = 0;    // grid chosen for the cooperative Jacobi kernel
   int64_t stage_bytes[10] = {0};  // algorithmic bytes of each profiling stage
   std::vector<int32_t> row_perm;  // device row q holds the constraint row row_perm[q]
+  int64_t* cat_map = nullptr;     // device iterate exchange: source of each concatenated position (lazy)
+  int64_t cat_total = 0;
   // persistent batched path
   bool persistent = false;
   int32_t solve_mode = 0;
@@ -1167,6 +1169,41 @@ int sos_get_iterate(sos_handle* h, double* u, double* v) {
     v[pos] = kappa[i];
     pos += 1;
   }
+  return SOS_OK;
+}
+
+static int ensure_cat_map(sos_handle* h) {
+  if (h->cat_map) return SOS_OK;
+  std::vector<int32_t> inv(h->M);
+  for (int64_t q = 0; q < h->M; ++q) inv[h->row_perm[q]] = static_cast<int32_t>(q);
+  std::vector<int64_t> map;
+  for (int i = 0; i < h->n_inst; ++i) {
+    const InstInfo& in = h->inst[i];
+    for (int k = 0; k < in.nx; ++k) map.push_back(in.x_off + k);
+    for (int k = 0; k < in.m; ++k) map.push_back(h->NX + inv[in.y_off + k]);
+    map.push_back(h->NX + h->M + i);
+  }
+  h->cat_total = static_cast<int64_t>(map.size());
+  return upload(h, map, &h->cat_map);
+}
+
+int sos_get_iterate_device(sos_handle* h, double* u, double* v) {
+  if (!h || !u || !v) return SOS_ERR_INVALID_ARG;
+  TRY(ensure_cat_map(h));
+  CK(iter64(h) ? launch_gather_iterate<double>(h->d64, h->cat_map, h->cat_total, u, v, h->stream)
+               : launch_gather_iterate<float>(h->d32, h->cat_map, h->cat_total, u, v, h->stream));
+  return SOS_OK;
+}
+
+int sos_set_iterate_device(sos_handle* h, const double* u, const double* v) {
+  if (!h || !u || !v) return SOS_ERR_INVALID_ARG;
+  TRY(ensure_cat_map(h));
+  CK(iter64(h) ? launch_scatter_iterate<double>(h->d64, h->cat_map, h->cat_total, u, v, h->active, h->stream)
+               : launch_scatter_iterate<float>(h->d32, h->cat_map, h->cat_total, u, v, h->active, h->stream));
+  TRY(init_wl(h));
+  std::fill(h->active_h.begin(), h->active_h.end(), 1);
+  std::fill(h->iters_h.begin(), h->iters_h.end(), 0);
+  std::fill(h->status_h.begin(), h->status_h.end(), SOS_RUNNING);
   return SOS_OK;
 }
 

@@ -18,6 +18,7 @@
 //   W_e = u_hat_1,e - v_e = u_e + a_e u_hat_2[row(e)].
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cstdio>
 
@@ -1881,5 +1882,75 @@ SOS_INSTANTIATE(float)
 SOS_INSTANTIATE_PROJ(double, double)
 SOS_INSTANTIATE_PROJ(double, float)
 SOS_INSTANTIATE_PROJ(float, float)
+
+// ---------------------------------------------------------------------------
+// Iterate exchange with caller device buffers (layout in kernels.h)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_gather_iterate(DevPlan<T> p, const int64_t* map, int64_t total, double* u, double* v) {
+  const int64_t NX = p.NX, M = p.M;
+  for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < total;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t src = map[q];
+    if (src < NX) {
+      u[q] = static_cast<double>(p.ux[src]);
+      v[q] = static_cast<double>(p.vx[src]);
+    } else if (src < NX + M) {
+      u[q] = static_cast<double>(p.uy[src - NX]);
+      v[q] = static_cast<double>(p.vy[src - NX]);
+    } else {
+      u[q] = p.tau[src - NX - M];
+      v[q] = p.kappa[src - NX - M];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_scatter_iterate(DevPlan<T> p, const int64_t* map, int64_t total, const double* u, const double* v,
+                                  int32_t* active) {
+  const int64_t NX = p.NX, M = p.M;
+  for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < total;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t dst = map[q];
+    if (dst < NX) {
+      p.ux[dst] = static_cast<T>(u[q]);
+      p.vx[dst] = static_cast<T>(v[q]);
+    } else if (dst < NX + M) {
+      p.uy[dst - NX] = static_cast<T>(u[q]);
+      p.vy[dst - NX] = static_cast<T>(v[q]);
+    } else {
+      p.tau[dst - NX - M] = u[q];
+      p.kappa[dst - NX - M] = v[q];
+      active[dst - NX - M] = 1;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_gather_iterate(const DevPlan<T>& p, const int64_t* map, int64_t total, double* u, double* v,
+                                  cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, 152 * 16));
+  k_gather_iterate<T><<<grid, 256, 0, s>>>(p, map, total, u, v);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scatter_iterate(const DevPlan<T>& p, const int64_t* map, int64_t total, const double* u,
+                                   const double* v, int32_t* active, cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, 152 * 16));
+  k_scatter_iterate<T><<<grid, 256, 0, s>>>(p, map, total, u, v, active);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_gather_iterate<double>(const DevPlan<double>&, const int64_t*, int64_t, double*, double*,
+                                                   cudaStream_t);
+template cudaError_t launch_gather_iterate<float>(const DevPlan<float>&, const int64_t*, int64_t, double*, double*,
+                                                  cudaStream_t);
+template cudaError_t launch_scatter_iterate<double>(const DevPlan<double>&, const int64_t*, int64_t, const double*,
+                                                    const double*, int32_t*, cudaStream_t);
+template cudaError_t launch_scatter_iterate<float>(const DevPlan<float>&, const int64_t*, int64_t, const double*,
+                                                   const double*, int32_t*, cudaStream_t);
 
 }  // namespace sos

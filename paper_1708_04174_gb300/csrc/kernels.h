@@ -178,6 +178,17 @@ template <typename T, typename TC>
 constexpr int form_of() {
   return sizeof(TC) == 8 ? kFormFP64 : (sizeof(T) == 8 ? kFormMixed : kFormFP32);
 }
+// Iterate exchange with caller DEVICE buffers in the concatenated layout
+// (per instance [xi (n_x), y (m), tau] for u, [z, s, kappa] for v): map[q]
+// is the source of position q, an index into x (< NX), into the device rows
+// (NX .. NX + M) or an instance (NX + M + i) for tau / kappa.  The scatter
+// also marks every instance running.
+template <typename T>
+cudaError_t launch_gather_iterate(const DevPlan<T>& p, const int64_t* map, int64_t total, double* u, double* v,
+                                  cudaStream_t s);
+template <typename T>
+cudaError_t launch_scatter_iterate(const DevPlan<T>& p, const int64_t* map, int64_t total, const double* u,
+                                   const double* v, int32_t* active, cudaStream_t s);
 size_t psd_small_smem_bytes(int maxN, int form);
 size_t large_smem_bytes(int N, size_t es);
 int psd_small_max_n(int form);

@@ -266,3 +266,24 @@ def test_interval_minimum_by_eq42_choice(capi, deg, seed):
     x = np.linspace(-1.0, 1.0, 2000001)
     pmin = np.min(sum(c * x ** e[0] for e, c in prog.meta["p"].items()))
     assert abs(-r["obj_primal"] - pmin) <= 1e-7 * max(1.0, abs(pmin))
+
+
+def test_batch_with_per_instance_weighted_form(capi):
+    """eq. (42) is applied per program: in one batch an interval POP of
+    degree 8 takes the extra form and a ball POP the direct one; each
+    instance's FP64 iterates match the oracle on that instance's form."""
+    from oracle import extra_form
+
+    progs = [W.interval_pop(8, 5), W.ball_pop(3, 2), W.interval_pop(4, 6), W.matrix_pop(2, 2, 4)]
+    iters = 50
+    s = capi.Solver(progs, precision=capi.PREC_FP64)
+    s.iterate(iters)
+    s.sync()
+    ug, vg = s.get_iterate()
+    for (xg, yg, tg), (zg, sg, kg), prog in zip(s.split(ug), s.split(vg), progs):
+        form = extra_form.extra_form(prog) if extra_form.prefers_extra(prog) else prog
+        uo, vo = oracle_packed(form, iters)
+        assert rel(np.concatenate([xg, yg, [tg]]), uo) < 1e-9
+        assert rel(np.concatenate([zg, sg, [kg]]), vo) < 1e-9
+    assert [d[2] for d in s.dims] == [8, 1, 1, 1]
+    s.close()

@@ -76,3 +76,53 @@ def test_iterate_round_trip_keeps_row_order(capi):
         assert np.array_equal(u2[pos + nx:pos + nx + m], u[pos + nx:pos + nx + m])
         pos += nx + m + 1
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "fp32"])
+def test_device_iterate_exchange(capi, precision):
+    # sos_get_iterate_device / sos_set_iterate_device: the same layout and row
+    # order as the host calls; iterating after a device set equals iterating
+    # after a host set of the same values
+    import torch
+
+    prec = {"fp64": capi.PREC_FP64, "mixed": capi.PREC_MIXED, "fp32": capi.PREC_FP32}[precision]
+    a = capi.Solver(BATCH, precision=prec, k_check=10)
+    b = capi.Solver(BATCH, precision=prec, k_check=10)
+    a.iterate(7)
+    a.sync()
+    uh, vh = a.get_iterate()
+    ud = torch.empty(a.total, dtype=torch.float64, device="cuda")
+    vd = torch.empty(a.total, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    a.get_iterate_device(ud.data_ptr(), vd.data_ptr())
+    a.sync()
+    assert np.array_equal(ud.cpu().numpy(), uh) and np.array_equal(vd.cpu().numpy(), vh)
+
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(a.total)
+    v = rng.standard_normal(a.total)
+    pos = 0
+    for d in a.dims:  # tau > 0 and kappa >= 0 as after any ADMM step
+        pos += d[0] + d[1]
+        u[pos], v[pos] = 1.0 + abs(u[pos]), abs(v[pos])
+        pos += 1
+    ud.copy_(torch.from_numpy(u))
+    vd.copy_(torch.from_numpy(v))
+    torch.cuda.synchronize()
+    a.set_iterate_device(ud.data_ptr(), vd.data_ptr())
+    a.sync()
+    b.set_iterate(u, v)
+    ua, va = a.get_iterate()
+    ub, vb = b.get_iterate()
+    assert np.array_equal(ua, ub) and np.array_equal(va, vb)
+    if precision != "fp32":
+        assert np.array_equal(ua, u) and np.array_equal(va, v)
+    a.iterate(5)
+    b.iterate(5)
+    a.sync()
+    b.sync()
+    ua, va = a.get_iterate()
+    ub, vb = b.get_iterate()
+    assert np.array_equal(ua, ub) and np.array_equal(va, vb)
+    a.close()
+    b.close()
