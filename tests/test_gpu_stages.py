@@ -86,8 +86,9 @@ def test_device_iterate_exchange(capi, precision):
     import torch
 
     prec = {"fp64": capi.PREC_FP64, "mixed": capi.PREC_MIXED, "fp32": capi.PREC_FP32}[precision]
-    a = capi.Solver(BATCH, precision=prec, k_check=10)
-    b = capi.Solver(BATCH, precision=prec, k_check=10)
+    # one launch path for both (the autotuner may otherwise pick different ones)
+    a = capi.Solver(BATCH, precision=prec, k_check=10, solve_mode=1)
+    b = capi.Solver(BATCH, precision=prec, k_check=10, solve_mode=1)
     a.iterate(7)
     a.sync()
     uh, vh = a.get_iterate()
