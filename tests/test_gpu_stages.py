@@ -89,8 +89,13 @@ def test_device_iterate_exchange(capi, precision):
     # one launch path for both (the autotuner may otherwise pick different ones)
     a = capi.Solver(BATCH, precision=prec, k_check=10, solve_mode=1)
     b = capi.Solver(BATCH, precision=prec, k_check=10, solve_mode=1)
+    # the same history on both: the Jacobi projections start from the
+    # previous iteration's eigenvectors, so only equal histories give
+    # bit-equal iterates
     a.iterate(7)
+    b.iterate(7)
     a.sync()
+    b.sync()
     uh, vh = a.get_iterate()
     ud = torch.empty(a.total, dtype=torch.float64, device="cuda")
     vd = torch.empty(a.total, dtype=torch.float64, device="cuda")
