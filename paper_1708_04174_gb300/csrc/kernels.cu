@@ -982,11 +982,16 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
       __syncthreads();
       if (any_rot != round_id) continue;  // same decision in every CTA
       sweep_rot = true;
-      const int64_t nblk = static_cast<int64_t>(H) * H;
+      // 2x2 tasks over pairs k1 <= k2 only (numbered k2 (k2 + 1) / 2 + k1),
+      // then N x H row tasks of V: on 152 CTAs of 256 threads at most one task
+      // per thread up to N = 248
+      const int64_t nblk = static_cast<int64_t>(H) * (H + 1) / 2;
       for (int64_t task = gt; task < nblk + static_cast<int64_t>(N) * H; task += gs) {
         if (task < nblk) {
-          const int k1 = static_cast<int>(task / H), k2 = static_cast<int>(task - static_cast<int64_t>(k1) * H);
-          if (k1 > k2) continue;
+          int k2 = static_cast<int>((sqrtf(8.0f * static_cast<float>(task) + 1.0f) - 1.0f) * 0.5f);
+          while (k2 > 0 && static_cast<int64_t>(k2) * (k2 + 1) / 2 > task) --k2;
+          while (k2 < H - 1 && static_cast<int64_t>(k2 + 1) * (k2 + 2) / 2 <= task) ++k2;
+          const int k1 = static_cast<int>(task - static_cast<int64_t>(k2) * (k2 + 1) / 2);
           const int p1 = rp[k1], q1 = rq[k1], p2 = rp[k2], q2 = rq[k2];
           const TC c1 = rc[k1], s1 = rs[k1], c2 = rc[k2], s2 = rs[k2];
           if (k1 == k2) {
