@@ -86,6 +86,11 @@ struct sos_handle {
   InstReport* p_rep = nullptr;
   cudaGraphExec_t graph = nullptr;
   bool graph_tried = false;
+  // small-block projections of an iteration run beside the large-block ones
+  // (disjoint blocks): forked onto this stream after the affine step, joined
+  // before the next step
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err;
 };
 
@@ -240,11 +245,21 @@ cudaError_t enqueue_stage(sos_handle* h, const DevPlan<T>& p, std::vector<LargeB
     e = launch_affine<T>(p, h->shape, h->stream);
     if (e != cudaSuccess) return e;
   }
+  const bool fork = stage == 3 && h->side && !h->small.empty() && (!large.empty() || !h->ns_large.empty());
+  if (fork) {
+    e = cudaEventRecord(h->ev_fork, h->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    if (e != cudaSuccess) return e;
+  }
   if (stage == 1 || stage == 3)
     for (auto& c : h->small) {
-      e = launch_psd_small<T, TC>(p, c.ids, c.count, c.maxN, wm, h->stream);
+      e = launch_psd_small<T, TC>(p, c.ids, c.count, c.maxN, wm, fork ? h->side : h->stream);
       if (e != cudaSuccess) return e;
     }
+  if (fork) {
+    e = cudaEventRecord(h->ev_join, h->side);
+    if (e != cudaSuccess) return e;
+  }
   if (stage == 2 || stage == 3) {
     for (auto& lb : large) {
       e = launch_psd_large<T, TC>(p, lb.bid, lb.N, lb.scratch, lb.grid, h->stream);
@@ -255,6 +270,7 @@ cudaError_t enqueue_stage(sos_handle* h, const DevPlan<T>& p, std::vector<LargeB
       if (e != cudaSuccess) return e;
     }
   }
+  if (fork) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
   return e;
 }
 
@@ -812,6 +828,11 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   h->d64.kappa = c.kappa;
   h->d64.err = c.err;
   h->d64.resid = c.resid;
+  if (!h->small.empty() && !large.empty()) {  // small and large projections side by side
+    CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  }
   // persistent batched path: every block small, and either requested or a batch
   const bool eligible = large.empty();
   h->persistent = eligible && (h->solve_mode == 2 || (h->solve_mode == 0 && n_progs > 1));
@@ -974,6 +995,12 @@ void sos_destroy(sos_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (void* p : h->allocs) cudaFree(p);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
