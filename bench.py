@@ -650,7 +650,7 @@ def main():
         fp64_peak = 1190.0 if prec == capi.PREC_FP64 else 69700.0
         # DRAM bytes of one launch from the ncu capture of the current kernel
         # summarised in profiles/k_psd_large_fp64_ball_pop_n20.md (FP64 only)
-        traffic = 492288 + 356864 if prec == capi.PREC_FP64 and args.workload == "ball_pop_n20" else None
+        traffic = None
         roof = {"kernel": "k_psd_large (grid Jacobi eigen-projection)", "bound": "alu",
                 "achieved": flops / (dom_ms / 1e3) / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
                 "frac": flops / (dom_ms / 1e3) / 1e9 / fp64_peak, "traffic": traffic,

@@ -53,6 +53,23 @@ __device__ double block_sum(double v, double* sh) {
   return sh[32];
 }
 
+// Block maximum (inputs >= 0); result valid in every thread.
+__device__ double block_max(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (w == 0) {
+    double x = (l < nw) ? sh[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (l == 0) sh[32] = x;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
 template <typename T>
 __device__ __forceinline__ double d(T x) {
   return static_cast<double>(x);
@@ -876,7 +893,7 @@ __device__ T tile_mm(const T* A, const T* B, int Np, int ti, int tj, int mode, T
 }
 
 template <typename T, typename TC>
-__global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeScratch<TC> L) {
+__global__ void __launch_bounds__(256, 1) k_psd_large(DevPlan<T> p, int bid, LargeScratch<TC> L) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double red[40];
   __shared__ TC sA[16 * 17], sB[16 * 17];
@@ -960,6 +977,27 @@ __global__ void __launch_bounds__(256) k_psd_large(DevPlan<T> p, int bid, LargeS
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
     bool sweep_rot = false;
     sweeps = sweep + 1;
+    {
+      // A sweep in which no off-diagonal entry exceeds thr rotates nothing
+      // and leaves the matrix as it is: one grid-wide maximum decides that
+      // up front (the same value in every CTA) instead of N - 1 rounds of
+      // rotation parameters.  The partial maxima alternate between two
+      // buffers: check k + 2 cannot overwrite check k's partials before
+      // every CTA has passed check k + 1's barrier.
+      TC mx = 0;
+      for (int64_t q = gt; q < static_cast<int64_t>(N) * Np; q += gs) {
+        const int i = static_cast<int>(q / Np), j = static_cast<int>(q - static_cast<int64_t>(i) * Np);
+        if (j > i && j < N) mx = fmax(mx, fabs(ldg_cg(cur + q)));
+      }
+      const double bm = block_max(d(mx), red);
+      double* part = L.partial + static_cast<int64_t>(1 + (sweep & 1)) * G;
+      if (threadIdx.x == 0) part[blockIdx.x] = bm;
+      if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+      double gv = 0.0;
+      for (unsigned c = threadIdx.x; c < G; c += blockDim.x) gv = fmax(gv, __ldcg(part + c));
+      const double gm = block_max(gv, red);
+      if (!(gm > d(thr))) break;
+    }
     for (int r = 0; r < Np - 1; ++r, ++round_id) {
       for (int k = threadIdx.x; k < H; k += blockDim.x) {
         int a, b;

@@ -79,7 +79,7 @@ struct LargeScratch {
   T* B1 = nullptr;
   T* V = nullptr;    // eigenvectors, kept across iterations (warm start)
   T* T1 = nullptr;   // GEMM temporary
-  double* partial = nullptr;   // per-CTA partial sums
+  double* partial = nullptr;   // per-CTA partials, 3 x grid (norm; sweep checks, alternating)
   int32_t* flags = nullptr;    // unused (kept for layout)
   uint32_t* bar = nullptr;     // grid barrier: [arrivals, released generation], zeroed before each launch
   int32_t* sweeps_out = nullptr;  // number of sweeps of the last launch
