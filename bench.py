@@ -648,9 +648,9 @@ def main():
         flops = sum(9.0 * N ** 3 for N in big)
         dom_ms = stage_ms["psd_large"]
         fp64_peak = 1190.0 if prec == capi.PREC_FP64 else 69700.0
-        # DRAM bytes of one launch from the ncu capture of the current kernel
-        # summarised in profiles/k_psd_large_fp64_ball_pop_n20.md (FP64 only)
-        traffic = None
+        # DRAM bytes of one launch (read + write) from the ncu capture of the
+        # current kernel, summarised in profiles/k_psd_large_fp64_ball_pop_n20.md
+        traffic = 482048 + 476928 if prec == capi.PREC_FP64 and args.workload == "ball_pop_n20" else None
         roof = {"kernel": "k_psd_large (grid Jacobi eigen-projection)", "bound": "alu",
                 "achieved": flops / (dom_ms / 1e3) / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
                 "frac": flops / (dom_ms / 1e3) / 1e9 / fp64_peak, "traffic": traffic,
