@@ -74,8 +74,22 @@ def test_index_map_bit_exact(capi, make):
     _check_index_map(capi.host_plan(prog, weighted_form=1), conic.build(prog))
 
 
+def _two_weighted_constraints():
+    # constraint 0: s0 + (1 - x^2 - y^2) s1 + (x + 2) s2 (two weighted blocks);
+    # constraint 1: s3 + (4 - y^2) s4; one shared u
+    from instances.program import Block, Constraint, SOSProgram
+
+    p = W.quartic_poly(2, 7)
+    c0 = Constraint(degree=4, g0=p, g=[{(0, 0): 1.0}],
+                    blocks=[Block(2), Block(1, {(0, 0): 1.0, (2, 0): -1.0, (0, 2): -1.0}), Block(1, {(1, 0): 1.0, (0, 0): 2.0})])
+    q = W.quartic_poly(2, 8)
+    c1 = Constraint(degree=4, g0=q, g=[{(0, 0): 1.0}], blocks=[Block(2), Block(1, {(0, 0): 4.0, (0, 2): -1.0})])
+    return SOSProgram(n=2, w=np.array([-1.0]), constraints=[c0, c1])
+
+
 @pytest.mark.parametrize("make", [lambda: W.ball_pop(2, 1), lambda: W.ball_pop(4, 2), lambda: W.lyapunov_local(4, 2),
-                                  lambda: W.interval_pop(8, 0), lambda: _scalar_and_matrix()])
+                                  lambda: W.interval_pop(8, 0), lambda: _scalar_and_matrix(),
+                                  lambda: _two_weighted_constraints()])
 def test_extra_form_index_map_bit_exact(capi, make):
     # weighted blocks rewritten with extra polynomials (end of Section II): the
     # library's own rewrite against the oracle's, entry by entry
@@ -126,6 +140,21 @@ def test_local_lyapunov_matches_table3_shape(capi):
     hp = capi.host_plan(W.lyapunov_local(10, 10))
     nx, m, t, teff, nb, nent = hp["dims"]
     assert teff == 110 and t == 55 and m == 1045
+
+
+def test_extra_form_of_two_weighted_constraints_keeps_the_optimum(capi):
+    # the rewrite with three weighted blocks in two constraints: same optimum
+    # as the direct form (oracle), and the library's sizes equal the oracle's
+    from oracle import extra_form
+
+    prog = _two_weighted_constraints()
+    ex = extra_form.extra_form(prog)
+    a = admm.solve(conic.build(prog), 1e-9, 400000, k_check=10)
+    b = admm.solve(conic.build(ex), 1e-9, 400000, k_check=10)
+    assert a.status == admm.SOLVED and b.status == admm.SOLVED
+    assert abs(a.res["pobj"] - b.res["pobj"]) <= 1e-6 * max(1.0, abs(a.res["pobj"]))
+    hp = capi.host_plan(prog, weighted_form=2)
+    assert hp["dims"][2] == 1 + 3 * 6 and hp["dims"][4] == 5  # 3 x C(4, 2) coefficients; blocks 2 + 3
 
 
 def test_setup_rejects_bad_input(capi):
