@@ -151,6 +151,28 @@ struct ExtraForm {
   sos_program prog{};
 };
 
+// Structural checks of one program (sizes and pointers), before anything
+// reads its arrays; the coefficient matching reports the rest.
+const char* program_error(const sos_program& pg) {
+  if (pg.n_vars < 1) return "n_vars must be >= 1";
+  if (pg.t < 0 || (pg.t > 0 && !pg.w)) return "t < 0 or w missing";
+  if (pg.n_constraints < 1 || !pg.constraints) return "no constraints";
+  for (int j = 0; j < pg.n_constraints; ++j) {
+    const sos_constraint& c = pg.constraints[j];
+    if (c.n_rows < 1 || !c.row_exps) return "constraint without rows";
+    if (c.n_terms < 0 || (c.n_terms > 0 && (!c.term_poly || !c.term_exps || !c.term_coef)))
+      return "term arrays missing";
+    if (c.n_blocks < 0 || (c.n_blocks > 0 && !c.blocks)) return "block array missing";
+    for (int k = 0; k < c.n_blocks; ++k) {
+      const sos_block& bk = c.blocks[k];
+      if (bk.N < 1 || !bk.basis_exps) return "block with N < 1";
+      if (bk.n_weight_terms < 0 || (bk.n_weight_terms > 0 && (!bk.weight_exps || !bk.weight_coef)))
+        return "weight arrays missing";
+    }
+  }
+  return nullptr;
+}
+
 bool has_weighted(const sos_program& pg) {
   for (int j = 0; j < pg.n_constraints; ++j)
     for (int k = 0; k < pg.constraints[j].n_blocks; ++k)
@@ -501,7 +523,9 @@ int build_plan(const sos_program* progs, int32_t n_progs, HostPlan& P, std::stri
   for (unsigned w = 0; w < nth; ++w)
     pool.emplace_back([&, w]() {
       for (int32_t i = static_cast<int32_t>(w); i < n_progs; i += static_cast<int32_t>(nth)) {
-        if (progs[i].n_constraints >= 1 && progs[i].constraints && choose_extra_form(progs[i], weighted_form)) {
+        if (const char* msg = program_error(progs[i])) {
+          fail(loc[i], SOS_ERR_INVALID_ARG, msg);
+        } else if (choose_extra_form(progs[i], weighted_form)) {
           ExtraForm F;
           to_extra_form(progs[i], F);
           build_instance(F.prog, loc[i]);

@@ -157,6 +157,50 @@ def test_extra_form_of_two_weighted_constraints_keeps_the_optimum(capi):
     assert hp["dims"][2] == 1 + 3 * 6 and hp["dims"][4] == 5  # 3 x C(4, 2) coefficients; blocks 2 + 3
 
 
+@pytest.mark.parametrize("defect", ["terms", "weights", "blocks", "negative_terms"])
+@pytest.mark.parametrize("form", [0, 2])
+def test_setup_rejects_missing_arrays(capi, defect, form):
+    # programs built directly as C structs with a count but no array: setup
+    # reports INVALID_ARG (before the extra-polynomial rewrite reads anything)
+    import ctypes as C
+
+    n = 1
+    rows = np.ascontiguousarray([[0], [1], [2]], dtype=np.int32)
+    bas = np.ascontiguousarray([[0], [1]], dtype=np.int32)
+    wexp = np.ascontiguousarray([[0], [2]], dtype=np.int32)
+    wcoef = np.ascontiguousarray([1.0, -1.0])
+    tp = np.ascontiguousarray([0, 1], dtype=np.int32)
+    te = np.ascontiguousarray([[2], [0]], dtype=np.int32)
+    tc = np.ascontiguousarray([1.0, 1.0])
+    w = np.ascontiguousarray([-1.0])
+    blk = (capi.sos_block * 2)()
+    for b in blk:
+        b.N = 2
+        b.basis_exps = bas.ctypes.data_as(C.POINTER(C.c_int32))
+    blk[1].N = 1
+    blk[1].n_weight_terms = 2
+    blk[1].weight_exps = None if defect == "weights" else wexp.ctypes.data_as(C.POINTER(C.c_int32))
+    blk[1].weight_coef = wcoef.ctypes.data_as(C.POINTER(C.c_double))
+    con = (capi.sos_constraint * 1)()
+    con[0].n_rows = 3
+    con[0].row_exps = rows.ctypes.data_as(C.POINTER(C.c_int32))
+    con[0].n_terms = -1 if defect == "negative_terms" else 2
+    con[0].term_poly = None if defect == "terms" else tp.ctypes.data_as(C.POINTER(C.c_int32))
+    con[0].term_exps = te.ctypes.data_as(C.POINTER(C.c_int32))
+    con[0].term_coef = tc.ctypes.data_as(C.POINTER(C.c_double))
+    con[0].n_blocks = 2
+    con[0].blocks = None if defect == "blocks" else blk
+    prog = (capi.sos_program * 1)()
+    prog[0].n_vars = n
+    prog[0].t = 1
+    prog[0].w = w.ctypes.data_as(C.POINTER(C.c_double))
+    prog[0].n_constraints = 1
+    prog[0].constraints = con
+    dims = (C.c_int64 * 6)()
+    rc = capi.lib().sos_host_plan(prog, form, dims, None, None, None, None)
+    assert rc == capi.SOS_ERR_INVALID_ARG
+
+
 def test_setup_rejects_bad_input(capi):
     from instances.program import Block, Constraint, SOSProgram
 
