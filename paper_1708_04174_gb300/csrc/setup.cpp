@@ -10,6 +10,7 @@
 #include "setup.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -98,36 +99,120 @@ int fail(Local& L, int code, const std::string& msg) {
   return code;
 }
 
-// Dense FP64 Cholesky C = L L^T (row-major, lower), in place.  false if not SPD.
-bool cholesky(std::vector<double>& C, int n) {
-  for (int j = 0; j < n; ++j) {
-    double d = C[static_cast<size_t>(j) * n + j];
-    for (int k = 0; k < j; ++k) d -= C[static_cast<size_t>(j) * n + k] * C[static_cast<size_t>(j) * n + k];
-    if (!(d > 0.0) || !std::isfinite(d)) return false;
-    d = std::sqrt(d);
-    C[static_cast<size_t>(j) * n + j] = d;
-    for (int i = j + 1; i < n; ++i) {
-      double s = C[static_cast<size_t>(i) * n + j];
-      for (int k = 0; k < j; ++k) s -= C[static_cast<size_t>(i) * n + k] * C[static_cast<size_t>(j) * n + k];
-      C[static_cast<size_t>(i) * n + j] = s / d;
+// Barrier for the threads of one dense factorisation (spins, then yields).
+class SpinBarrier {
+ public:
+  explicit SpinBarrier(int n) : n_(n) {}
+  void wait() {
+    const int g = gen_.load(std::memory_order_acquire);
+    if (count_.fetch_add(1, std::memory_order_acq_rel) == n_ - 1) {
+      count_.store(0, std::memory_order_relaxed);
+      gen_.fetch_add(1, std::memory_order_release);
+      return;
     }
+    for (int spin = 0; gen_.load(std::memory_order_acquire) == g; ++spin)
+      if (spin > 256) std::this_thread::yield();
   }
+
+ private:
+  const int n_;
+  std::atomic<int> count_{0}, gen_{0};
+};
+
+// Dense FP64 Cholesky C = L L^T (row-major, lower), in place.  false if not
+// SPD.  Column j: L_jj = sqrt(C_jj - sum_k<j L_jk^2), then every row below it
+// L_ij = (C_ij - sum_k<j L_ik L_jk) / L_jj, the sums in ascending k.  With
+// nth > 1 the rows of a column are shared cyclically among threads (one
+// barrier per column; the owner of row j + 1 also forms L_{j+1,j+1}); every
+// entry is computed by the same operations in the same order as with one
+// thread.
+bool cholesky(std::vector<double>& C, int n, int nth) {
+  double* A = C.data();
+  auto row_entry = [&](int i, int j, double d) {
+    double s = A[static_cast<size_t>(i) * n + j];
+    for (int k = 0; k < j; ++k) s -= A[static_cast<size_t>(i) * n + k] * A[static_cast<size_t>(j) * n + k];
+    A[static_cast<size_t>(i) * n + j] = s / d;
+  };
+  auto diag = [&](int j) {  // false if not positive
+    double d = A[static_cast<size_t>(j) * n + j];
+    for (int k = 0; k < j; ++k) d -= A[static_cast<size_t>(j) * n + k] * A[static_cast<size_t>(j) * n + k];
+    if (!(d > 0.0) || !std::isfinite(d)) return false;
+    A[static_cast<size_t>(j) * n + j] = std::sqrt(d);
+    return true;
+  };
+  nth = std::max(1, std::min(nth, n / 64));
+  bool ok = true;
+  if (nth == 1) {
+    for (int j = 0; j < n && ok; ++j) {
+      ok = diag(j);
+      if (!ok) break;
+      const double d = A[static_cast<size_t>(j) * n + j];
+      for (int i = j + 1; i < n; ++i) row_entry(i, j, d);
+    }
+  } else {
+    ok = n < 1 || diag(0);
+    std::atomic<bool> bad{!ok};
+    SpinBarrier bar(nth);
+    auto work = [&](int t) {
+      for (int j = 0; j < n - 1; ++j) {
+        const double d = A[static_cast<size_t>(j) * n + j];
+        if ((j + 1) % nth == t) {  // row j + 1 first, then the next diagonal
+          row_entry(j + 1, j, d);
+          if (!diag(j + 1)) bad.store(true, std::memory_order_relaxed);
+        }
+        for (int i = j + 2 + ((t - (j + 2)) % nth + nth) % nth; i < n; i += nth) row_entry(i, j, d);
+        bar.wait();
+        if (bad.load(std::memory_order_relaxed)) return;
+      }
+    };
+    if (ok) {
+      std::vector<std::thread> pool;
+      for (int t = 1; t < nth; ++t) pool.emplace_back(work, t);
+      work(0);
+      for (auto& th : pool) th.join();
+    }
+    ok = !bad.load();
+  }
+  if (!ok) return false;
   for (int i = 0; i < n; ++i)
-    for (int j = i + 1; j < n; ++j) C[static_cast<size_t>(i) * n + j] = 0.0;
+    for (int j = i + 1; j < n; ++j) A[static_cast<size_t>(i) * n + j] = 0.0;
   return true;
 }
 
-// Inverse of a lower-triangular matrix (row-major), FP64.
-std::vector<double> tri_inverse(const std::vector<double>& Lm, int n) {
+// Inverse of a lower-triangular matrix (row-major), FP64.  Column c of L^{-1}
+// solves L x = e_c and depends on no other column, so threads take chunks of
+// columns; inside a chunk row i is formed from the rows k < i by contiguous
+// multiply-adds: X_ic = -(sum_{k=c}^{i-1} L_ik X_kc) / L_ii (ascending k),
+// X_ii = 1 / L_ii.
+std::vector<double> tri_inverse(const std::vector<double>& Lm, int n, int nth) {
   std::vector<double> X(static_cast<size_t>(n) * n, 0.0);
-  for (int j = 0; j < n; ++j) {  // column j of L^{-1}: solve L x = e_j
-    X[static_cast<size_t>(j) * n + j] = 1.0 / Lm[static_cast<size_t>(j) * n + j];
-    for (int i = j + 1; i < n; ++i) {
-      double s = 0.0;
-      for (int k = j; k < i; ++k) s += Lm[static_cast<size_t>(i) * n + k] * X[static_cast<size_t>(k) * n + j];
-      X[static_cast<size_t>(i) * n + j] = -s / Lm[static_cast<size_t>(i) * n + i];
+  constexpr int kChunk = 32;
+  const int nchunk = (n + kChunk - 1) / kChunk;
+  auto chunk = [&](int q) {
+    const int c0 = q * kChunk, c1 = std::min(n, c0 + kChunk);
+    for (int i = c0; i < n; ++i) {
+      double* xi = &X[static_cast<size_t>(i) * n];
+      const double* li = &Lm[static_cast<size_t>(i) * n];
+      for (int k = c0; k < i; ++k) {
+        const double a = li[k];
+        const double* xk = &X[static_cast<size_t>(k) * n];
+        const int ce = std::min(k + 1, c1);
+        for (int c = c0; c < ce; ++c) xi[c] += a * xk[c];
+      }
+      const double lii = li[i];
+      const int ce = std::min(i, c1);
+      for (int c = c0; c < ce; ++c) xi[c] = -xi[c] / lii;
+      if (i < c1) xi[i] = 1.0 / lii;
     }
-  }
+  };
+  nth = std::max(1, std::min(nth, nchunk));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nth; ++t)
+    pool.emplace_back([&, t]() {
+      for (int q = t; q < nchunk; q += nth) chunk(q);
+    });
+  for (int q = 0; q < nchunk; q += nth) chunk(q);
+  for (auto& th : pool) th.join();
   return X;
 }
 
@@ -297,7 +382,9 @@ void to_extra_form(const sos_program& pg, ExtraForm& F) {
   F.prog.constraints = F.cons.data();
 }
 
-int build_instance(const sos_program& pg, Local& L) {
+// inner_threads: threads the dense factorisation of this instance may use
+// (1 while the instances of a plan are built in parallel)
+int build_instance(const sos_program& pg, Local& L, int inner_threads) {
   const int nv = pg.n_vars;
   if (nv < 1) return fail(L, SOS_ERR_INVALID_ARG, "n_vars must be >= 1");
   if (pg.t < 0 || (pg.t > 0 && !pg.w)) return fail(L, SOS_ERR_INVALID_ARG, "t < 0 or w missing");
@@ -435,8 +522,8 @@ int build_instance(const sos_program& pg, Local& L) {
     }
   }
   std::vector<double> Lf = C;
-  if (!cholesky(Lf, te)) return fail(L, SOS_ERR_FACTOR, "Woodbury core is not positive definite");
-  L.linv = tri_inverse(Lf, te);
+  if (!cholesky(Lf, te, inner_threads)) return fail(L, SOS_ERR_FACTOR, "Woodbury core is not positive definite");
+  L.linv = tri_inverse(Lf, te, inner_threads);
 
   // h = M^{-1} zeta, zeta = [c; -b] (eq. (25)), via eq. (27) with the Cholesky factor
   //   r = -b - A c ; sigma2 = (P + A_L A_L^T)^{-1} r ; sigma1 = c + A^T sigma2
@@ -518,6 +605,9 @@ int build_plan(const sos_program* progs, int32_t n_progs, HostPlan& P, std::stri
   }
   std::vector<Local> loc(n_progs);
   unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  // few programs: one builder thread, and the dense factorisations of the
+  // Woodbury cores use the cores instead
+  const int inner = n_progs < 4 ? static_cast<int>(nth) : 1;
   if (n_progs < 4) nth = 1;
   std::vector<std::thread> pool;
   for (unsigned w = 0; w < nth; ++w)
@@ -528,10 +618,10 @@ int build_plan(const sos_program* progs, int32_t n_progs, HostPlan& P, std::stri
         } else if (choose_extra_form(progs[i], weighted_form)) {
           ExtraForm F;
           to_extra_form(progs[i], F);
-          build_instance(F.prog, loc[i]);
+          build_instance(F.prog, loc[i], inner);
           loc[i].extra_form = 1;
         } else {
-          build_instance(progs[i], loc[i]);
+          build_instance(progs[i], loc[i], inner);
         }
       }
     });

@@ -201,6 +201,16 @@ def test_setup_rejects_missing_arrays(capi, defect, form):
     assert rc == capi.SOS_ERR_INVALID_ARG
 
 
+def test_factor_failure_is_reported(capi):
+    # a NaN coefficient makes the Woodbury core non-finite; the threaded
+    # Cholesky (core of order 420) stops in every thread and setup reports it
+    prog = W.lyapunov_local(20, 20)
+    g = prog.constraints[1].g[0]
+    g[next(iter(g))] = float("nan")
+    with pytest.raises(RuntimeError, match="positive definite"):
+        capi.host_plan(prog)
+
+
 def test_setup_rejects_bad_input(capi):
     from instances.program import Block, Constraint, SOSProgram
 
