@@ -225,7 +225,7 @@ int make_large(sos_handle* h, std::vector<LargeBlock<T>>& out, const std::vector
     TRY(alloc(h, Np * Np, &lb.scratch.B1));
     TRY(alloc(h, Np * Np, &lb.scratch.V));
     TRY(alloc(h, Np * Np, &lb.scratch.T1));
-    TRY(alloc(h, 3 * static_cast<size_t>(lb.grid), &lb.scratch.partial));  // norm, two sweep checks
+    TRY(alloc(h, large_partials_size(lb.grid, lb.N), &lb.scratch.partial));
     TRY(alloc(h, kMaxSweeps, &lb.scratch.flags));
     TRY(alloc(h, 2, &lb.scratch.bar));
     TRY(alloc(h, 1, &lb.scratch.sweeps_out));

@@ -22,58 +22,13 @@
 #include <cfloat>
 #include <cstdio>
 
+#include "dev_common.cuh"
 #include "kernels.h"
 #include "tcgen05.cuh"
 
 namespace sos {
 namespace {
 
-constexpr long long kSpinLimitCycles = 4000000000ll;  // ~2 s at 2 GHz
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Deterministic block sum; result valid in every thread.
-__device__ double block_sum(double v, double* sh) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  const int nw = (blockDim.x + 31) >> 5;
-  if (w == 0) {
-    double x = (l < nw) ? sh[l] : 0.0;
-    x = warp_sum(x);
-    if (l == 0) sh[32] = x;
-  }
-  __syncthreads();
-  return sh[32];
-}
-
-// Block maximum (inputs >= 0); result valid in every thread.
-__device__ double block_max(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  const int nw = (blockDim.x + 31) >> 5;
-  if (w == 0) {
-    double x = (l < nw) ? sh[l] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-    if (l == 0) sh[32] = x;
-  }
-  __syncthreads();
-  return sh[32];
-}
-
-template <typename T>
-__device__ __forceinline__ double d(T x) {
-  return static_cast<double>(x);
-}
 
 // ---------------------------------------------------------------------------
 // affine step
@@ -263,25 +218,6 @@ __global__ void k_rows_y(DevPlan<T> p) {
   d_rows_y(p, static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x, static_cast<int64_t>(gridDim.x) * blockDim.x);
 }
 
-// Input of the PSD projection for packed entry e of block bd:
-//   plain:    W_e = u_e + a_e u_hat_2[row(e)]
-//   weighted: W_e = u_e + z_j - s g_j      (j = low-rank column of e)
-template <typename T>
-__device__ __forceinline__ T proj_input(const DevPlan<T>& p, const BlockDesc& bd, int64_t k, bool off, double s) {
-  const int64_t e = bd.x_off + k;
-  if (bd.kind == kRaw) return p.ux[e];
-  if (bd.kind == kPlain) {
-    const int row = p.ent_row[e] & ~kEntOffBit;
-    const T a = off ? static_cast<T>(kSqrt2) : static_cast<T>(1);
-    return p.ux[e] + a * p.uh2[row];
-  }
-  const int j = bd.lr_first + static_cast<int>(k);
-  return static_cast<T>(d(p.ux[e]) + p.zlr[j] - s * p.lr_g[j]);
-}
-
-__device__ __forceinline__ int64_t packed_index(int i, int j, int N) {  // i >= j
-  return static_cast<int64_t>(j) * N - static_cast<int64_t>(j) * (j - 1) / 2 + (i - j);
-}
 
 // Round-robin (circle method) pairing: pair k of round r, for Np even.
 // q = x / d, r = x % d for 0 <= x < 2^24 without an integer division: the
@@ -810,59 +746,6 @@ __global__ void __launch_bounds__(512) k_psd_small(DevPlan<T> p, const int32_t* 
 // from the current buffer), then U = V max(diag B, 0) V^T.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* ptr) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ptr) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release_u32(unsigned* ptr, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(ptr), "r"(v) : "memory");
-}
-
-// Grid-wide barrier.  bar[0] counts arrivals (zeroed before the launch),
-// bar[1] holds the last released generation; the CTA that completes a
-// generation releases it, the others poll bar[1].  Ordering comes from the
-// atomics themselves, not from full fences: __syncthreads orders the CTA's
-// writes before thread 0's arrival, the arrival is an acquire-release
-// read-modify-write at GPU scope (so the last arriver acquires every earlier
-// arrival), the release is a store-release and the pollers load-acquire it.
-// Bounded spin: on expiry (or when another CTA already raised the error
-// word) every CTA returns false.
-__device__ bool grid_barrier(unsigned* bar, unsigned target, int32_t* err) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned gen = target / gridDim.x;
-    unsigned old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
-    int good = 1;
-    if (old == target - 1) {
-      st_release_u32(bar + 1, gen);
-    } else {
-      const long long t0 = clock64();
-      while (ld_acquire_u32(bar + 1) < gen) {
-        if (*reinterpret_cast<volatile int32_t*>(err) != 0) {
-          good = 0;
-          break;
-        }
-        if (clock64() - t0 > kSpinLimitCycles) {
-          atomicExch(err, 1);
-          good = 0;
-          break;
-        }
-      }
-    }
-    ok = good;
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-template <typename T>
-__device__ __forceinline__ T ldg_cg(const T* ptr) {
-  return __ldcg(ptr);
-}
 
 // C tile (16x16, 256 threads) of one of:
 //   mode 0: C = A B           mode 1: C = A^T B        (A, B: Np x Np, ld Np)
@@ -900,6 +783,7 @@ __global__ void __launch_bounds__(256, 1) k_psd_large(DevPlan<T> p, int bid, Lar
   __shared__ int any_rot;
   const BlockDesc bd = p.blocks[bid];
   if (!p.active[bd.inst]) return;
+  if (sizeof(TC) == 8 && sizeof(T) == 8 && tri_path(bd.N) && __ldcg(L.flags) == 1) return;  // projected already
   if (threadIdx.x == 0) any_rot = -1;  // the load phase's block_sum orders this before any use
   const double s_sm = p.st[bd.inst].s;
   const int N = bd.N, Np = N + (N & 1), H = Np / 2;
@@ -1805,7 +1689,14 @@ size_t large_smem_bytes(int N, size_t es) {
 template <typename T, typename TC>
 cudaError_t launch_psd_large(const DevPlan<T>& p, int bid, int N, const LargeScratch<TC>& ls, int grid,
                              cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(ls.bar, 0, 2 * sizeof(uint32_t), s);
+  cudaError_t e = cudaSuccess;
+  if constexpr (sizeof(T) == 8 && sizeof(TC) == 8) {
+    if (tri_path(N)) {
+      e = launch_psd_tri(p, bid, N, ls, grid, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  e = cudaMemsetAsync(ls.bar, 0, 2 * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);

@@ -79,8 +79,8 @@ struct LargeScratch {
   T* B1 = nullptr;
   T* V = nullptr;    // eigenvectors, kept across iterations (warm start)
   T* T1 = nullptr;   // GEMM temporary
-  double* partial = nullptr;   // per-CTA partials, 3 x grid (norm; sweep checks, alternating)
-  int32_t* flags = nullptr;    // unused (kept for layout)
+  double* partial = nullptr;   // large_partials_size(grid, N) doubles
+  int32_t* flags = nullptr;    // [0]: 1 if the tridiagonal path projected the block in this iteration
   uint32_t* bar = nullptr;     // grid barrier: [arrivals, released generation], zeroed before each launch
   int32_t* sweeps_out = nullptr;  // number of sweeps of the last launch
   int32_t* warm = nullptr;     // 1 if V holds the previous eigenvectors
@@ -88,6 +88,21 @@ struct LargeScratch {
 };
 
 constexpr int kMaxSweeps = 40;
+// LargeScratch::partial: kLargePartials doubles per CTA (the Jacobi kernel
+// uses three: norm and two alternating sweep checks; the tridiagonal path
+// four), then N doubles of the tridiagonal path's eigenvalue estimates
+constexpr int kLargePartials = 4;
+inline size_t large_partials_size(int grid, int N) {
+  return static_cast<size_t>(kLargePartials) * static_cast<size_t>(grid) + static_cast<size_t>(N) + 1;
+}
+
+// FP64 large blocks of kTriMinN <= N <= kTriMaxN are projected through a
+// tridiagonal reduction (csrc/eigproj.cu); the grid Jacobi kernel launched
+// after it does nothing unless that path left the block to it (flags[0] = 0).
+constexpr int kTriMinN = 33, kTriMaxN = 232;
+__host__ __device__ constexpr bool tri_path(int N) { return N >= kTriMinN && N <= kTriMaxN; }
+cudaError_t launch_psd_tri(const DevPlan<double>& p, int bid, int N, const LargeScratch<double>& L, int grid,
+                           cudaStream_t s);
 
 // Scratch of the Newton-Schulz projection (tensor cores) of one large block.
 struct NsScratch {
