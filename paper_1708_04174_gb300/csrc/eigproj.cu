@@ -46,10 +46,11 @@
 namespace sos {
 namespace {
 
-constexpr int kTriThreads = 1024;  // reduction CTA
+constexpr int kTriThreads = 256;   // reduction CTA (8 warps: little redundant per-warp work)
 constexpr int kVecThreads = 256;   // one CTA per eigenvector
 constexpr int kRecThreads = 128;   // reconstruction CTAs
 constexpr int kTriSlots = (kTriMaxN + 31) / 32;  // per-lane register slots of a length-N vector
+constexpr int kTriRows = 256;                     // p vectors of the reduction (float4 chunks of two slots)
 
 // Output of the reduction inside LargeScratch::B0 (as floats):
 //   U[k * N + j]   entry j (>= k + 2) of reflector k; its entry k + 1 is 1
@@ -85,14 +86,20 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 //   beta = -sign(alpha) |A[k+1.., k]|,  tau = (beta - alpha) / beta,
 //   v = A[k+1.., k] / (alpha - beta),   p = tau A22 v,
 //   w = p - (tau / 2)(p^T v) v,         A22 <- A22 - v w^T - w v^T,
-// with A22 the trailing block A[k+1.., k+1..].  Only the lower triangle is
-// kept (row-major, odd leading dimension, so that a row and a column of it
-// are both read without shared-memory bank conflicts).  Warp w owns the rows
-// r = w (mod 32) of the product and of the update, its lanes the columns
-// c = lane (mod 32); every warp forms the reflector itself from the column
-// (held in registers), and the update also sums the squares of the next
-// column, so a step needs two barriers.
+// with A22 the trailing block A[k+1.., k+1..].
+//
+// Layout: the whole symmetric matrix, index-reversed, B[i][j] = A[N-1-i][N-1-j],
+// rows padded to a multiple of 4 floats.  The trailing block of step k is
+// then the leading m x m block of B (m = N - 1 - k) and every access is an
+// aligned float4 along a row: lane l holds columns 4 l + 128 s .. + 3
+// (s = 0, 1), warp w owns the row chunks q = w + 8 t (rows 4 q .. 4 q + 3,
+// whose entries of a chunked vector sit in lane q mod 32).  The update of step k and the
+// product A22 v of step k + 1 are one pass over each owned row (the next
+// reflector comes from row m - 1 of the updated block, which every warp
+// forms for itself), so a step reads and writes each element once and needs
+// one barrier.
 // ---------------------------------------------------------------------------
+
 // Sums of eight per-lane values over the warp, spread out: on return lane l
 // holds the total of value (l >> 2) & 7 (nine shuffles instead of forty).
 __device__ __forceinline__ float warp_sum8(float (&a)[8], int lane) {
@@ -115,156 +122,287 @@ __device__ __forceinline__ float warp_sum8(float (&a)[8], int lane) {
   return x;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kTriThreads, 1) k_tri_reduce(DevPlan<T> p, int bid, LargeScratch<double> L) {
-  static_assert(kTriSlots == 8, "the row reduction handles eight rows per warp");
-  extern __shared__ __align__(16) float tsm[];
-  __shared__ double redd[40];
-  __shared__ float sg_part[32];
-  const BlockDesc bd = p.blocks[bid];
-  if (!p.active[bd.inst]) return;
-  const int N = bd.N, LD = N | 1;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float* A = tsm;
-  float* pp = A + static_cast<size_t>(N) * LD;
-  const TriOut out = tri_out(L.B0, N);
-  const double s_sm = p.st[bd.inst].s;
+__device__ __forceinline__ float f4get(const float4& a, int c) { return c == 0 ? a.x : (c == 1 ? a.y : (c == 2 ? a.z : a.w)); }
 
-  // the lower triangle in FP32 (column j by warp j mod 32, coalesced over the
-  // packed column), |W|_F in FP64, then the scaling by 1 / |W|_F
-  double nrm2 = 0.0;
-  for (int j = warp; j < N; j += 32) {
-    const int64_t base = packed_index(j, j, N);
-#pragma unroll 4
-    for (int i = j + lane; i < N; i += 32) {
-      const double w = d(proj_input(p, bd, base + (i - j), i != j, s_sm));
-      nrm2 += w * w;  // packed entries carry sqrt(2): w^2 counts both halves
-      A[i * LD + j] = static_cast<float>(i == j ? w : w * 0.70710678118654752440);
+// Entry i of a vector held as float4 chunks (lane l: entries 4 l + 128 s ..).
+__device__ __forceinline__ float chunk_entry(const float4 (&v)[2], int i) {
+  const int src = (i >> 2) & 31;
+  const float4 a = (i >> 7) ? v[1] : v[0];
+  return __shfl_sync(0xffffffffu, f4get(a, i & 3), src);
+}
+
+// Reflector from x (entries 0 .. mk-1 in chunks; the pivot alpha is entry
+// mk - 1): v (pivot entry 1, zero from mk on), tau and beta; the same
+// arithmetic in every warp.
+__device__ __forceinline__ void make_reflector(const float4 (&x)[2], int mk, int lane, float4 (&v)[2], float& tau,
+                                               float& beta) {
+  float s2 = 0.f;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int j0 = 128 * s + 4 * lane;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float e = f4get(x[s], c);
+      if (j0 + c < mk - 1) s2 = fmaf(e, e, s2);
     }
   }
-  nrm2 = block_sum(nrm2, redd);
-  {
-    const float scale = nrm2 > 0.0 ? static_cast<float>(1.0 / sqrt(nrm2)) : 1.f;
-    float sg = 0.f;
-    for (int j = warp; j < N; j += 32)
-      for (int i = j + lane; i < N; i += 32) {
-        const float x = A[i * LD + j] * scale;
-        A[i * LD + j] = x;
-        if (j == 0 && i >= 2) sg = fmaf(x, x, sg);  // squares of column 0 below the subdiagonal
+  s2 = warp_sum_f(s2);
+  const float alpha = chunk_entry(x, mk - 1);
+  tau = 0.f;
+  beta = alpha;
+  float sc = 0.f;
+  if (s2 > 0.f) {
+    beta = -copysignf(sqrtf(fmaf(alpha, alpha, s2)), alpha);
+    tau = (beta - alpha) / beta;
+    sc = 1.f / (alpha - beta);
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int j0 = 128 * s + 4 * lane;
+    float e[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + c;
+      e[c] = j < mk - 1 ? f4get(x[s], c) * sc : (j == mk - 1 ? 1.f : 0.f);
+    }
+    v[s] = make_float4(e[0], e[1], e[2], e[3]);
+  }
+}
+
+// One pass over the rows i < nrows owned by this warp (row chunks q = warp
+// + 8 t, rows 4 q .. 4 q + 3): a = a - v_i w - w_i v on the columns j < ncols,
+// then p_i = tau a v' (v' zero from nrows on), written to pn[i].  All eight
+// rows of two chunks are loaded before any is used; rows and columns past
+// the block are read at clamped addresses and neither written nor counted.
+// SL: float4 slots per lane (columns 4 lane + 128 s), 1 when ncols <= 128.
+template <int SL>
+__device__ __forceinline__ void fused_rows(float* B, int LD, int N, int nrows, int ncols, int warp, int lane,
+                                           const float4 (&v)[2], const float4 (&w)[2], const float4 (&vn)[2],
+                                           float tau, float* pn) {
+#pragma unroll
+  for (int t0 = 0; t0 < 8; t0 += 2) {
+    if (4 * (warp + 8 * t0) >= nrows) break;  // warp-uniform: later chunks are further out
+    float vi[8], wi[8];
+    int row[8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int t = t0 + h, src = warp + 8 * (t & 3);
+      const float4 vq = t < 4 ? v[0] : v[1], wq = t < 4 ? w[0] : w[1];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        vi[4 * h + c] = __shfl_sync(0xffffffffu, f4get(vq, c), src);
+        wi[4 * h + c] = __shfl_sync(0xffffffffu, f4get(wq, c), src);
+        row[4 * h + c] = 4 * (warp + 8 * t) + c;
       }
-    sg = warp_sum_f(sg);
-    if (lane == 0) sg_part[warp] = sg;
+    }
+    float4 a[8][SL];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int s = 0; s < SL; ++s) {
+        const int i = min(row[r], N - 1), j0 = min(128 * s + 4 * lane, LD - 4);
+        a[r][s] = *reinterpret_cast<const float4*>(B + i * LD + j0);
+      }
+    float acc[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      acc[r] = 0.f;
+      const bool rok = row[r] < nrows;
+#pragma unroll
+      for (int s = 0; s < SL; ++s) {
+        const int j0 = 128 * s + 4 * lane;
+        float4 t = a[r][s];
+        t.x = fmaf(-vi[r], w[s].x, fmaf(-wi[r], v[s].x, t.x));
+        t.y = fmaf(-vi[r], w[s].y, fmaf(-wi[r], v[s].y, t.y));
+        t.z = fmaf(-vi[r], w[s].z, fmaf(-wi[r], v[s].z, t.z));
+        t.w = fmaf(-vi[r], w[s].w, fmaf(-wi[r], v[s].w, t.w));
+        if (rok && j0 < ncols) *reinterpret_cast<float4*>(B + row[r] * LD + j0) = t;
+        const float d4 = fmaf(t.x, vn[s].x, fmaf(t.y, vn[s].y, fmaf(t.z, vn[s].z, t.w * vn[s].w)));
+        acc[r] += (j0 < ncols) ? d4 : 0.f;
+      }
+    }
+    const float tot = warp_sum8(acc, lane);
+    const int idx = (lane >> 2) & 7;
+    const int i = 4 * (warp + 8 * (t0 + (idx >> 2))) + (idx & 3);
+    if ((lane & 3) == 0 && i < nrows) pn[i] = tau * tot;
+  }
+}
+
+constexpr int kGatherCtas = 64;
+
+// W of the block into the reduction's layout (index-reversed, both
+// triangles, FP32, unscaled) in L.T1, and per-CTA partial sums of |W|_F^2
+// (FP64) in L.partial: many CTAs do the dependent gathers of the
+// projection input, so the one-CTA reduction reads a dense array.
+template <typename T>
+__global__ void __launch_bounds__(256) k_tri_gather(DevPlan<T> p, int bid, LargeScratch<double> L) {
+  __shared__ double red[40];
+  const BlockDesc bd = p.blocks[bid];
+  if (!p.active[bd.inst]) return;
+  const int N = bd.N, LD = (N + 3) & ~3;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), nwg = gridDim.x * (blockDim.x / 32);
+  float* Bg = reinterpret_cast<float*>(L.T1);
+  const double s_sm = p.st[bd.inst].s;
+  double nrm2 = 0.0;
+  for (int c = gw; c < N; c += nwg) {
+    const int64_t base = packed_index(c, c, N);
+#pragma unroll 4
+    for (int r = c + lane; r < N; r += 32) {
+      const double w = d(proj_input(p, bd, base + (r - c), r != c, s_sm));
+      nrm2 += w * w;  // packed entries carry sqrt(2): w^2 counts both halves
+      const float a = static_cast<float>(r == c ? w : w * 0.70710678118654752440);
+      Bg[(N - 1 - r) * LD + (N - 1 - c)] = a;
+      Bg[(N - 1 - c) * LD + (N - 1 - r)] = a;
+    }
+  }
+  if (blockIdx.x == 0)
+    for (int q = threadIdx.x; q < N * (LD - N); q += blockDim.x) Bg[(q / (LD - N)) * LD + N + q % (LD - N)] = 0.f;
+  nrm2 = block_sum(nrm2, red);
+  if (threadIdx.x == 0) L.partial[blockIdx.x] = nrm2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTriThreads, 1) k_tri_reduce(DevPlan<T> p, int bid, LargeScratch<double> L) {
+  extern __shared__ __align__(16) float tsm[];
+  __shared__ double redd[40];
+  const BlockDesc bd = p.blocks[bid];
+  if (!p.active[bd.inst]) return;
+  const int N = bd.N, LD = (N + 3) & ~3;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* B = tsm;
+  float* pbuf = B + static_cast<size_t>(N) * LD;  // two alternating copies of p (kTriRows each)
+  const TriOut out = tri_out(L.B0, N);
+
+  // W (dense FP32 copy from k_tri_gather), scaled by 1 / |W|_F
+  {
+    double nrm2 = 0.0;
+    for (int c = tid; c < kGatherCtas; c += kTriThreads) nrm2 += __ldcg(L.partial + c);  // same order everywhere
+    nrm2 = block_sum(nrm2, redd);
+    const float scale = nrm2 > 0.0 ? static_cast<float>(1.0 / sqrt(nrm2)) : 1.f;
+    const float4* src = reinterpret_cast<const float4*>(L.T1);
+    float4* dst = reinterpret_cast<float4*>(B);
+#pragma unroll 4
+    for (int q = tid; q < N * LD / 4; q += kTriThreads) {
+      float4 a = __ldcg(src + q);
+      a.x *= scale;
+      a.y *= scale;
+      a.z *= scale;
+      a.w *= scale;
+      dst[q] = a;
+    }
+    for (int q = tid; q < 2 * kTriRows; q += kTriThreads) pbuf[q] = 0.f;
+  }
+  __syncthreads();
+
+  // reflector 0 from column 0 of A: row N - 1 of B (its entries 0 .. N-2)
+  float4 vk[2], wk[2], vn[2];
+  float tauk, beta;
+  {
+    float4 x[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int j0 = 128 * s + 4 * lane;
+      x[s] = j0 < LD ? *reinterpret_cast<const float4*>(B + (N - 1) * LD + j0) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    make_reflector(x, N - 1, lane, vk, tauk, beta);
+    if (tid == 0) {
+      out.d[0] = B[(N - 1) * LD + N - 1];
+      out.e[0] = beta;
+      out.tau[0] = tauk;
+    }
+  }
+  // p = tau A22 v for step 0 (no update before it)
+  {
+    const float4 zero[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    fused_rows<2>(B, LD, N, N - 1, N - 1, warp, lane, vk, zero, vk, tauk, pbuf);
   }
   __syncthreads();
 
   for (int k = 0; k < N - 2; ++k) {
-    const int m = N - k - 1;
-    float* A22 = A + (k + 1) * LD + (k + 1);  // A22[r * LD + c], r >= c
-    const float* col = A + (k + 1) * LD + k;  // col[r * LD] = A[k+1+r][k]
-    // the reflector (the same arithmetic in every warp)
-    const float s2 = warp_sum_f(sg_part[lane]);
-    const float alpha = col[0];
-    float tau = 0.f, beta = alpha, sc = 0.f;
-    if (s2 > 0.f) {
-      beta = -copysignf(sqrtf(fmaf(alpha, alpha, s2)), alpha);
-      tau = (beta - alpha) / beta;
-      sc = 1.f / (alpha - beta);
-    }
-    if (tid == 0) {
-      out.d[k] = A[k * LD + k];
-      out.e[k] = beta;
-      out.tau[k] = tau;
-    }
-    if (tau == 0.f) {  // H_k = I: only the squares of the next column
-      float sg = 0.f;
-      for (int r = 2 + tid; r < m; r += kTriThreads) sg = fmaf(A22[r * LD], A22[r * LD], sg);
-      __syncthreads();  // every warp has read sg_part
-      sg = warp_sum_f(sg);
-      if (lane == 0) sg_part[warp] = sg;
-      __syncthreads();
-      continue;
-    }
-    float vr[kTriSlots];
-#pragma unroll
-    for (int q = 0; q < kTriSlots; ++q) {
-      const int c = lane + 32 * q;
-      vr[q] = c == 0 ? 1.f : (c < m ? col[c * LD] * sc : 0.f);
-    }
-    if (warp < kTriSlots) {  // reflector k for the back-transformation: entries k + 2 ..
-      const int c = lane + 32 * warp;
-      if (c >= 1 && c < m) out.U[static_cast<int64_t>(k) * N + k + 1 + c] = vr[warp];
-    }
-    // p = tau A22 v for the rows r = warp + 32 i; slots of 32 columns wholly
-    // on or below the diagonal read a row, wholly above it a column
+    const int m = N - 1 - k;        // trailing block of step k: B[0..m-1][0..m-1]
+    const float* pc = pbuf + (k & 1) * kTriRows;
+    float* pn = pbuf + ((k + 1) & 1) * kTriRows;
+    // w_k = p - (tau / 2)(p^T v) v, every warp for itself
     {
-      float acc[kTriSlots];
+      float dot = 0.f;
+      float4 pk[2];
 #pragma unroll
-      for (int i = 0; i < kTriSlots; ++i) {
-        acc[i] = 0.f;
-        const int r = warp + 32 * i;
-        if (r < m) {
-#pragma unroll
-          for (int q = 0; q < kTriSlots; ++q) {
-            const int c = lane + 32 * q;
-            if (32 * q + 31 <= r) {
-              acc[i] = fmaf(A22[r * LD + c], vr[q], acc[i]);
-            } else if (32 * q > r) {
-              if (32 * q < m && c < m) acc[i] = fmaf(A22[c * LD + r], vr[q], acc[i]);
-            } else if (c < m) {
-              acc[i] = fmaf(c <= r ? A22[r * LD + c] : A22[c * LD + r], vr[q], acc[i]);
-            }
-          }
-        }
+      for (int s = 0; s < 2; ++s) {
+        const int j0 = 128 * s + 4 * lane;
+        pk[s] = j0 < kTriRows ? *reinterpret_cast<const float4*>(pc + j0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        dot = fmaf(pk[s].x, vk[s].x, fmaf(pk[s].y, vk[s].y, fmaf(pk[s].z, vk[s].z, fmaf(pk[s].w, vk[s].w, dot))));
       }
-      const float tot = warp_sum8(acc, lane);
-      const int r = warp + 32 * ((lane >> 2) & 7);
-      if ((lane & 3) == 0 && r < m) pp[r] = tau * tot;
-    }
-    __syncthreads();
-    // w = p - (tau / 2)(p^T v) v (every warp forms p^T v itself)
-    float wr[kTriSlots];
-    float pv = 0.f;
+      const float K = -0.5f * tauk * warp_sum_f(dot);
 #pragma unroll
-    for (int q = 0; q < kTriSlots; ++q) {
-      const int c = lane + 32 * q;
-      wr[q] = c < m ? pp[c] : 0.f;
-      pv = fmaf(wr[q], vr[q], pv);
-    }
-    const float K = -0.5f * tau * warp_sum_f(pv);
+      for (int s = 0; s < 2; ++s) {
+        const int j0 = 128 * s + 4 * lane;
+        float e[4];
 #pragma unroll
-    for (int q = 0; q < kTriSlots; ++q) wr[q] = fmaf(K, vr[q], wr[q]);
-    // A22 <- A22 - v w^T - w v^T on the lower triangle; squares of its column 0 (the next reflector's)
-    float sg = 0.f;
+        for (int c = 0; c < 4; ++c) e[c] = (j0 + c < m) ? fmaf(K, f4get(vk[s], c), f4get(pk[s], c)) : 0.f;
+        wk[s] = make_float4(e[0], e[1], e[2], e[3]);
+      }
+      if (tauk == 0.f) {  // H_k = I
 #pragma unroll
-    for (int i = 0; i < kTriSlots; ++i) {
-      const int r = warp + 32 * i;
-      if (r < m) {
-        const float vrr = __shfl_sync(0xffffffffu, vr[i], warp), wrr = __shfl_sync(0xffffffffu, wr[i], warp);
-#pragma unroll
-        for (int q = 0; q < kTriSlots; ++q) {
-          const int c = lane + 32 * q;
-          if (32 * q > r) continue;
-          if (32 * q + 31 <= r || c <= r) {
-            float* a = A22 + r * LD + c;
-            const float x = fmaf(-vrr, wr[q], fmaf(-wrr, vr[q], *a));
-            *a = x;
-            if (q == 0 && c == 0 && r >= 2) sg = fmaf(x, x, sg);
-          }
-        }
+        for (int s = 0; s < 2; ++s) wk[s] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
-    sg = warp_sum_f(sg);
-    if (lane == 0) sg_part[warp] = sg;
+    // row m - 1 of the updated block: the diagonal entry d_{k+1} and the next
+    // reflector's column (entries 0 .. m-2)
+    float taun = 0.f;
+    {
+      const float vm = chunk_entry(vk, m - 1), wm = chunk_entry(wk, m - 1);
+      float4 y[2];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int j0 = 128 * s + 4 * lane;
+        float4 t = j0 < LD ? *reinterpret_cast<const float4*>(B + (m - 1) * LD + j0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        t.x = fmaf(-vm, wk[s].x, fmaf(-wm, vk[s].x, t.x));
+        t.y = fmaf(-vm, wk[s].y, fmaf(-wm, vk[s].y, t.y));
+        t.z = fmaf(-vm, wk[s].z, fmaf(-wm, vk[s].z, t.z));
+        t.w = fmaf(-vm, wk[s].w, fmaf(-wm, vk[s].w, t.w));
+        y[s] = t;
+      }
+      const float dn = chunk_entry(y, m - 1);
+      if (k + 1 <= N - 3) {
+        make_reflector(y, m - 1, lane, vn, taun, beta);
+        if (tid == 0) {
+          out.d[k + 1] = dn;
+          out.e[k + 1] = beta;
+          out.tau[k + 1] = taun;
+        }
+      } else {  // the last 2 x 2 block: no reflector
+        const float e_last = chunk_entry(y, 0);
+        if (tid == 0) {
+          out.d[k + 1] = dn;
+          out.e[k + 1] = e_last;
+          out.tau[k + 1] = 0.f;
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) vn[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    // reflector k for the back-transformation (A order: entries k + 2 .. N-1
+    // = B entries 0 .. m - 2, reversed)
+    if (warp < 2) {
+      const int j0 = 128 * warp + 4 * lane;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = j0 + c;
+        if (j < m - 1) out.U[static_cast<int64_t>(k) * N + (N - 1 - j)] = f4get(vk[warp], c);
+      }
+    }
+    // own rows i < m - 1: update with (v_k, w_k), then the product with v_{k+1}
+    if (m > 129)
+      fused_rows<2>(B, LD, N, m - 1, m, warp, lane, vk, wk, vn, taun, pn);
+    else
+      fused_rows<1>(B, LD, N, m - 1, m, warp, lane, vk, wk, vn, taun, pn);
     __syncthreads();
+#pragma unroll
+    for (int s = 0; s < 2; ++s) vk[s] = vn[s];
+    tauk = taun;
   }
-  if (tid == 0) {
-    out.d[N - 2] = A[(N - 2) * LD + N - 2];
-    out.d[N - 1] = A[(N - 1) * LD + N - 1];
-    out.e[N - 2] = A[(N - 1) * LD + N - 2];
-    out.e[N - 1] = 0.f;
-    out.tau[N - 2] = 0.f;
-    out.tau[N - 1] = 0.f;
-  }
+  if (tid == 0) out.d[N - 1] = B[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -910,7 +1048,7 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
   }
 }
 
-size_t tri_reduce_smem(int N) { return sizeof(float) * (static_cast<size_t>(N) * (N | 1) + kTriMaxN); }
+size_t tri_reduce_smem(int N) { return sizeof(float) * (static_cast<size_t>(N) * ((N + 3) & ~3) + 2 * kTriRows); }
 
 size_t tri_vectors_smem(int N) {
   return (sizeof(float) * (4 + 5 * (kVecThreads / 32)) + sizeof(int) * (kVecThreads / 32)) * static_cast<size_t>(N);
@@ -923,6 +1061,9 @@ cudaError_t launch_psd_tri(const DevPlan<double>& p, int bid, int N, const Large
   const size_t sm1 = tri_reduce_smem(N), sm2 = tri_vectors_smem(N);
   cudaError_t e = cudaFuncSetAttribute(k_tri_reduce<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm1));
+  if (e != cudaSuccess) return e;
+  k_tri_gather<double><<<kGatherCtas, 256, 0, s>>>(p, bid, L);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_tri_reduce<double><<<1, kTriThreads, sm1, s>>>(p, bid, L);
   e = cudaGetLastError();
