@@ -39,6 +39,10 @@ SOLVED, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE, MAX_ITER, NUMERICAL = 1, 2, 3, 4, 5
 
 def proj_psd(S: np.ndarray) -> np.ndarray:
     """Projection of a symmetric matrix onto S_+: V max(Lambda, 0) V^T."""
+    if not np.all(np.isfinite(S)):
+        # IEEE propagation: a non-finite entry makes the whole projection
+        # NaN, and the next residual check reports the iterate non-finite
+        return np.full_like(S, np.nan)
     lam, V = np.linalg.eigh(S)
     return (V * np.maximum(lam, 0.0)) @ V.T
 
@@ -77,8 +81,10 @@ class HSDE:
         """(I + A A^T)^{-1} r = (P + A_L A_L^T)^{-1} r via Woodbury (Appendix)."""
         x = r / self.P
         y = self.AL.T @ x
-        z = sla.solve_triangular(self.L, y, lower=True)
-        z = sla.solve_triangular(self.L.T, z, lower=False)
+        # check_finite=False: a non-finite iterate propagates (IEEE) to the
+        # residual check, which classifies it, instead of raising here
+        z = sla.solve_triangular(self.L, y, lower=True, check_finite=False)
+        z = sla.solve_triangular(self.L.T, z, lower=False, check_finite=False)
         return x - (self.AL @ z) / self.P
 
     def solve_M(self, w1: np.ndarray, w2: np.ndarray):

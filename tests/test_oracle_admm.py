@@ -217,3 +217,17 @@ def test_binary_quartic_form_reduced_basis(seed):
     th = np.linspace(0.0, np.pi, 2000001)  # p is even: half the circle suffices
     gmin = np.min(sum(c * np.cos(th) ** e[0] * np.sin(th) ** e[1] for e, c in p.items()))
     assert abs(-r.res["pobj"] - gmin) <= 1e-6 * max(1.0, abs(gmin))
+
+
+def test_non_finite_start_is_a_numerical_failure():
+    # IEEE propagation: a NaN in the iterate reaches every component through
+    # the affine step and the projections, and the first residual check
+    # classifies the run as a numerical failure (not a solve, not a raise)
+    cd = conic.build(W.quartic_pop(4, 0))
+    hs = admm.HSDE(cd)
+    u, v = hs.start()
+    u = u.copy()
+    u[0] = np.nan
+    r = admm.solve(cd, 1e-8, 50, k_check=10, u0=u, v0=v)
+    assert r.status == admm.NUMERICAL and r.iters == 10
+    assert np.isnan(admm.proj_psd(np.array([[1.0, np.nan], [np.nan, 1.0]]))).all()
