@@ -41,6 +41,42 @@ WORKLOADS = {
 }
 
 
+METRIC = "ADMM iterations/s (one iteration = affine step + PSD projections + update)"
+
+
+def alu_peaks(sm_mhz: float):
+    """ALU peaks from unit counts and the SM clock (GFLOP/s): 152 SMs, each
+    with 2 FP64 and 128 FP32 fused multiply-adds per cycle (a multiply-add
+    counts as two flops).  An FMA-loop probe on GB300 measured 2.00 FP64 and
+    123.6 FP32 multiply-adds per cycle per SM at 2070 MHz."""
+    ghz = sm_mhz / 1e3
+    return {"fp64": 152 * 2 * 2 * ghz, "fp32": 152 * 128 * 2 * ghz}
+
+
+def source_hash(*paths) -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for q in paths:
+        with open(os.path.join(ROOT, q), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of a kernel from the ncu capture recorded in
+    profiles/traffic.json, if the kernel's source is unchanged since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    e = rec.get(kernel, {}).get(workload)
+    if not e or e.get("source_sha256") != source_hash(*e.get("sources", [])):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
 def make_program(name):
     from instances import workloads as W
 
@@ -178,7 +214,7 @@ def reference_arm(args, rank):
     prog = make_program(args.workload)
     k, dt = run_oracle_iters(prog, seconds=max(2.0, 8.0 * (args.steps + args.warmup) / 20), max_iters=10**9)
     ips = k / dt
-    line = {"impl": "reference", "metric": "ADMM iterations/s (plain FP64)", "value": ips, "unit": "iter/s",
+    line = {"impl": "reference", "metric": METRIC, "value": ips, "unit": "iter/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / ips,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"]},
@@ -332,15 +368,13 @@ def batched_arm(args):
 
                 Ns.append(blk.size(prog.n))
     flops = sum(9.0 * N ** 3 for N in Ns)
-    fp32_peak = 69700.0
+    fp32_peak = alu_peaks(2070.0)["fp32"]
     roof = {"kernel": "k_psd_small<double,float> (FP32 Jacobi + compensated refinement, one CTA per block)",
             "bound": "alu", "achieved": flops / (stage_ms["psd_small"] / 1e3) / 1e9, "peak": fp32_peak,
             "unit": "GFLOP/s", "frac": flops / (stage_ms["psd_small"] / 1e3) / 1e9 / fp32_peak,
-            # DRAM bytes of the stage's five class launches of one iteration (ncu
-            # capture summarised in profiles/lyapunov_batch4096_launches_and_kernels.md)
-            "traffic": 6534400 + 18487040 + 12453888 + (28714240 + 616448) + (68750848 + 19795456),
-            "note": "algorithmic flops 9 N^3 per block over all 8192 blocks; peak = FMA-loop FP32 rate measured "
-                    "on GB300", "stage_ms": stage_ms,
+            "traffic": recorded_traffic("k_psd_small", "lyapunov_batch4096"),
+            "note": "algorithmic flops 9 N^3 per block over all 8192 blocks; peak = FP32 multiply-add rate from "
+                    "unit counts at 2070 MHz", "stage_ms": stage_ms,
             "stage_bytes": {"affine": s.stage_bytes(0), "psd_small": s.stage_bytes(1)}}
     tuning = s.tuning()
     launches = s.launches_per_iteration()
@@ -608,12 +642,14 @@ def main():
     ips = aggregate_rate(args.steps, world, total_ms / 1e3)
 
     # dominant kernel: a fresh handle replays the timed iteration range
-    # (warm-up, then the steps) stage by stage (stages 0, 1, 2 in order make
-    # one iteration), each stage bracketed by events on that handle's stream
-    # and L2 flushed before each iteration as in the timed region; the
-    # warm-started Jacobi needs more sweeps early in a solve than late, so
-    # the launches timed here are the same iterations as the timed steps
-    stage_names = ((0, "affine"), (1, "psd_small"), (2, "psd_large"))
+    # (warm-up, then the steps) kernel group by kernel group (stages 0, 1 and
+    # 10..14 in order make one iteration), each bracketed by events on that
+    # handle's stream and L2 flushed before each iteration as in the timed
+    # region.  In the timed steps the small-block projections run on a side
+    # stream beside the large-block ones, so a step is affine + max(small,
+    # large); the replay is trusted only if that sum is within 10% of it.
+    stage_names = ((0, "affine"), (1, "psd_small"), (10, "tri_gather"), (11, "tri_reduce"), (12, "tri_vectors"),
+                   (13, "tri_recon"), (14, "psd_large_jacobi"))
     sk = capi.Solver(prog, precision=prec, k_check=10)
     sk.iterate(args.warmup)
     sk.sync()
@@ -633,39 +669,65 @@ def main():
     sk.sync()
     sk.close()
     stage_ms = {name: float(np.mean([a.elapsed_time(b) for a, b in evs[name]])) for _, name in stage_names}
+    large_ms = sum(stage_ms[k] for k in ("tri_gather", "tri_reduce", "tri_vectors", "tri_recon", "psd_large_jacobi"))
+    replay_ms = stage_ms["affine"] + max(stage_ms["psd_small"], large_ms)
+    step_ms = total_ms / args.steps
+    consistent = abs(replay_ms - step_ms) <= 0.1 * step_ms
 
     d = solver.dims[0]
-    from instances import workloads as W  # noqa: F401
-    blocks = []
-    for con in prog.constraints:
-        for blk in con.blocks:
-            from math import comb
-
-            blocks.append(blk.size(prog.n))
-    big = [N for N in blocks if N > (96 if prec == capi.PREC_FP64 else 160)]
-    pk, pk_kind = peaks()
-    if big and stage_ms["psd_large"] >= stage_ms["psd_small"]:
+    blocks = [blk.size(prog.n) for con in prog.constraints for blk in con.blocks]
+    clk_sum = clk.summary(local)
+    sm_mhz = (clk_sum or {}).get("sm_max_mhz") or 2070.0
+    alu = alu_peaks(sm_mhz)
+    big = [N for N in blocks if 33 <= N <= 232] if prec == capi.PREC_FP64 else []
+    note_tail = (f"; kernel times from a replay of the timed iterations; replay affine + max(small, large) = "
+                 f"{replay_ms:.3f} ms against {step_ms:.3f} ms per step"
+                 + ("" if consistent else " (more than 10% apart: achieved and frac withheld)"))
+    if big:
+        # The dominant unit is the large-block projection: four kernels in a
+        # row on one stream (gather, FP32 tridiagonal reduction, FP32
+        # eigenvectors, FP64 refinement and reconstruction), ~90% of a step.
+        # Algorithmic work: 9 N^3 flops, the count of a dense symmetric
+        # eigendecomposition plus the reconstruction V max(L, 0) V^T (the
+        # figure the grid Jacobi kernel was measured against before), bound
+        # by the GPU's FP64 multiply-add rate.
+        proj_ms = sum(stage_ms[k] for k in ("tri_gather", "tri_reduce", "tri_vectors", "tri_recon"))
         flops = sum(9.0 * N ** 3 for N in big)
-        dom_ms = stage_ms["psd_large"]
-        fp64_peak = 1190.0 if prec == capi.PREC_FP64 else 69700.0
-        # DRAM bytes of one launch (read + write) from the ncu capture of the
-        # current kernel, summarised in profiles/k_psd_large_fp64_ball_pop_n20.md
-        traffic = 482048 + 476928 if prec == capi.PREC_FP64 and args.workload == "ball_pop_n20" else None
-        roof = {"kernel": "k_psd_large (grid Jacobi eigen-projection)", "bound": "alu",
-                "achieved": flops / (dom_ms / 1e3) / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
-                "frac": flops / (dom_ms / 1e3) / 1e9 / fp64_peak, "traffic": traffic,
-                "note": f"algorithmic flops 9 N^3 per N x N eigen-projection (N={big}); peak = FMA-loop "
-                        f"{'FP64' if prec == capi.PREC_FP64 else 'FP32'} rate measured on GB300"}
+        achieved = flops / (proj_ms / 1e3) / 1e9
+        # per kernel: the reduction is one CTA, so its own ceiling is one SM's
+        # FP32 rate (4/3 N^3 flops); the refinement and reconstruction run on
+        # every SM (at least 7 N^3 FP64 flops: V^T V, W V, V^T W V lower half,
+        # V M, V M V^T lower half, plus 2 N^3 per Newton-Schulz or Newton pass)
+        per = {"k_tri_reduce": {"ms": stage_ms["tri_reduce"], "flops": sum(4.0 / 3.0 * N ** 3 for N in big),
+                                "peak": alu["fp32"] / 152, "peak_scope": "one SM, FP32 (the kernel is one CTA)"},
+               "k_tri_recon": {"ms": stage_ms["tri_recon"], "flops": sum(7.0 * N ** 3 for N in big),
+                               "peak": alu["fp64"], "peak_scope": "all SMs, FP64"},
+               "k_tri_vectors": {"ms": stage_ms["tri_vectors"], "flops": None, "peak": None,
+                                 "peak_scope": "latency bound: bisection and inverse iteration, O(N^2) per eigenvalue"},
+               "k_tri_gather": {"ms": stage_ms["tri_gather"], "flops": None, "peak": None, "peak_scope": "copy"}}
+        for v in per.values():
+            v["achieved_gflops"] = v["flops"] / (v["ms"] / 1e3) / 1e9 if v["flops"] else None
+            v["frac"] = v["achieved_gflops"] / v["peak"] if v["flops"] else None
+        roof = {"kernel": "large-block FP64 projection (k_tri_gather, k_tri_reduce, k_tri_vectors, k_tri_recon)",
+                "bound": "alu", "achieved": achieved if consistent else None, "peak": alu["fp64"],
+                "unit": "GFLOP/s", "frac": achieved / alu["fp64"] if consistent else None,
+                "traffic": recorded_traffic("large_projection_fp64", args.workload),
+                "work_flops": flops, "ms_per_launch": proj_ms, "kernels": per,
+                "note": f"peak = FP64 multiply-add rate from unit counts and the SM clock ({sm_mhz:.0f} MHz)"
+                        + note_tail,
+                "stage_ms": stage_ms}
     else:
-        small = [N for N in blocks if N not in big]
-        flops = sum(9.0 * N ** 3 for N in small)
-        dom_ms = stage_ms["psd_small"]
-        peak = 1190.0 if prec == capi.PREC_FP64 else 69700.0
-        roof = {"kernel": "k_psd_small (shared-memory Jacobi eigen-projection)", "bound": "alu",
-                "achieved": flops / (dom_ms / 1e3) / 1e9, "peak": peak, "unit": "GFLOP/s",
-                "frac": flops / (dom_ms / 1e3) / 1e9 / peak, "traffic": None,
-                "note": "algorithmic flops 9 N^3 per block; peak = FMA-loop rate measured on GB300"}
-    roof["stage_ms"] = stage_ms
+        flops = sum(9.0 * N ** 3 for N in blocks)
+        dom_ms = stage_ms["psd_small"] if stage_ms["psd_small"] >= large_ms else large_ms
+        peak = alu["fp64"] if prec == capi.PREC_FP64 else alu["fp32"]
+        prec_name = "FP64" if prec == capi.PREC_FP64 else "FP32"
+        achieved = flops / (dom_ms / 1e3) / 1e9
+        roof = {"kernel": "PSD projection (Jacobi kernels)", "bound": "alu",
+                "achieved": achieved if consistent else None, "peak": peak, "unit": "GFLOP/s",
+                "frac": achieved / peak if consistent else None, "traffic": None,
+                "note": f"peak = {prec_name} multiply-add rate from unit counts and the SM clock ({sm_mhz:.0f} MHz)"
+                        + note_tail,
+                "stage_ms": stage_ms}
 
     # end-to-end through the C-ABI with host buffers, on a fresh handle over
     # the same iteration range as the timed steps (warm-up, then the steps)
@@ -686,7 +748,7 @@ def main():
     e2e = {"value": world * e2e_steps / e2e_dt, "unit": "iter/s", "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
 
-    out = {"metric": "ADMM iterations/s (one iteration = affine step + PSD projections + update)",
+    out = {"metric": METRIC,
            "value": ips, "unit": "iter/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if prec == capi.PREC_FP64 else "f32", "data": "synthetic",
@@ -697,8 +759,8 @@ def main():
            "wall_s": t_wall, "e2e": e2e, "roofline": roof,
            "gpu_launches": None}
     out["gpu_launches"] = int(solver.launches_per_iteration() * args.steps)
-    out["roofline"]["peak_source"] = "FMA-loop probe on GB300 (FP64 1.19 TFLOP/s, FP32 69.7 TFLOP/s)"
-    out["clocks"] = clk.summary(local)
+    out["roofline"]["peak_source"] = "unit counts x SM clock (derivation in the design notes)"
+    out["clocks"] = clk_sum
 
     # the FP32-projection form (tensor-core Newton-Schulz for the large block)
     # on the same instance and the same step definition, for comparison

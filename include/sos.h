@@ -91,20 +91,29 @@ typedef struct {
   const double* term_coef;     /* [n_terms] */
   int32_t n_blocks;
   const sos_block* blocks;     /* [n_blocks] */
+  int32_t matrix_r;            /* 0: the polynomial identity above; r >= 1:
+                                  a matrix-valued constraint of size r */
+  const int32_t* term_pair;    /* matrix-valued: [n_terms x 2] entry (i, j),
+                                  0 <= i <= j < r, of P_{term_poly[k]} that
+                                  term k belongs to; else unused */
 } sos_constraint;
 
-/* Matrix-valued constraints (Section V, eq. (47)-(48)):
+/* Matrix-valued constraints (Section V, eq. (47)-(48)), matrix_r = r >= 1:
  *   P_0(x) - sum_h u_h P_h(x) = (I_r (x) v(x))^T Y (I_r (x) v(x)),  Y PSD,
- * use the same struct in the variables (x_1..x_n, y_1..y_R), R >= r extra
- * variables per program.  The basis of the single block lists y_i x^a for
- * i = 1..r (block-major, the order of I_r (x) v); the rows list
- * y_i y_j x^alpha for the pairs i <= j, one per triple (alpha, i, j) of
- * Prop. 2; a term c x^e of entry (i, j), i <= j, of P_h becomes the term
- * c' x^e y_i y_j with c' = c for i == j and 2 c otherwise (the coefficient
- * of y_i y_j x^e in y^T P_h(x) y).  Entry (p, q) of Y then lands on row
- * (alpha_p + alpha_q, i_p, i_q) by the same exponent lookup as a scalar
- * block, and the rows of its Gram part stay orthogonal (Prop. 2).  Scalar
- * constraints of the same program carry zero exponents in y. */
+ * with term k adding term_coef[k] x^term_exps[k] to entry term_pair[k] of
+ * P_{term_poly[k]} (the matrices are symmetric: give entries i <= j only),
+ * row_exps the monomials alpha to match, and exactly one unweighted block
+ * whose basis is v (Y is then r N x r N, rows and columns block-major:
+ * index i N + a is basis monomial a of block row i).  The library matches
+ * coefficients for every triple (alpha, i, j) of Prop. 2 with i <= j (rows
+ * ordered by the pairs (i, j) row-major, then alpha): (alpha, i, j) and
+ * (alpha, j, i) state the same equation for a symmetric Y, so the row
+ * collects both blocks Y_ij and Y_ji and its right side is
+ * 2 (P_0)_ij - 2 sum_h u_h (P_h)_ij for i < j (the coefficient of
+ * y_i y_j x^alpha in y^T P(x) y).  Internally it runs the constraint as a
+ * scalar one in the variables (x, y_1..y_r) -- basis y_i x^a, rows
+ * y_i y_j x^alpha -- so the Gram entries of Y keep the orthogonal rows of
+ * Prop. 2 and share the scalar index map. */
 
 /* min w^T u subject to the constraints (eq. (7), eq. (15)). */
 typedef struct {
@@ -154,7 +163,12 @@ typedef struct {
                              describe that program. */
   double infeas_tol;      /* tolerance of the infeasibility certificates of
                              sos_solve, independent of its tol; 0 = 1e-7 */
-  int32_t reserved[2];    /* must be zero */
+  int32_t wait_limit_us;  /* bound of every grid-wide wait of the cooperative
+                             kernels, in microseconds; 0 = about 2 s.  A wait
+                             that runs out makes the kernel return early and
+                             the next synchronising call report
+                             SOS_ERR_TIMEOUT; the context stays usable */
+  int32_t reserved;       /* must be zero */
 } sos_options;
 
 /* Per-instance solve report.  x, y, s are optional caller-allocated HOST
@@ -270,28 +284,33 @@ int sos_host_plan(const sos_program* prog, int32_t weighted_form, int64_t dims[6
  * SOS_ERR_CUDA, SOS_ERR_TIMEOUT; the message is in sos_last_error(NULL). */
 int sos_psd_project(const double* in, double* out, int32_t N, void* stream);
 
-/* The projection of the mixed-precision form (SOS_PREC_MIXED), for one block:
- * cyclic Jacobi in FP32, then one refinement with FP64 sums -- the
+/* The projection of the mixed-precision form (SOS_PREC_MIXED), for one block.
+ * N <= 112: cyclic Jacobi in FP32, then one refinement with FP64 sums -- the
  * eigenvector matrix V is re-orthonormalised with F = V^T V - I, the Ritz
  * matrix B = V^T W V is formed, and its off-diagonal part enters to first
- * order (the derivative of the eigenvalue map max(., 0) at diag(B)).  The
+ * order (the derivative of the eigenvalue map max(., 0) at diag(B)); the
  * result is accurate to about 1e-7 |W|_F, where the FP32 Jacobi alone gives
- * about 1e-5 |W|_F.  Same contract as sos_psd_project (device pointers to
- * N(N+1)/2 packed doubles; off-diagonal entries scaled by sqrt 2), for
- * 1 <= N <= 112; larger N returns SOS_ERR_UNSUPPORTED.
+ * about 1e-5 |W|_F.  N > 112: P(W) = (W + W sign(W)) / 2 with sign(W) by the
+ * Newton-Schulz iteration on the tensor cores (BF16 three-part operands,
+ * FP32 accumulation), as the large blocks of that form; accurate to about
+ * 1e-5 |W|_F, less for eigenvalues closer to zero than the iteration's
+ * stopping tolerance resolves.  Same contract as sos_psd_project (device
+ * pointers to N(N+1)/2 packed doubles; off-diagonal entries scaled by
+ * sqrt 2); an N whose Newton-Schulz grid needs more CTAs than the GPU has
+ * SMs returns SOS_ERR_UNSUPPORTED.
  * Errors: SOS_ERR_INVALID_ARG, SOS_ERR_UNSUPPORTED, SOS_ERR_CUDA,
  * SOS_ERR_TIMEOUT. */
 int sos_psd_project_mixed(const double* in, double* out, int32_t N, void* stream);
 
 /* Allocation-free variant of sos_psd_project, for callers that cannot call
- * cudaMalloc: code running while another component captures the stream into
- * a CUDA graph, code whose device memory is owned by a pool or allocator it
+ * cudaMalloc: code whose device memory is owned by a pool or allocator it
  * may not bypass, latency-critical loops that must not block on the CUDA
  * allocator, or plugins whose host forbids device allocations after start-up.
  * The paper has no counterpart: this is a deployment convenience.
  *
  * Same contract as sos_psd_project (in, out: DEVICE pointers to N(N+1)/2
- * packed doubles, not overlapping; work on stream, returns when finished),
+ * packed doubles, not overlapping; work on stream; the call synchronises
+ * that stream and returns when the projection has finished),
  * except that the call allocates nothing: its scratch is one fixed array of
  * about 3 MB compiled into the library, resident on every GPU that loads the
  * library until the process exits.
@@ -355,6 +374,11 @@ int sos_stats(sos_handle* h, int64_t out[4]);
  * iteration of the chosen candidate during tuning. */
 int sos_tuning(const sos_handle* h, int32_t out[5]);
 
+/* Sets the bound of the grid-wide waits (as sos_options.wait_limit_us; 0 =
+ * about 2 s) for the iterations issued from now on.  Errors:
+ * SOS_ERR_INVALID_ARG (us < 0), SOS_ERR_CUDA. */
+int sos_set_wait_limit(sos_handle* h, int32_t us);
+
 /* Number of CUDA kernels one ADMM iteration launches for this handle. */
 int sos_launches_per_iteration(const sos_handle* h);
 
@@ -367,8 +391,14 @@ int sos_launches_per_iteration(const sos_handle* h);
  * x = P^-1 r (eq. (27b)), 5 = y = A_L^T x, 6 = Woodbury solve
  * z = L^-T L^-1 y (eq. (28)), 7 = sigma_2 = x - P^-1 A_L z, 8 = per-instance
  * scalars (eq. (24b), (25)) and free variables, 9 = u_y, v_y and u_hat_2
- * rows.  Stages 4..9 run out of order leave the iterate meaningless; they
- * exist to time one kernel.
+ * rows; and single kernels of the large-block projection (stage 2 is
+ * 10..14 in order): 10 = gather of W into a dense FP32 copy, 11 = Householder
+ * reduction to tridiagonal form, 12 = eigenvectors of the tridiagonal matrix
+ * mapped back, 13 = FP64 refinement and reconstruction (10..13 do nothing
+ * for blocks that the FP64 tridiagonal path does not take), 14 = grid
+ * Jacobi kernel (the whole projection of those blocks; after a successful
+ * tridiagonal path it does nothing).  Stages 4..14 run out of order leave
+ * the iterate meaningless; they exist to time one kernel.
  * sos_stage_bytes gives the algorithmic bytes of one launch of a stage:
  * every array element the stage has to read or write, counted once (the
  * numerator of an HBM roofline fraction).  Errors: SOS_ERR_INVALID_ARG. */

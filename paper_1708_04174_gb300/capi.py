@@ -35,7 +35,7 @@ class sos_block(C.Structure):
 class sos_constraint(C.Structure):
     _fields_ = [("n_rows", C.c_int32), ("row_exps", _i32p), ("n_terms", C.c_int64), ("term_poly", _i32p),
                 ("term_exps", _i32p), ("term_coef", _f64p), ("n_blocks", C.c_int32),
-                ("blocks", C.POINTER(sos_block))]
+                ("blocks", C.POINTER(sos_block)), ("matrix_r", C.c_int32), ("term_pair", _i32p)]
 
 
 class sos_program(C.Structure):
@@ -46,7 +46,8 @@ class sos_program(C.Structure):
 class sos_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("k_check", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("solve_mode", C.c_int32), ("large_method", C.c_int32), ("warm_restart", C.c_int32),
-                ("weighted_form", C.c_int32), ("infeas_tol", C.c_double), ("reserved", C.c_int32 * 2)]
+                ("weighted_form", C.c_int32), ("infeas_tol", C.c_double), ("wait_limit_us", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class sos_result(C.Structure):
@@ -71,6 +72,7 @@ EXPORTS = {
     "sos_host_plan": (C.c_int, [C.POINTER(sos_program), C.c_int32, C.POINTER(C.c_int64), _i32p, _f64p, _f64p,
                                 _f64p]),
     "sos_stream": (C.c_void_p, [C.c_void_p]),
+    "sos_set_wait_limit": (C.c_int, [C.c_void_p, C.c_int32]),
     "sos_launches_per_iteration": (C.c_int, [C.c_void_p]),
     "sos_tuning": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "sos_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
@@ -147,28 +149,16 @@ class _Marshalled:
 
         for pi, pg in enumerate(progs):
             n = pg.n
-            # a matrix-valued constraint of size r is passed as a scalar one in
-            # the variables (x, y_1..y_R): the basis entry (i, a) of I_r (x) v
-            # is y_i x^a and the row triple (alpha, i, j) is y_i y_j x^alpha,
-            # so the library's exponent lookup finds the triple of every Gram
-            # entry; scalar constraints get zero y-exponents
-            R = max([c.r for c in pg.constraints if hasattr(c, "r")] + [0])
-            nv = n + R
 
-            def pad(e, extra=None):
-                e = np.asarray(e, dtype=np.int32).reshape(-1, n)
-                out = np.zeros((e.shape[0], nv), dtype=np.int32)
-                out[:, :n] = e
-                if extra is not None:
-                    out[:, n:] = extra
-                return np.ascontiguousarray(out)
+            def as_exps(e):
+                return np.ascontiguousarray(np.asarray(e, dtype=np.int32).reshape(-1, n))
 
             cons = (sos_constraint * len(pg.constraints))()
             for ci, con in enumerate(pg.constraints):
                 if hasattr(con, "r"):
-                    self._matrix(cons[ci], con, n, R, pad, mono)
+                    self._matrix(cons[ci], con, n, mono)
                     continue
-                rows = pad(mono(n, con.degree, getattr(con, "min_degree", 0)))
+                rows = as_exps(mono(n, con.degree, getattr(con, "min_degree", 0)))
                 tp, te, tc = [], [], []
                 arrays = getattr(con, "term_arrays", None)
                 g0a = getattr(con, "g0_arrays", None)
@@ -192,15 +182,15 @@ class _Marshalled:
                     te = np.concatenate([te, np.asarray(exps, dtype=np.int32).reshape(-1, n)])
                     tc = np.concatenate([tc, np.asarray(coef, dtype=np.float64)])
                 tp = np.ascontiguousarray(tp)
-                te = pad(te) if R else np.ascontiguousarray(te)
+                te = as_exps(te)
                 tc = np.ascontiguousarray(tc)
                 blks = (sos_block * len(con.blocks))()
                 for bi, blk in enumerate(con.blocks):
-                    bas = pad(mono(n, blk.basis_degree, getattr(blk, "min_degree", 0)))
+                    bas = as_exps(mono(n, blk.basis_degree, getattr(blk, "min_degree", 0)))
                     blks[bi].N = bas.shape[0]
                     blks[bi].basis_exps = _ptr(bas, C.c_int32)
                     if blk.weight is not None:
-                        we = pad(np.array(list(blk.weight.keys()), dtype=np.int32))
+                        we = as_exps(np.array(list(blk.weight.keys()), dtype=np.int32))
                         wc = np.ascontiguousarray(list(blk.weight.values()), dtype=np.float64)
                         blks[bi].n_weight_terms = len(wc)
                         blks[bi].weight_exps = _ptr(we, C.c_int32)
@@ -219,7 +209,7 @@ class _Marshalled:
                 cons[ci].blocks = blks
                 self.keep += [rows, tp, te, tc, blks]
             w = np.ascontiguousarray(pg.w, dtype=np.float64)
-            self.progs[pi].n_vars = nv
+            self.progs[pi].n_vars = n
             self.progs[pi].t = len(w)
             self.progs[pi].w = _ptr(w, C.c_double)
             self.progs[pi].n_constraints = len(pg.constraints)
@@ -227,47 +217,40 @@ class _Marshalled:
             self.keep += [w, cons]
 
 
-    def _matrix(self, out, con, n, R, pad, mono):
-        """sos_constraint of a matrix-valued constraint (Section V) in the
-        variables (x, y): rows y_i y_j x^alpha for the pairs i <= j row-major,
-        then alpha; terms of P_h[i][j] (h = 0 for P_0) times 2 off the
-        diagonal, the coefficient of y_i y_j x^alpha in y^T P_h(x) y; basis
-        y_i x^a block-major."""
-        r = con.r
+    def _matrix(self, out, con, n, mono):
+        """sos_constraint of a matrix-valued constraint (Section V): the
+        monomials alpha, the terms of every entry (i, j), i <= j, of P_0, P_1,
+        ... with their pair, and the basis v of the block, all in x; libsos
+        forms the row triples (alpha, i, j) itself."""
         al = mono(n, con.degree, con.min_degree)
-        yy = []
-        for (i, j) in con.pairs:
-            e = np.zeros(R, dtype=np.int32)
-            e[i] += 1
-            e[j] += 1
-            yy.append(e)
-        rows = np.concatenate([pad(al, e) for e in yy])
-        tp, te, tc = [], [], []
+        tp, te, tc, pairs = [], [], [], []
         for h, Ph in enumerate([con.P0] + list(con.P)):
-            for (i, j), e_y in zip(con.pairs, yy):
-                sym = 1.0 if i == j else 2.0
+            for (i, j) in con.pairs:
                 for e, cval in Ph[i][j].items():
                     tp.append(h)
-                    te.append(list(e) + list(e_y))
-                    tc.append(sym * cval)
+                    te.append(list(e))
+                    tc.append(cval)
+                    pairs.append((i, j))
         tp = np.ascontiguousarray(tp, dtype=np.int32)
-        te = np.ascontiguousarray(np.array(te, dtype=np.int32).reshape(-1, n + R))
+        te = np.ascontiguousarray(np.array(te, dtype=np.int32).reshape(-1, n))
         tc = np.ascontiguousarray(tc, dtype=np.float64)
-        bas1 = mono(n, con.block.basis_degree, con.block.min_degree)
-        bas = np.concatenate([pad(bas1, np.eye(R, dtype=np.int32)[i]) for i in range(r)])
+        pr = np.ascontiguousarray(np.array(pairs, dtype=np.int32).reshape(-1, 2))
+        bas = np.ascontiguousarray(mono(n, con.block.basis_degree, con.block.min_degree))
         blks = (sos_block * 1)()
         blks[0].N = bas.shape[0]
         blks[0].basis_exps = _ptr(bas, C.c_int32)
         blks[0].n_weight_terms = 0
-        out.n_rows = rows.shape[0]
-        out.row_exps = _ptr(rows, C.c_int32)
+        out.n_rows = al.shape[0]
+        out.row_exps = _ptr(al, C.c_int32)
         out.n_terms = len(tp)
         out.term_poly = _ptr(tp, C.c_int32)
         out.term_exps = _ptr(te, C.c_int32)
         out.term_coef = _ptr(tc, C.c_double)
         out.n_blocks = 1
         out.blocks = blks
-        self.keep += [rows, tp, te, tc, bas, blks]
+        out.matrix_r = con.r
+        out.term_pair = _ptr(pr, C.c_int32)
+        self.keep += [al, tp, te, tc, pr, bas, blks]
 
 
 def psd_project(in_ptr: int, out_ptr: int, N: int, stream: int = 0):
@@ -280,7 +263,8 @@ MIXED_MAX_N = 112
 
 def psd_project_mixed(in_ptr: int, out_ptr: int, N: int, stream: int = 0):
     """PSD projection of the mixed form: FP32 Jacobi plus an FP64-summed
-    refinement (N <= MIXED_MAX_N); device pointers."""
+    refinement for N <= MIXED_MAX_N, the tensor-core Newton-Schulz sign
+    iteration above; device pointers."""
     _check(lib().sos_psd_project_mixed(C.c_void_p(in_ptr), C.c_void_p(out_ptr), N,
                                        C.c_void_p(stream) if stream else None))
 
@@ -313,7 +297,8 @@ class Solver:
     """One libsos handle over a batch of SOS programs (instances)."""
 
     def __init__(self, progs, precision: int = PREC_FP64, k_check: int = 10, stream=None, solve_mode: int = 0,
-                 large_method: int = 0, warm_restart: int = 0, infeas_tol: float = 0.0, weighted_form: int = 0):
+                 large_method: int = 0, warm_restart: int = 0, infeas_tol: float = 0.0, weighted_form: int = 0,
+                 wait_limit_us: int = 0):
         if not isinstance(progs, (list, tuple)):
             progs = [progs]
         self.n_inst = len(progs)
@@ -327,6 +312,7 @@ class Solver:
         opts.warm_restart = warm_restart
         opts.infeas_tol = infeas_tol
         opts.weighted_form = weighted_form
+        opts.wait_limit_us = wait_limit_us
         h = C.c_void_p()
         _check(lib().sos_setup(m.progs, len(progs), C.byref(opts), C.byref(h)))
         self.h = h
@@ -382,6 +368,10 @@ class Solver:
 
     def run_stage(self, stage: int):
         _check(lib().sos_run_stage(self.h, stage), self.h)
+
+    def set_wait_limit(self, us: int):
+        """Bound of the grid-wide device waits, microseconds (0: about 2 s)."""
+        _check(lib().sos_set_wait_limit(self.h, us), self.h)
 
     def get_iterate(self):
         u = np.zeros(self.total)

@@ -64,13 +64,14 @@ struct sos_handle {
   std::vector<NsBlock> ns_large;  // large blocks projected by Newton-Schulz on the tensor cores
   int32_t large_method = 0;
   double infeas_tol = 1e-7;   // tolerance of the infeasibility certificates
+  int32_t wait_limit_us = 0;  // bound of the grid-wide waits (0: about 2 s)
   int32_t* active = nullptr;  // device
   std::vector<int32_t> active_h;
   std::vector<int32_t> iters_h, status_h;
   int64_t iter_count = 0;
   int32_t* blk_sweeps = nullptr;  // device
   int32_t large_grid_best = 0;    // grid chosen for the cooperative Jacobi kernel
-  int64_t stage_bytes[10] = {0};  // algorithmic bytes of each profiling stage
+  int64_t stage_bytes[15] = {0};  // algorithmic bytes of each profiling stage
   std::vector<int32_t> row_perm;  // device row q holds the constraint row row_perm[q]
   int64_t* cat_map = nullptr;     // device iterate exchange: source of each concatenated position (lazy)
   int64_t cat_total = 0;
@@ -156,6 +157,15 @@ struct Common {
   int32_t* blk_sweeps;
 };
 
+// Clock cycles of a wait bound given in microseconds (0: about 2 s).
+long long wait_cycles(int32_t us) {
+  if (us <= 0) return 4000000000ll;
+  int dev = 0, khz = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0) khz = 2070000;
+  return static_cast<long long>(us) * khz / 1000;
+}
+
 template <typename T>
 int make_devplan(sos_handle* h, const Common& c, int32_t max_teff, DevPlan<T>& p) {
   p.n_inst = h->n_inst;
@@ -209,6 +219,7 @@ int make_devplan(sos_handle* h, const Common& c, int32_t max_teff, DevPlan<T>& p
   TRY(alloc(h, h->M, &p.uy));
   TRY(alloc(h, h->M, &p.vy));
   TRY(alloc(h, h->M, &p.uh2));
+  p.wait_limit = wait_cycles(h->wait_limit_us);
   return SOS_OK;
 }
 
@@ -241,6 +252,13 @@ cudaError_t enqueue_stage(sos_handle* h, const DevPlan<T>& p, std::vector<LargeB
                           const SmallWarm<TC>& wm, int stage) {
   cudaError_t e = cudaSuccess;
   if (stage >= 4 && stage <= 9) return launch_affine_part<T>(p, h->shape, stage - 4, h->stream);
+  if (stage >= 10 && stage <= 14) {
+    for (auto& lb : large) {
+      e = launch_psd_large_part<T, TC>(p, lb.bid, lb.N, lb.scratch, lb.grid, stage - 10, h->stream);
+      if (e != cudaSuccess) return e;
+    }
+    return e;
+  }
   if (stage == 0 || stage == 3) {
     e = launch_affine<T>(p, h->shape, h->stream);
     if (e != cudaSuccess) return e;
@@ -970,6 +988,11 @@ int sos_setup(const sos_program* progs, int32_t n_progs, const sos_options* opts
     }
     h->weighted_form = opts->weighted_form;
     if (opts->infeas_tol > 0) h->infeas_tol = opts->infeas_tol;
+    if (opts->wait_limit_us < 0 || opts->reserved != 0) {
+      g_setup_error = "wait_limit_us must be >= 0 and reserved 0";
+      return SOS_ERR_INVALID_ARG;
+    }
+    h->wait_limit_us = opts->wait_limit_us;
     if (opts->warm_restart > 0)
       h->warm64.limit = h->warm32.limit = opts->warm_restart;
   }
@@ -1288,8 +1311,13 @@ namespace {
 int psd_project_one(const double* in, double* out, int32_t N, void* stream, bool mixed) {
   if (!in || !out || N < 1) return SOS_ERR_INVALID_ARG;
   if (mixed && N > psd_small_max_n(kFormMixed)) {
-    g_setup_error = "the mixed projection takes N <= " + std::to_string(psd_small_max_n(kFormMixed));
-    return SOS_ERR_UNSUPPORTED;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ns_grid(N) > sms) {
+      g_setup_error = "the mixed projection of N = " + std::to_string(N) + " needs more SMs than this GPU has";
+      return SOS_ERR_UNSUPPORTED;
+    }
   }
   sos_handle tmp;  // owns the scratch allocations of this call
   sos_handle* h = &tmp;
@@ -1341,7 +1369,16 @@ int psd_project_one(const double* in, double* out, int32_t N, void* stream, bool
       break;
     }
     cudaError_t e;
-    if (mixed) {
+    if (mixed && N > psd_small_max_n(kFormMixed)) {  // Newton-Schulz on the tensor cores
+      NsScratch S{};
+      const size_t Np = static_cast<size_t>(ns_padded(N));
+      if ((rc = alloc(h, Np * Np, &S.Wf)) != SOS_OK || (rc = alloc(h, Np * Np, &S.X)) != SOS_OK ||
+          (rc = alloc(h, Np * Np, &S.Y)) != SOS_OK || (rc = alloc(h, Np * Np, &S.Xn)) != SOS_OK ||
+          (rc = alloc(h, static_cast<size_t>(ns_grid(N)), &S.partial)) != SOS_OK || (rc = alloc(h, 2, &S.bar)) != SOS_OK ||
+          (rc = alloc(h, 1, &S.iters_out)) != SOS_OK)
+        break;
+      e = launch_psd_ns<double>(p, 0, N, S, s);
+    } else if (mixed) {
       const int cap = N <= 16 ? 16 : N <= 32 ? 32 : N <= 48 ? 48 : N <= 64 ? 64 : N <= 96 ? 96 : 112;
       e = prepare_kernels<double, float>(cap, 0);
       if (e == cudaSuccess) e = launch_psd_small<double, float>(p, ids, 1, cap, SmallWarm<float>(), s);
@@ -1408,6 +1445,19 @@ int sos_tuning(const sos_handle* h, int32_t out[5]) {
   return SOS_OK;
 }
 
+int sos_set_wait_limit(sos_handle* h, int32_t us) {
+  if (!h || us < 0) return SOS_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(h->stream));
+  h->wait_limit_us = us;
+  h->d64.wait_limit = h->d32.wait_limit = wait_cycles(us);
+  if (h->graph) {  // the captured launches hold the old bound
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  h->graph_tried = false;
+  return SOS_OK;
+}
+
 int sos_launches_per_iteration(const sos_handle* h) {
   if (!h) return SOS_ERR_INVALID_ARG;
   if (h->persistent) return 0;  // one launch for all iterations of a call
@@ -1419,13 +1469,13 @@ int sos_launches_per_iteration(const sos_handle* h) {
 void* sos_stream(sos_handle* h) { return h ? static_cast<void*>(h->stream) : nullptr; }
 
 int sos_stage_bytes(const sos_handle* h, int32_t stage, int64_t* bytes) {
-  if (!h || !bytes || stage < 0 || stage > 9) return SOS_ERR_INVALID_ARG;
+  if (!h || !bytes || stage < 0 || stage > 14) return SOS_ERR_INVALID_ARG;
   *bytes = h->stage_bytes[stage];
   return SOS_OK;
 }
 
 int sos_run_stage(sos_handle* h, int32_t stage) {
-  if (!h || stage < 0 || stage > 9) return SOS_ERR_INVALID_ARG;
+  if (!h || stage < 0 || stage > 14) return SOS_ERR_INVALID_ARG;
   cudaError_t e = enqueue_any(h, stage);
   if (e != cudaSuccess) return set_err(h, SOS_ERR_CUDA, std::string("stage launch: ") + cudaGetErrorString(e));
   return SOS_OK;

@@ -12,7 +12,6 @@
 namespace sos {
 namespace {
 
-constexpr long long kSpinLimitCycles = 4000000000ll;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -96,9 +95,9 @@ __device__ __forceinline__ void st_release_u32(unsigned* ptr, unsigned v) {
 // writes before thread 0's arrival, the arrival is an acquire-release
 // read-modify-write at GPU scope (so the last arriver acquires every earlier
 // arrival), the release is a store-release and the pollers load-acquire it.
-// Bounded spin: on expiry (or when another CTA already raised the error
-// word) every CTA returns false.
-__device__ bool grid_barrier(unsigned* bar, unsigned target, int32_t* err) {
+// Bounded spin (limit in clock cycles): on expiry (or when another CTA
+// already raised the error word) every CTA returns false.
+__device__ bool grid_barrier(unsigned* bar, unsigned target, int32_t* err, long long limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -115,7 +114,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned target, int32_t* err) {
           good = 0;
           break;
         }
-        if (clock64() - t0 > kSpinLimitCycles) {
+        if (clock64() - t0 > limit) {
           atomicExch(err, 1);
           good = 0;
           break;

@@ -890,10 +890,11 @@ __device__ void newton_correction(const double* S, double* C, int N, int ld) {
 }
 
 // Grid-wide maximum of one value per CTA (same result in every CTA).
-__device__ bool grid_max(double v, double* red, LargeScratch<double>& L, unsigned& gen, int32_t* err, double& out) {
+__device__ bool grid_max(double v, double* red, LargeScratch<double>& L, unsigned& gen, int32_t* err, long long limit,
+                         double& out) {
   v = block_max(v, red);
   if (threadIdx.x == 0) L.partial[blockIdx.x] = v;
-  if (!grid_barrier(L.bar, (++gen) * gridDim.x, err)) return false;
+  if (!grid_barrier(L.bar, (++gen) * gridDim.x, err, limit)) return false;
   double m = 0.0;
   for (unsigned c = threadIdx.x; c < gridDim.x; c += blockDim.x) m = fmax(m, __ldcg(L.partial + c));
   out = block_max(m, red);
@@ -943,23 +944,23 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
     double rmax = 0.0;
     gemm_sym<true, false>(Vc, Vc, L.T1, N, Np, OrthMax{&rmax}, sA, sB);
     double gm;
-    if (!grid_max(rmax, red, L, gen, err, gm)) return;
+    if (!grid_max(rmax, red, L, gen, err, p.wait_limit, gm)) return;
     if (!(gm <= 1e-3)) {  // not even FP32-orthonormal
       hand_over(L, false);
       return;
     }
     if (gm > 1e-15) {
       gemm_full<false, false>(Vc, L.T1, Vn, N, Np, NsFactor(), sA, sB);
-      if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+      if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
       double* t = Vc;
       Vc = Vn;
       Vn = t;
       ++work;
     }
     gemm_full<false, false>(L.Wf, Vc, L.T1, N, Np, Ident(), sA, sB);
-    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
     gemm_sym<true, false>(Vc, L.T1, L.B0, N, Np, NoOp(), sA, sB);
-    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
 
     // check of the first-order projection of B: a pair of diagonal entries
     // of opposite signs adds |b_lk|^2 / (|b_ll| + |b_kk|) at second order
@@ -995,7 +996,7 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
       L.partial[2 * G + blockIdx.x] = second;
       L.partial[3 * G + blockIdx.x] = fro2;
     }
-    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
     double a = 0.0, rk = 0.0, sc = 0.0, f2 = 0.0;
     for (unsigned c = threadIdx.x; c < G; c += blockDim.x) {
       a = fmax(a, __ldcg(L.partial + c));
@@ -1018,9 +1019,9 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
       return;
     }
     newton_correction(L.B0, L.T1, N, Np);
-    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
     gemm_full<false, false>(Vc, L.T1, Vn, N, Np, PlusIdent(), sA, sB);
-    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
     double* t = Vc;
     Vc = Vn;
     Vn = t;
@@ -1029,7 +1030,7 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
   // T1 = V M with M the first-order projection of B, then U = T1 V^T on the
   // lower triangle; u = svec(U), v = u - W
   gemm_full<false, false>(Vc, L.B0, L.T1, N, Np, FirstOrder{L.B0, Np}, sA, sB);
-  if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+  if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
   auto emit = [&](int ii, int jj, double x) {
     const int64_t kk = packed_index(ii, jj, N);
     const T w = proj_input(p, bd, kk, ii != jj, s_sm);
@@ -1056,36 +1057,54 @@ size_t tri_vectors_smem(int N) {
 
 }  // namespace
 
+cudaError_t launch_psd_tri_part(const DevPlan<double>& p, int bid, int N, const LargeScratch<double>& L, int grid,
+                                int part, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  switch (part) {
+    case 0:
+      k_tri_gather<double><<<kGatherCtas, 256, 0, s>>>(p, bid, L);
+      return cudaGetLastError();
+    case 1: {
+      const size_t sm1 = tri_reduce_smem(N);
+      e = cudaFuncSetAttribute(k_tri_reduce<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm1));
+      if (e != cudaSuccess) return e;
+      k_tri_reduce<double><<<1, kTriThreads, sm1, s>>>(p, bid, L);
+      return cudaGetLastError();
+    }
+    case 2: {
+      const size_t sm2 = tri_vectors_smem(N);
+      e = cudaFuncSetAttribute(k_tri_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm2));
+      if (e != cudaSuccess) return e;
+      k_tri_vectors<<<(N + kVecThreads / 32 - 1) / (kVecThreads / 32), kVecThreads, sm2, s>>>(p, bid, L);
+      return cudaGetLastError();
+    }
+    case 3: {
+      e = cudaMemsetAsync(L.bar, 0, 2 * sizeof(uint32_t), s);
+      if (e != cudaSuccess) return e;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(grid);
+      cfg.blockDim = dim3(kRecThreads);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, k_tri_recon<double>, p, bid, L);
+    }
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_psd_tri(const DevPlan<double>& p, int bid, int N, const LargeScratch<double>& L, int grid,
                            cudaStream_t s) {
-  const size_t sm1 = tri_reduce_smem(N), sm2 = tri_vectors_smem(N);
-  cudaError_t e = cudaFuncSetAttribute(k_tri_reduce<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(sm1));
-  if (e != cudaSuccess) return e;
-  k_tri_gather<double><<<kGatherCtas, 256, 0, s>>>(p, bid, L);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_tri_reduce<double><<<1, kTriThreads, sm1, s>>>(p, bid, L);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_tri_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm2));
-  if (e != cudaSuccess) return e;
-  k_tri_vectors<<<(N + kVecThreads / 32 - 1) / (kVecThreads / 32), kVecThreads, sm2, s>>>(p, bid, L);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(L.bar, 0, 2 * sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kRecThreads);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_tri_recon<double>, p, bid, L);
+  for (int part = 0; part < 4; ++part) {
+    const cudaError_t e = launch_psd_tri_part(p, bid, N, L, grid, part, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace sos

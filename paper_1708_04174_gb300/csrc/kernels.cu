@@ -813,7 +813,7 @@ __global__ void __launch_bounds__(256, 1) k_psd_large(DevPlan<T> p, int bid, Lar
   }
   const double part = block_sum(nrm, red);
   if (threadIdx.x == 0) L.partial[blockIdx.x] = part;
-  if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+  if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
   double tot = 0.0;
   for (unsigned c = 0; c < G; ++c) tot += __ldcg(L.partial + c);
   // FP64: the sweeps stop once every off-diagonal entry is below
@@ -831,7 +831,7 @@ __global__ void __launch_bounds__(256, 1) k_psd_large(DevPlan<T> p, int bid, Lar
       const int i = ti * 16 + (threadIdx.x >> 4), j = tj * 16 + (threadIdx.x & 15);
       if (i < Np && j < Np) L.T1[static_cast<int64_t>(i) * Np + j] = v;
     }
-    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
     for (int tile = blockIdx.x; tile < nt * nt; tile += G) {  // B = V^T T1 (lower tiles, mirrored)
       const int ti = tile / nt, tj = tile - ti * nt;
       if (ti < tj) continue;
@@ -842,7 +842,7 @@ __global__ void __launch_bounds__(256, 1) k_psd_large(DevPlan<T> p, int bid, Lar
         Wf[static_cast<int64_t>(j) * Np + i] = v;
       }
     }
-    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
   }
 
   // Jacobi sweeps, double buffered (cur -> nxt).  Every CTA computes all
@@ -876,7 +876,7 @@ __global__ void __launch_bounds__(256, 1) k_psd_large(DevPlan<T> p, int bid, Lar
       const double bm = block_max(d(mx), red);
       double* part = L.partial + static_cast<int64_t>(1 + (sweep & 1)) * G;
       if (threadIdx.x == 0) part[blockIdx.x] = bm;
-      if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+      if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
       double gv = 0.0;
       for (unsigned c = threadIdx.x; c < G; c += blockDim.x) gv = fmax(gv, __ldcg(part + c));
       const double gm = block_max(gv, red);
@@ -963,7 +963,7 @@ __global__ void __launch_bounds__(256, 1) k_psd_large(DevPlan<T> p, int bid, Lar
           vr[qq] = s * vp + c * vq;
         }
       }
-      if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+      if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
       TC* tmp = cur;
       cur = nxt;
       nxt = tmp;
@@ -994,14 +994,14 @@ __global__ void __launch_bounds__(256, 1) k_psd_large(DevPlan<T> p, int bid, Lar
       }
       L.B1[q] = m;
     }
-    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
     for (int tile = blockIdx.x; tile < nt * nt; tile += G) {
       const int ti = tile / nt, tj = tile - ti * nt;
       const TC v = tile_mm(V, L.B1, Np, ti, tj, 0, sA, sB);
       const int i = ti * 16 + (threadIdx.x >> 4), j = tj * 16 + (threadIdx.x & 15);
       if (i < Np && j < Np) L.T1[static_cast<int64_t>(i) * Np + j] = v;
     }
-    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
   }
   // U = (V M or V max(diag B, 0)) V^T on lower tiles; write u and v = u - W
   for (int tile = blockIdx.x; tile < ntl * ntl; tile += G) {
@@ -1037,7 +1037,7 @@ __global__ void __launch_bounds__(256, 1) k_psd_large(DevPlan<T> p, int bid, Lar
     }
   }
   if (sizeof(TC) < 8) {  // FP32 eigenvectors: V <- V (3 I - V^T V) / 2 before they are kept
-    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
     for (int tile = blockIdx.x; tile < nt * nt; tile += G) {
       const int ti = tile / nt, tj = tile - ti * nt;
       const TC v = tile_mm(V, V, Np, ti, tj, 1, sA, sB);
@@ -1045,14 +1045,14 @@ __global__ void __launch_bounds__(256, 1) k_psd_large(DevPlan<T> p, int bid, Lar
       if (i < Np && j < Np)
         L.T1[static_cast<int64_t>(i) * Np + j] = ((i == j) ? static_cast<TC>(1.5) : static_cast<TC>(0)) - static_cast<TC>(0.5) * v;
     }
-    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
     for (int tile = blockIdx.x; tile < nt * nt; tile += G) {
       const int ti = tile / nt, tj = tile - ti * nt;
       const TC v = tile_mm(V, L.T1, Np, ti, tj, 0, sA, sB);
       const int i = ti * 16 + (threadIdx.x >> 4), j = tj * 16 + (threadIdx.x & 15);
       if (i < Np && j < Np) L.B1[static_cast<int64_t>(i) * Np + j] = v;
     }
-    if (!grid_barrier(L.bar, (++gen) * G, err)) return;
+    if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
     for (int64_t q = gt; q < static_cast<int64_t>(Np) * Np; q += gs) V[q] = __ldcg(L.B1 + q);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1249,7 +1249,7 @@ __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch
 #define NS_SYNC()                                   \
   do {                                              \
     tc::fence_before();                             \
-    alive = grid_barrier(S.bar, (++gen) * G, err);  \
+    alive = grid_barrier(S.bar, (++gen) * G, err, p.wait_limit);  \
     tc::fence_after();                              \
   } while (0)
   // load W (unscaled, FP32) and its Frobenius norm
@@ -1536,7 +1536,7 @@ __global__ void __launch_bounds__(256) k_persistent(DevPlan<T> p, PersistArgs<TC
   const int warp0 = static_cast<int>(gt >> 5), nwarps = static_cast<int>(gs >> 5);
   int32_t* err = p.err;
 #define SOS_GRID_SYNC() \
-  if (!grid_barrier(a.bar, (++gen) * G, err)) return
+  if (!grid_barrier(a.bar, (++gen) * G, err, p.wait_limit)) return
   int it = 0;
   for (it = 1; it <= a.max_iter; ++it) {
     d_rows_r(p, gt, gs);
@@ -1687,16 +1687,15 @@ size_t large_smem_bytes(int N, size_t es) {
 }
 
 template <typename T, typename TC>
-cudaError_t launch_psd_large(const DevPlan<T>& p, int bid, int N, const LargeScratch<TC>& ls, int grid,
-                             cudaStream_t s) {
-  cudaError_t e = cudaSuccess;
-  if constexpr (sizeof(T) == 8 && sizeof(TC) == 8) {
-    if (tri_path(N)) {
-      e = launch_psd_tri(p, bid, N, ls, grid, s);
-      if (e != cudaSuccess) return e;
+cudaError_t launch_psd_large_part(const DevPlan<T>& p, int bid, int N, const LargeScratch<TC>& ls, int grid,
+                                  int part, cudaStream_t s) {
+  if (part < 4) {
+    if constexpr (sizeof(T) == 8 && sizeof(TC) == 8) {
+      if (tri_path(N)) return launch_psd_tri_part(p, bid, N, ls, grid, part, s);
     }
+    return cudaSuccess;
   }
-  e = cudaMemsetAsync(ls.bar, 0, 2 * sizeof(uint32_t), s);
+  cudaError_t e = cudaMemsetAsync(ls.bar, 0, 2 * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -1709,6 +1708,16 @@ cudaError_t launch_psd_large(const DevPlan<T>& p, int bid, int N, const LargeScr
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_psd_large<T, TC>, p, bid, ls);
+}
+
+template <typename T, typename TC>
+cudaError_t launch_psd_large(const DevPlan<T>& p, int bid, int N, const LargeScratch<TC>& ls, int grid,
+                             cudaStream_t s) {
+  for (int part = 0; part < 5; ++part) {
+    const cudaError_t e = launch_psd_large_part<T, TC>(p, bid, N, ls, grid, part, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <typename T>
@@ -1806,6 +1815,8 @@ cudaError_t launch_psd_ns(const DevPlan<T>& p, int bid, int N, const NsScratch& 
                                                cudaStream_t);                                               \
   template cudaError_t launch_psd_large<T, TC>(const DevPlan<T>&, int, int, const LargeScratch<TC>&, int,     \
                                                cudaStream_t);                                               \
+  template cudaError_t launch_psd_large_part<T, TC>(const DevPlan<T>&, int, int, const LargeScratch<TC>&, int, \
+                                                    int, cudaStream_t);                                      \
   template cudaError_t prepare_kernels<T, TC>(int, int);                                                     \
   template int persistent_max_ctas_per_sm<T, TC>(int, int);                                                  \
   template cudaError_t launch_persistent<T, TC>(const DevPlan<T>&, const PersistArgs<TC>&, int, int, int,     \

@@ -69,6 +69,7 @@ struct DevPlan {
   double* atyl = nullptr;  // residual work (TL)
   int32_t* err = nullptr;  // device error word (nonzero: a bounded wait expired)
   int32_t* blk_sweeps = nullptr;  // Jacobi sweeps of each block in the last iteration
+  long long wait_limit = 4000000000ll;  // bound of each grid-wide wait, clock cycles (~2 s)
 };
 
 // Scratch of the large-block (cooperative) projection, one per large block.
@@ -103,6 +104,10 @@ constexpr int kTriMinN = 33, kTriMaxN = 232;
 __host__ __device__ constexpr bool tri_path(int N) { return N >= kTriMinN && N <= kTriMaxN; }
 cudaError_t launch_psd_tri(const DevPlan<double>& p, int bid, int N, const LargeScratch<double>& L, int grid,
                            cudaStream_t s);
+// one kernel of that path (profiling): 0 gather, 1 reduction, 2 eigenvectors,
+// 3 FP64 refinement and reconstruction
+cudaError_t launch_psd_tri_part(const DevPlan<double>& p, int bid, int N, const LargeScratch<double>& L, int grid,
+                                int part, cudaStream_t s);
 
 // Scratch of the Newton-Schulz projection (tensor cores) of one large block.
 struct NsScratch {
@@ -172,6 +177,12 @@ cudaError_t launch_psd_small(const DevPlan<T>& p, const int32_t* ids, int count,
 template <typename T, typename TC>
 cudaError_t launch_psd_large(const DevPlan<T>& p, int bid, int N, const LargeScratch<TC>& ls, int grid,
                              cudaStream_t s);
+// one kernel of the large-block projection (profiling): parts 0..3 the
+// tridiagonal path (FP64 form, kTriMinN <= N <= kTriMaxN), part 4 the grid
+// Jacobi kernel (which does nothing after a successful tridiagonal path)
+template <typename T, typename TC>
+cudaError_t launch_psd_large_part(const DevPlan<T>& p, int bid, int N, const LargeScratch<TC>& ls, int grid,
+                                  int part, cudaStream_t s);
 int large_grid_size(int N);
 template <typename T, typename TC>
 cudaError_t prepare_kernels(int max_small_n, int max_teff);

@@ -2,7 +2,6 @@
 // that must not allocate device memory.
 //
 // Who needs it: code that runs where cudaMalloc is unavailable or unsafe --
-// inside a region that is being captured into a CUDA graph by someone else,
 // under a memory pool or allocator that owns all device memory, in a
 // real-time loop that may not block on the allocator, or in a plugin whose
 // host forbids allocations after start-up.  Such callers pass only their

@@ -254,8 +254,125 @@ const char* program_error(const sos_program& pg) {
       if (bk.n_weight_terms < 0 || (bk.n_weight_terms > 0 && (!bk.weight_exps || !bk.weight_coef)))
         return "weight arrays missing";
     }
+    if (c.matrix_r < 0) return "matrix_r < 0";
+    if (c.matrix_r > 0) {
+      if (c.n_blocks != 1 || c.blocks[0].n_weight_terms != 0)
+        return "a matrix-valued constraint takes exactly one unweighted block";
+      if (c.n_terms > 0 && !c.term_pair) return "term_pair missing";
+      for (int64_t k = 0; k < c.n_terms; ++k) {
+        const int32_t a = c.term_pair[2 * k], b = c.term_pair[2 * k + 1];
+        if (a < 0 || a > b || b >= c.matrix_r) return "term_pair outside 0 <= i <= j < matrix_r";
+      }
+    }
   }
   return nullptr;
+}
+
+bool has_matrix(const sos_program& pg) {
+  for (int j = 0; j < pg.n_constraints; ++j)
+    if (pg.constraints[j].matrix_r > 0) return true;
+  return false;
+}
+
+// A program with matrix-valued constraints (Section V) as one with scalar
+// constraints only, in the variables (x, y_1..y_R), R the largest size:
+// the basis entry (i, a) of I_r (x) v becomes y_i x^a, the row triple
+// (alpha, i, j), i <= j, becomes y_i y_j x^alpha, and a term c x^e of entry
+// (i, j) of P_h becomes c' x^e y_i y_j with c' = c on the diagonal and 2 c
+// off it -- the coefficient of y_i y_j x^e in y^T P_h(x) y.  An entry (p, q)
+// of Y then meets row (alpha_p + alpha_q, i_p, i_q) through the same
+// exponent lookup as a scalar Gram entry (Prop. 2).  Scalar constraints get
+// zero exponents in y.
+struct MatrixForm {
+  std::vector<sos_constraint> cons;
+  std::deque<std::vector<sos_block>> blocks;
+  std::deque<std::vector<int32_t>> i32;
+  std::deque<std::vector<double>> f64;
+  sos_program prog{};
+};
+
+void to_scalar_form(const sos_program& pg, MatrixForm& F) {
+  const int n = pg.n_vars;
+  int R = 0;
+  for (int j = 0; j < pg.n_constraints; ++j) R = std::max(R, pg.constraints[j].matrix_r);
+  const int nv = n + R;
+  auto pad = [&](const int32_t* e, int64_t count) -> const int32_t* {
+    std::vector<int32_t> out(static_cast<size_t>(count) * nv, 0);
+    for (int64_t q = 0; q < count; ++q)
+      for (int a = 0; a < n; ++a) out[q * nv + a] = e[q * n + a];
+    F.i32.push_back(std::move(out));
+    return F.i32.back().data();
+  };
+  F.cons.assign(pg.constraints, pg.constraints + pg.n_constraints);
+  for (int j = 0; j < pg.n_constraints; ++j) {
+    const sos_constraint& c = pg.constraints[j];
+    sos_constraint& o = F.cons[j];
+    o.matrix_r = 0;
+    o.term_pair = nullptr;
+    if (c.matrix_r == 0) {
+      o.row_exps = pad(c.row_exps, c.n_rows);
+      o.term_exps = pad(c.term_exps, c.n_terms);
+      F.blocks.emplace_back(c.blocks, c.blocks + c.n_blocks);
+      for (auto& bk : F.blocks.back()) {
+        bk.basis_exps = pad(bk.basis_exps, bk.N);
+        if (bk.n_weight_terms > 0) bk.weight_exps = pad(bk.weight_exps, bk.n_weight_terms);
+      }
+      o.blocks = F.blocks.back().data();
+      continue;
+    }
+    const int r = c.matrix_r;
+    // rows: pairs i <= j row-major, then alpha
+    std::vector<int32_t> rows;
+    for (int i = 0; i < r; ++i)
+      for (int jj = i; jj < r; ++jj)
+        for (int32_t q = 0; q < c.n_rows; ++q) {
+          std::vector<int32_t> e(nv, 0);
+          for (int a = 0; a < n; ++a) e[a] = c.row_exps[static_cast<int64_t>(q) * n + a];
+          e[n + i] += 1;
+          e[n + jj] += 1;
+          rows.insert(rows.end(), e.begin(), e.end());
+        }
+    F.i32.push_back(std::move(rows));
+    o.row_exps = F.i32.back().data();
+    o.n_rows = c.n_rows * r * (r + 1) / 2;
+    // terms
+    std::vector<int32_t> tp(c.n_terms), te(static_cast<size_t>(c.n_terms) * nv, 0);
+    std::vector<double> tc(c.n_terms);
+    for (int64_t k = 0; k < c.n_terms; ++k) {
+      const int32_t i = c.term_pair[2 * k], jj = c.term_pair[2 * k + 1];
+      tp[k] = c.term_poly[k];
+      for (int a = 0; a < n; ++a) te[k * nv + a] = c.term_exps[k * n + a];
+      te[k * nv + n + i] += 1;
+      te[k * nv + n + jj] += 1;
+      tc[k] = (i == jj ? 1.0 : 2.0) * c.term_coef[k];
+    }
+    F.i32.push_back(std::move(tp));
+    o.term_poly = F.i32.back().data();
+    F.i32.push_back(std::move(te));
+    o.term_exps = F.i32.back().data();
+    F.f64.push_back(std::move(tc));
+    o.term_coef = F.f64.back().data();
+    // one block: y_i x^a, block-major
+    const sos_block& b0 = c.blocks[0];
+    std::vector<int32_t> bas(static_cast<size_t>(r) * b0.N * nv, 0);
+    for (int i = 0; i < r; ++i)
+      for (int a = 0; a < b0.N; ++a) {
+        int32_t* e = bas.data() + (static_cast<size_t>(i) * b0.N + a) * nv;
+        for (int v = 0; v < n; ++v) e[v] = b0.basis_exps[static_cast<int64_t>(a) * n + v];
+        e[n + i] = 1;
+      }
+    F.i32.push_back(std::move(bas));
+    sos_block nb{};
+    nb.N = r * b0.N;
+    nb.basis_exps = F.i32.back().data();
+    nb.n_weight_terms = 0;
+    F.blocks.emplace_back(1, nb);
+    o.blocks = F.blocks.back().data();
+    o.n_blocks = 1;
+  }
+  F.prog = pg;
+  F.prog.n_vars = nv;
+  F.prog.constraints = F.cons.data();
 }
 
 bool has_weighted(const sos_program& pg) {
@@ -615,13 +732,21 @@ int build_plan(const sos_program* progs, int32_t n_progs, HostPlan& P, std::stri
       for (int32_t i = static_cast<int32_t>(w); i < n_progs; i += static_cast<int32_t>(nth)) {
         if (const char* msg = program_error(progs[i])) {
           fail(loc[i], SOS_ERR_INVALID_ARG, msg);
-        } else if (choose_extra_form(progs[i], weighted_form)) {
+          continue;
+        }
+        MatrixForm MF;
+        const sos_program* pg = &progs[i];
+        if (has_matrix(*pg)) {
+          to_scalar_form(*pg, MF);
+          pg = &MF.prog;
+        }
+        if (choose_extra_form(*pg, weighted_form)) {
           ExtraForm F;
-          to_extra_form(progs[i], F);
+          to_extra_form(*pg, F);
           build_instance(F.prog, loc[i], inner);
           loc[i].extra_form = 1;
         } else {
-          build_instance(progs[i], loc[i], inner);
+          build_instance(*pg, loc[i], inner);
         }
       }
     });

@@ -51,6 +51,26 @@ def test_persistent_fp64_iterates_match_oracle(capi):
     s.close()
 
 
+def test_persistent_fp64_iterates_full_size_blocks(capi):
+    """The largest blocks of the 4096-search batch (n = 5, 6: Gram blocks of
+    21/56 and 28/84, the 512-thread size classes) through the persistent
+    launch: FP64 iterates within 1e-9 of the oracle."""
+    iters = 40
+    progs = W.lyapunov_batch(4, seed=3, n_min=5, n_max=6)
+    assert {max(b.size(p.n) for c in p.constraints for b in c.blocks) for p in progs} == {56, 84}
+    s = capi.Solver(progs, precision=capi.PREC_FP64, solve_mode=2)
+    assert s.tuning()["persistent"] == 1
+    s.iterate(iters)
+    s.sync()
+    ug, vg = s.get_iterate()
+    for (xg, yg, tg), (zg, sg, kg), prog in zip(s.split(ug), s.split(vg), progs):
+        hs = admm.HSDE(conic.build(prog))
+        uo, vo = _packed(prog, *hs.run(iters))
+        assert _rel(np.concatenate([xg, yg, [tg]]), uo) < 1e-9
+        assert _rel(np.concatenate([zg, sg, [kg]]), vo) < 1e-9
+    s.close()
+
+
 def test_persistent_solve_matches_kernel_path(capi):
     """Same iterates, same checks: statuses, iteration counts and objectives of
     the device-side termination equal the host-side loop of the per-phase path."""

@@ -112,6 +112,20 @@ def test_fp64_large_block_config1(capi):
     assert rel(vg, vo) < 1e-9, rel(vg, vo)
 
 
+def test_fp64_config1_solve_to_1e6(capi):
+    """Constrained quartic POP n = 20 (Gram 231 + weighted 21) solved to a
+    1e-6 residual: the same number of iterations as the oracle (same checks
+    every 10 iterations) and the objective within 1e-6 relative."""
+    prog = W.ball_pop(20, 0)
+    ro = admm.solve(conic.build(prog), 1e-6, 5000, k_check=10)
+    s = capi.Solver(prog, precision=capi.PREC_FP64, k_check=10)
+    r = s.solve(1e-6, 5000, want_solution=False)[0]
+    s.close()
+    assert r["status"] == capi.SOLVED and ro.status == admm.SOLVED
+    assert r["iters"] == ro.iters, (r["iters"], ro.iters)
+    assert abs(r["obj_primal"] - ro.res["pobj"]) <= 1e-6 * abs(ro.res["pobj"])
+
+
 def test_fp64_solve_objective_and_status(capi):
     prog = W.quartic_pop(6, 0)
     cd = conic.build(prog)

@@ -125,12 +125,19 @@ def test_mixed_projection_admm_like_spectrum(env, N):
     assert np.abs(project_gpu_mixed(env, np.zeros((N, N)))).max() == 0.0
 
 
-def test_mixed_projection_rejects_large_block(env):
+def test_mixed_projection_rejects_oversize_block(env):
+    # above MIXED_MAX_N the Newton-Schulz kernel takes the block; it needs
+    # one CTA per 128 x 64 lower tile of the padded matrix, all resident, so
+    # an N whose tiles outnumber the SMs is refused before any allocation
     torch, capi = env
-    N = capi.MIXED_MAX_N + 1
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nti = 1
+    while (nti + 1) * (nti + 2) <= sms:
+        nti += 1
+    N = 128 * nti + 1  # nti + 1 row tiles: (nti + 1)(nti + 2) CTAs > sms
     w = torch.zeros(N * (N + 1) // 2, dtype=torch.float64, device="cuda")
     u = torch.empty_like(w)
-    with pytest.raises(RuntimeError):
+    with pytest.raises(RuntimeError, match="unsupported|SMs|UNSUPPORTED"):
         capi.psd_project_mixed(w.data_ptr(), u.data_ptr(), N)
 
 

@@ -1,11 +1,12 @@
 """The allocation-free projection entry point (sos_psd_project_noalloc).
 
-It exists for callers that cannot call cudaMalloc -- e.g. code running while
-a stream is being captured into a CUDA graph, or code whose device memory is
-owned by a pool it may not bypass.  It must give the same result as the
-allocating entry point (sos_psd_project) on the same input, on consecutive
-calls that share its fixed scratch array, on both the shared-memory path and
-the grid path, and it must reject sizes above its fixed maximum.
+It exists for callers that cannot call cudaMalloc -- e.g. code whose device
+memory is owned by a pool it may not bypass, or a plugin whose host forbids
+allocations after start-up.  It must give the same result as the allocating
+entry point (sos_psd_project) on the same input, on consecutive calls that
+share its fixed scratch array, on the shared-memory path, the tridiagonal
+path and the grid path, agree with the oracle's eigen-clamp, and reject
+sizes above its fixed maximum.
 
 This file sorts last so that a run stopping at the first failure has already
 run every other test; it also passes on its own in a fresh process.
@@ -15,6 +16,8 @@ import os
 
 import numpy as np
 import pytest
+
+from oracle.admm import proj_psd
 
 pytestmark = pytest.mark.gpu
 
@@ -58,6 +61,8 @@ def test_noalloc_matches_allocating_entry_point_twice(env, N):
         torch.cuda.synchronize()
         diff = (got - ref).abs().max().item()
         assert diff <= 1e-12 * max(1.0, float(np.abs(X).max())) * N, (call, diff)
+        err = np.abs(got.cpu().numpy() - _pack(proj_psd(X))).max()
+        assert err <= 1e-12 * max(1.0, float(np.abs(X).max())) * N, (call, err)
         assert torch.equal(w, torch.tensor(_pack(X), dtype=torch.float64, device="cuda"))  # input untouched
 
 
