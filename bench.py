@@ -224,20 +224,23 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def warmstart_arm(args):
+def measure_warmstart(args, n_train: int, n_test: int, epochs: int, full: bool):
     """Learned warm start (parametric quartic POP, n = 10, Gram 66, m = 1001):
-    time to a 1e-4 residual per instance for 1024 unseen members, batched with
-    FP32 projections and started from the network's prediction, against the
-    same batch from a cold start and against the plain FP64 form one instance
-    at a time (sample)."""
+    time to a 1e-4 residual for unseen members, batched, in three forms on
+    the SAME members: plain FP64 batched from the cold start, FP32
+    projections batched from the cold start, and FP32 projections batched
+    from the network's prediction.  The network is trained on n_train
+    members solved to args.train_tol by the batched solver.  ``full`` adds
+    the starts at the exact and at a noisy solution (what a better predictor
+    could gain) and the plain FP64 form one instance at a time (sample)."""
     import torch
 
     from instances import workloads as W
     from paper_1708_04174_gb300 import capi, warmstart
 
     fam = W.ParametricPOP(n=10, K=16, seed=0)
-    th_train = W.ParametricPOP.thetas(args.train, 100)
-    th_test = W.ParametricPOP.thetas(1024, 200)
+    th_train = W.ParametricPOP.thetas(n_train, 100)
+    th_test = W.ParametricPOP.thetas(n_test, 200)
     ws = warmstart.WarmStart(fam, hidden=512, seed=0)
     t0 = time.perf_counter()
     mi = args.max_iter
@@ -247,71 +250,81 @@ def warmstart_arm(args):
         raise RuntimeError(f"no training member reached {args.train_tol} within {mi} iterations")
     targets = warmstart.solution_vectors([r for r, k in zip(res, ok) if k], [d for d, k in zip(dims, ok) if k])
     t_data = time.perf_counter() - t0
-    losses = ws.train(th_train[ok], targets, epochs=args.epochs, batch=256, lr=1e-3)
+    losses = ws.train(th_train[ok], targets, epochs=epochs, batch=256, lr=1e-3)
     pred = ws.predict(th_test)
     torch.cuda.synchronize()
     warm, _, t_warm, _ = ws.solve(th_test, 1e-4, mi, start=pred)
     cold, _, t_cold, _ = ws.solve(th_test, 1e-4, mi)
-    it_w = np.array([r["iters"] for r in warm])
-    it_c = np.array([r["iters"] for r in cold])
-    # accuracy of the prediction against the cold-start solutions
     sol_c = warmstart.solution_vectors(cold, ws.last_dims)
+    fp64, _, t_fp64, _ = ws.solve(th_test, 1e-4, mi, precision=capi.PREC_FP64)
+
+    def summary(rs, secs):
+        it = np.array([r["iters"] for r in rs])
+        return {"seconds": secs, "per_instance_s": secs / n_test, "iters_mean": float(it.mean()),
+                "iters_median": float(np.median(it)), "iters_max": int(it.max()),
+                "solved": int(sum(r["status"] == capi.SOLVED for r in rs))}
+
+    def obj_diff(xs, ys):
+        d = np.array([abs(a["obj_primal"] - b["obj_primal"]) / max(1.0, abs(b["obj_primal"]))
+                      for a, b in zip(xs, ys) if a["status"] == capi.SOLVED and b["status"] == capi.SOLVED])
+        return {"max": float(d.max()) if d.size else None, "median": float(np.median(d)) if d.size else None,
+                "members": int(d.size)}
+
     pred_err = np.linalg.norm(pred - sol_c, axis=1) / np.maximum(np.linalg.norm(sol_c, axis=1), 1e-30)
-    # what a better predictor could gain: starts at the cold-start solution
-    # itself and at that solution with 5% relative Gaussian noise
-    rng = np.random.default_rng(0)
-    noisy = sol_c + 0.05 * np.linalg.norm(sol_c, axis=1, keepdims=True) / np.sqrt(sol_c.shape[1]) * \
-        rng.standard_normal(sol_c.shape)
-    bounds = {}
-    for name, start in (("exact_solution", sol_c), ("solution_5pct_noise", noisy)):
-        rb, _, tb, _ = ws.solve(th_test, 1e-4, mi, start=start.astype(np.float32))
-        ib = np.array([r["iters"] for r in rb])
-        bounds[name] = {"seconds": tb, "iters_mean": float(ib.mean()), "iters_median": float(np.median(ib)),
-                        "solved": int(sum(r["status"] == capi.SOLVED for r in rb))}
-    # plain FP64 form, one instance at a time, on a sample of the same test set
-    sample = list(range(0, 1024, 256))
-    t_plain = 0.0
-    it_plain = []
-    for i in sample:
-        s = capi.Solver(fam.program(th_test[i]), precision=capi.PREC_FP64, k_check=10)
-        t1 = time.perf_counter()
-        r = s.solve(1e-4, mi, want_solution=False)[0]
-        t_plain += time.perf_counter() - t1
-        it_plain.append(r["iters"])
-        s.close()
-    per_plain = t_plain / len(sample)
-    per_warm = t_warm / 1024
-    obj_err = np.array([abs(a["obj_primal"] - b["obj_primal"]) / max(1.0, abs(b["obj_primal"]))
-                        for a, b in zip(warm, cold)
-                        if a["status"] == capi.SOLVED and b["status"] == capi.SOLVED])  # members solved by both
+    out = {"config": {"family": "p0 + sum_k theta_k q_k, n=10, K=16, Gram 66, m=1001", "train": int(n_train),
+                      "test": int(n_test), "mlp": "16-512-512-5425", "epochs": int(epochs),
+                      "train_tol": args.train_tol, "max_iter": mi},
+           "plain_fp64_batched": summary(fp64, t_fp64),
+           "mixed_batched_cold": summary(cold, t_cold),
+           "mixed_batched_warm": summary(warm, t_warm),
+           "speedup_warm_mixed_vs_plain_fp64_batched": t_fp64 / t_warm,
+           "speedup_cold_mixed_vs_plain_fp64_batched": t_fp64 / t_cold,
+           "speedup_warm_vs_cold_mixed": t_cold / t_warm,
+           "objective_rel_diff": {"warm_vs_fp64": obj_diff(warm, fp64), "cold_vs_fp64": obj_diff(cold, fp64)},
+           "prediction_rel_err": {"median": float(np.median(pred_err)), "p90": float(np.percentile(pred_err, 90))},
+           "training": {"data_seconds": t_data, "solve_seconds": t_solve_train, "solved": int(ok.sum()),
+                        "iters_mean": float(np.mean([r["iters"] for r in res])),
+                        "train_seconds": ws.log["train_seconds"], "loss_first": losses[0], "loss_last": losses[-1]},
+           "tuning": tune}
+    if full:
+        # what a better predictor could gain: starts at the cold-start solution
+        # itself and at that solution with 5% relative Gaussian noise
+        rng = np.random.default_rng(0)
+        noisy = sol_c + 0.05 * np.linalg.norm(sol_c, axis=1, keepdims=True) / np.sqrt(sol_c.shape[1]) * \
+            rng.standard_normal(sol_c.shape)
+        bounds = {}
+        for name, start in (("exact_solution", sol_c), ("solution_5pct_noise", noisy)):
+            rb, _, tb, _ = ws.solve(th_test, 1e-4, mi, start=start.astype(np.float32))
+            bounds[name] = summary(rb, tb)
+        out["start_bounds"] = bounds
+        # plain FP64 form, one instance at a time, on a sample of the same members
+        sample = list(range(0, n_test, max(1, n_test // 4)))
+        t_plain = 0.0
+        it_plain = []
+        for i in sample:
+            s = capi.Solver(fam.program(th_test[i]), precision=capi.PREC_FP64, k_check=10)
+            t1 = time.perf_counter()
+            r = s.solve(1e-4, mi, want_solution=False)[0]
+            t_plain += time.perf_counter() - t1
+            it_plain.append(r["iters"])
+            s.close()
+        out["plain_fp64_single"] = {"seconds_per_instance": t_plain / len(sample),
+                                    "iters_mean": float(np.mean(it_plain)), "sample": len(sample)}
+    return out
+
+
+def warmstart_arm(args):
+    r = measure_warmstart(args, args.train, 1024, args.epochs, full=True)
+    warm = r["mixed_batched_warm"]
     line = {"metric": "time to a 1e-4 residual per instance (learned warm start + FP32 projections + batched)",
-            "value": per_warm, "unit": "s/instance", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "value": warm["per_instance_s"], "unit": "s/instance", "n_gpus": 1, "steps": 1, "warmup": 0,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64 iterates, f32 proj",
-            "data": "synthetic",
-            "config": {"workload": "parametric_warmstart", "family": "p0 + sum_k theta_k q_k, n=10, K=16, Gram 66, m=1001",
-                       "train": int(args.train), "test": 1024, "mlp": "16-512-512-5425", "epochs": args.epochs},
-            "speedup_vs_plain_fp64": per_plain / per_warm,
-            "speedup_vs_cold_batched": t_cold / t_warm,
-            "warm": {"seconds": t_warm, "iters_mean": float(it_w.mean()), "iters_median": float(np.median(it_w)),
-                     "iters_max": int(it_w.max()),
-                     "solved": int(sum(r["status"] == capi.SOLVED for r in warm))},
-            "cold_batched": {"seconds": t_cold, "iters_mean": float(it_c.mean()), "iters_median": float(np.median(it_c)),
-                             "iters_max": int(it_c.max()),
-                             "solved": int(sum(r["status"] == capi.SOLVED for r in cold))},
-            "plain_fp64_single": {"seconds_per_instance": per_plain, "iters_mean": float(np.mean(it_plain)),
-                                  "sample": len(sample)},
-            "objective_rel_diff_warm_vs_cold": {"max": float(obj_err.max()), "median": float(np.median(obj_err))},
-            "prediction_rel_err": {"median": float(np.median(pred_err)), "p90": float(np.percentile(pred_err, 90))},
-            "start_bounds": bounds,
-            "training": {"data_seconds": t_data, "solve_seconds": t_solve_train, "solved": int(ok.sum()),
-                         "tol": args.train_tol,
-                         "iters_mean": float(np.mean([r["iters"] for r in res])),
-                         "train_seconds": ws.log["train_seconds"], "loss_first": losses[0], "loss_last": losses[-1]},
-            "tuning": tune}
+            "data": "synthetic", "config": dict(workload="parametric_warmstart", **r.pop("config"))}
+    line.update(r)
     print(json.dumps(line), flush=True)
 
 
-def batched_arm(args):
+def measure_batch(args, steps: int, with_tt: bool, with_cpu: bool):
     """Batched form: 4096 cubic Lyapunov searches (n uniform in 2..6, Gram
     blocks 3x3 .. 84x84) advanced together.  One step = one ADMM iteration of
     every instance.  Mixed form (FP64 iterates, Woodbury and residuals; FP32
@@ -354,9 +367,9 @@ def batched_arm(args):
     clk = ClockSampler(os.path.join(clock_dir(), "clocks_rank0.csv"))
     torch.cuda.synchronize()
     with clk:
-        step_ms = timed(s, lambda: s.iterate(1), args.steps)
+        step_ms = timed(s, lambda: s.iterate(1), steps)
     total_ms = float(np.sum(step_ms))
-    ips = args.steps / (total_ms / 1e3)
+    ips = steps / (total_ms / 1e3)
     stage_ms = {name: float(np.mean(timed(s, lambda st=st: s.run_stage(st), 5)))
                 for st, name in ((0, "affine"), (1, "psd_small"))}
     dims = s.dims
@@ -394,7 +407,7 @@ def batched_arm(args):
 
     # time to a 1e-4 residual for the whole batch, from the cold start
     tt = None
-    if not args.no_tt:
+    if with_tt:
         sm = capi.Solver(progs, precision=capi.PREC_MIXED, k_check=10)
         t0 = time.perf_counter()
         res = sm.solve(1e-4, args.max_iter, want_solution=False)
@@ -422,7 +435,7 @@ def batched_arm(args):
     s64.close()
 
     cpu = None
-    if not args.no_cpu_baseline:
+    if with_cpu:
         # the oracle, as it stands, on a sample of the batch (one instance at a time)
         tot_k, tot_t, used = 0, 0.0, 0
         for prog in progs[::256]:
@@ -436,8 +449,8 @@ def batched_arm(args):
                          f"batch iterations/s = instance-iterations/s / {count}"}
 
     line = {"metric": "ADMM iterations/s of the whole batch (one iteration of all 4096 instances)",
-            "value": ips, "unit": "iter/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "value": ips, "unit": "iter/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 iterates, f32 proj", "data": "synthetic",
             "config": {"workload": "lyapunov_batch4096",
                        "desc": "4096 cubic Lyapunov searches, n uniform in 2..6, V degree 2..4, eps 1e-3; "
@@ -450,10 +463,14 @@ def batched_arm(args):
             "hbm_kernels_fp64": {"peak_gbs": hbm, "peak_source": pk_kind, "kernels": hbm_kernels},
             "fp64_form": {"ms_per_step": fp64_ms, "value": 1e3 / fp64_ms, "unit": "iter/s"},
             "time_to_1e-4": tt, "tuning": tuning,
-            "gpu_launches": int(launches * args.steps), "clocks": clk.summary(0)}
+            "gpu_launches": int(launches * steps), "clocks": clk.summary(0)}
     if cpu is not None:
         line["cpu_baseline"] = cpu
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def batched_arm(args):
+    print(json.dumps(measure_batch(args, args.steps, not args.no_tt, not args.no_cpu_baseline)), flush=True)
 
 
 # Published numbers for the constrained POP of eq. (46) (context only: a
@@ -576,6 +593,11 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tt", action="store_true", help="skip the time-to-1e-4 solves")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batch and warm-start keys of the default line")
+    ap.add_argument("--extras-train", type=int, default=4096, help="training members of the warm-start key")
+    ap.add_argument("--extras-test", type=int, default=256, help="unseen members of the warm-start key")
+    ap.add_argument("--extras-epochs", type=int, default=100, help="epochs of the warm-start key")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -805,9 +827,29 @@ def main():
         out["cpu_baseline"] = {"value": k / dt, "unit": "iter/s", "cores": cpu_cores(), "kind": "oracle",
                                "sample": f"{k} ADMM iterations of the FP64 NumPy/SciPy oracle on the same "
                                          f"instance (about 15 s), BLAS threads at their default"}
+    if world == 1 and not args.no_extras and args.workload == "ball_pop_n20":
+        # The targets of the other forms as extra keys of the headline line
+        # (one GPU only): the 4096-search batch (rate of the mixed and plain
+        # FP64 forms, HBM fraction of each FP64 affine kernel, short runs),
+        # and time to 1e-4 on the same unseen parametric members for plain
+        # FP64 batched, mixed batched cold and mixed batched warm (training
+        # set, test set and epochs scaled down from the full arm to keep the
+        # default run within minutes; stated in its config).
+        solver.close()
+        solver = None
+        b = measure_batch(args, 10, with_tt=False, with_cpu=False)
+        out["batch_lyapunov4096"] = {
+            "value": b["value"], "unit": "batch iter/s", "steps": 10,
+            "instance_iters_per_s": b["instance_iters_per_s"], "form": b["config"]["form"],
+            "ms_per_step": b["ms_per_step"], "fp64_form": b["fp64_form"],
+            "hbm_kernels_fp64": b["hbm_kernels_fp64"], "setup_s": b["config"]["setup_s"],
+            "roofline_psd_small": {k: b["roofline"][k] for k in ("kernel", "achieved", "peak", "unit", "frac")}}
+        out["warmstart_parametric"] = measure_warmstart(args, args.extras_train, args.extras_test,
+                                                        args.extras_epochs, full=False)
     if rank == 0:
         print(json.dumps(out), flush=True)
-    solver.close()
+    if solver is not None:
+        solver.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -152,7 +152,7 @@ struct Common {
   const int32_t* lr_sl_col;
   const double* lr_sl_val;
   double* wl;
-  double *tau, *kappa, *xP, *ylr, *zlr, *sig2, *ra, *atyl;
+  double *tau, *kappa, *xP, *ylr, *zlr, *wq, *sig2, *ra, *atyl;
   int32_t* err;
   int32_t* blk_sweeps;
 };
@@ -209,6 +209,7 @@ int make_devplan(sos_handle* h, const Common& c, int32_t max_teff, DevPlan<T>& p
   p.xP = c.xP;
   p.ylr = c.ylr;
   p.zlr = c.zlr;
+  p.wq = c.wq;
   p.sig2 = c.sig2;
   p.ra = c.ra;
   p.atyl = c.atyl;
@@ -452,7 +453,9 @@ int autotune_persistent(sos_handle* h) {
 // projection (after one affine step from the cold start, so the input is a
 // realistic W) for 1/4, 1/2 and all SMs, keeps the fastest, and resets the
 // iterate.  Fewer CTAs make each grid barrier cheaper; more give more FP64
-// and FP32 throughput per round.
+// and FP32 throughput per round.  FP64 blocks on the tridiagonal path take
+// every SM without a trial: there the grid only sizes the tile products of
+// the refinement and reconstruction, which divide evenly over the CTAs.
 template <typename TC>
 int autotune_large(sos_handle* h, std::vector<LargeBlock<TC>>& large) {
   if (large.empty()) return SOS_OK;
@@ -465,6 +468,11 @@ int autotune_large(sos_handle* h, std::vector<LargeBlock<TC>>& large) {
   for (auto& lb : large) {
     float best = 1e30f;
     int best_g = sms;
+    if (sizeof(TC) == 8 && tri_path(lb.N)) {
+      lb.grid = sms;
+      h->large_grid_best = sms;
+      continue;
+    }
     for (int g : cands) {
       if (g < 1) continue;
       lb.grid = g;
@@ -735,6 +743,7 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   TRY(alloc(h, h->M, &c.xP));
   TRY(alloc(h, h->TL, &c.ylr));
   TRY(alloc(h, h->TL, &c.zlr));
+  TRY(alloc(h, h->TL, &c.wq));
   TRY(alloc(h, h->M, &c.sig2));
   TRY(alloc(h, h->M, &c.ra));
   TRY(alloc(h, h->TL, &c.atyl));
@@ -1461,9 +1470,13 @@ int sos_set_wait_limit(sos_handle* h, int32_t us) {
 int sos_launches_per_iteration(const sos_handle* h) {
   if (!h) return SOS_ERR_INVALID_ARG;
   if (h->persistent) return 0;  // one launch for all iterations of a call
-  const int affine = h->TL > 0 ? 6 : 4;
-  return affine + static_cast<int>(h->small.size()) +
-         static_cast<int>(h->large64.size() + h->large32.size() + h->ns_large.size());
+  const int teff = h->precision == SOS_PREC_FP32 ? h->d32.max_teff : h->d64.max_teff;
+  int affine = h->TL > 0 ? 6 : 4;
+  if (h->TL > 0 && woodbury_wide(h->n_inst, teff)) affine += 1;
+  int large = 0;
+  for (const auto& lb : h->large64) large += tri_path(lb.N) ? 5 : 1;  // gather, reduce, vectors, recon, Jacobi
+  return affine + static_cast<int>(h->small.size()) + large +
+         static_cast<int>(h->large32.size() + h->ns_large.size());
 }
 
 void* sos_stream(sos_handle* h) { return h ? static_cast<void*>(h->stream) : nullptr; }

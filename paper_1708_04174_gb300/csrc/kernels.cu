@@ -133,6 +133,55 @@ __global__ void k_woodbury(DevPlan<T> p) {
   d_woodbury(p, blockIdx.x, shw);
 }
 
+// The same two triangular products for a single instance with a wide core,
+// spread over the GPU: every row of L^{-1} (first pass) or of L^{-T} (second
+// pass, the rows of the column-major copy) is one warp's dot product, its
+// lanes striding along the row (coalesced) with four independent partial
+// sums, then a warp reduction.  The first pass writes q = L^{-1} y to wq.
+template <typename T>
+__global__ void __launch_bounds__(256) k_woodbury_wide(DevPlan<T> p, int pass) {
+  if (!p.active[0]) return;
+  const InstInfo in = p.inst[0];
+  const int te = in.t_eff;
+  const int lane = threadIdx.x & 31;
+  const int nw = static_cast<int>((static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5);
+  const double* x = (pass == 0 ? p.ylr : p.wq) + in.lr_off;
+  for (int r = static_cast<int>((static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); r < te;
+       r += nw) {
+    // pass 0: sum_{k <= r} Li[r][k] y[k]; pass 1: sum_{k >= r} Li[k][r] q[k] = sum_k Lt[r][k] q[k]
+    const double* row = (pass == 0 ? p.linv : p.linv_t) + in.linv_off + static_cast<int64_t>(r) * te;
+    const int k0 = pass == 0 ? 0 : r, k1 = pass == 0 ? r + 1 : te;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int k = k0 + lane;
+    for (; k + 96 < k1; k += 128) {
+      a0 = fma(row[k], x[k], a0);
+      a1 = fma(row[k + 32], x[k + 32], a1);
+      a2 = fma(row[k + 64], x[k + 64], a2);
+      a3 = fma(row[k + 96], x[k + 96], a3);
+    }
+    for (; k < k1; k += 32) a0 = fma(row[k], x[k], a0);
+    const double acc = warp_sum((a0 + a1) + (a2 + a3));
+    if (lane == 0) {
+      if (pass == 0)
+        p.wq[in.lr_off + r] = acc;
+      else
+        p.zlr[in.lr_off + r] = acc;
+    }
+  }
+}
+
+template <typename T>
+void launch_woodbury(const DevPlan<T>& p, cudaStream_t s) {
+  if (woodbury_wide(p.n_inst, p.max_teff)) {
+    const int grid = (p.max_teff + 7) / 8;  // one warp per row
+    k_woodbury_wide<T><<<grid, 256, 0, s>>>(p, 0);
+    k_woodbury_wide<T><<<grid, 256, 0, s>>>(p, 1);
+    return;
+  }
+  const size_t wsm = sizeof(double) * 2 * static_cast<size_t>(p.max_teff > 0 ? p.max_teff : 1);
+  k_woodbury<T><<<p.n_inst, 256, wsm, s>>>(p);
+}
+
 template <typename T>
 __device__ void d_rows_sigma2(const DevPlan<T>& p, int64_t g0, int64_t stride) {
   for (int64_t a = g0; a < p.M; a += stride) {  // rows advance in whole warps
@@ -161,6 +210,7 @@ __device__ void d_inst_scalar(const DevPlan<T>& p, int i) {
   const double tau = p.tau[i], kappa = p.kappa[i];
   const double om3 = tau + kappa;
   double bs = 0.0;
+#pragma unroll 4
   for (int a = threadIdx.x; a < in.m; a += blockDim.x) bs += p.b[in.y_off + a] * p.sig2[in.y_off + a];
   const double bsig2 = block_sum(bs, sh);
   double cs = 0.0;
@@ -195,8 +245,14 @@ __device__ void d_inst_scalar(const DevPlan<T>& p, int i) {
 }
 
 template <typename T>
-__global__ void k_inst_scalar(DevPlan<T> p) {
+__global__ void __launch_bounds__(1024) k_inst_scalar(DevPlan<T> p) {
   d_inst_scalar(p, blockIdx.x);
+}
+
+// A single instance gets a whole 1024-thread CTA for its reductions over m.
+template <typename T>
+int inst_scalar_threads(const DevPlan<T>& p, const LaunchShape& ls) {
+  return p.n_inst == 1 ? 1024 : ls.inst_threads;
 }
 
 template <typename T>
@@ -1597,11 +1653,10 @@ cudaError_t launch_affine(const DevPlan<T>& p, const LaunchShape& ls, cudaStream
   k_rows_r<T><<<grid_for(p.M, rt, ls.sms), rt, 0, s>>>(p);
   if (p.TL > 0) {
     k_lr_y<T><<<grid_for(static_cast<int64_t>(p.TL) * 32, 256, ls.sms), 256, 0, s>>>(p);
-    const size_t wsm = sizeof(double) * 2 * static_cast<size_t>(p.max_teff > 0 ? p.max_teff : 1);
-    k_woodbury<T><<<p.n_inst, 256, wsm, s>>>(p);
+    launch_woodbury(p, s);
   }
   k_rows_sigma2<T><<<grid_for(p.M, rt, ls.sms), rt, 0, s>>>(p);
-  k_inst_scalar<T><<<p.n_inst, ls.inst_threads, 0, s>>>(p);
+  k_inst_scalar<T><<<p.n_inst, inst_scalar_threads(p, ls), 0, s>>>(p);
   k_rows_y<T><<<grid_for(p.M, rt, ls.sms), rt, 0, s>>>(p);
   return cudaGetLastError();
 }
@@ -1634,16 +1689,13 @@ cudaError_t launch_affine_part(const DevPlan<T>& p, const LaunchShape& ls, int p
       if (p.TL > 0) k_lr_y<T><<<grid_for(static_cast<int64_t>(p.TL) * 32, 256, ls.sms), 256, 0, s>>>(p);
       break;
     case 2:
-      if (p.TL > 0) {
-        const size_t wsm = sizeof(double) * 2 * static_cast<size_t>(p.max_teff > 0 ? p.max_teff : 1);
-        k_woodbury<T><<<p.n_inst, 256, wsm, s>>>(p);
-      }
+      if (p.TL > 0) launch_woodbury(p, s);
       break;
     case 3:
       k_rows_sigma2<T><<<grid_for(p.M, rt, ls.sms), rt, 0, s>>>(p);
       break;
     case 4:
-      k_inst_scalar<T><<<p.n_inst, ls.inst_threads, 0, s>>>(p);
+      k_inst_scalar<T><<<p.n_inst, inst_scalar_threads(p, ls), 0, s>>>(p);
       break;
     case 5:
       k_rows_y<T><<<grid_for(p.M, rt, ls.sms), rt, 0, s>>>(p);

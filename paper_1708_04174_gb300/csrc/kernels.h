@@ -63,6 +63,7 @@ struct DevPlan {
   double* xP = nullptr;    // P^{-1} r (M)
   double* ylr = nullptr;   // A_L^T P^{-1} r (TL)
   double* zlr = nullptr;   // core^{-1} ylr (TL)
+  double* wq = nullptr;    // L^{-1} ylr of a single wide instance (TL)
   double* sig2 = nullptr;  // sigma_2 (M)
   T* uh2 = nullptr;        // u_hat_2 (M)
   double* ra = nullptr;    // residual work (M)
@@ -163,6 +164,9 @@ struct LaunchShape {
 
 template <typename T>
 cudaError_t launch_affine(const DevPlan<T>& p, const LaunchShape& ls, cudaStream_t s);
+// A single instance whose Woodbury core is at least 64 wide applies it with
+// two launches spread over the GPU (one warp per row) instead of one CTA.
+inline bool woodbury_wide(int n_inst, int max_teff) { return n_inst == 1 && max_teff >= 64; }
 // w1_hat on the low-rank columns from the stored iterate (after a start or
 // sos_set_iterate; during the iteration the producers of u and v write it)
 template <typename T>

@@ -60,10 +60,12 @@ class WarmStart:
         self.log = {}
         self.last_dims = None
 
-    def solve(self, thetas: np.ndarray, tol: float, max_iter: int, start=None):
-        """Batched solve of the members for ``thetas``; returns results and dims."""
+    def solve(self, thetas: np.ndarray, tol: float, max_iter: int, start=None, precision=None):
+        """Batched solve of the members for ``thetas`` (in this object's
+        precision form unless ``precision`` is given); returns results and dims."""
         progs = self.family.programs(thetas)
-        s = capi.Solver(progs, precision=self.precision, k_check=self.k_check)
+        prec = self.precision if precision is None else precision
+        s = capi.Solver(progs, precision=prec, k_check=self.k_check)
         if start is not None:
             s.set_iterate(*start_points(start, s.dims))
         t0 = time.perf_counter()
