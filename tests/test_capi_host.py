@@ -232,3 +232,58 @@ def test_setup_rejects_bad_options(capi, kw, msg):
     # option checks run before any CUDA call, so they need no GPU
     with pytest.raises(RuntimeError, match=msg):
         capi.Solver(W.quartic_pop(3, 0), **kw)
+
+
+def test_native_matrix_constraint_rows_by_hand(capi):
+    """A matrix-valued constraint (Section V) built directly in the C structs,
+    with literal arrays only -- no coefficient arithmetic on the Python side:
+    P_0(x) - u P_1 = (I_2 (x) v)^T Y (I_2 (x) v), P_0 = [[1 + x^2, x], [x, 2]],
+    P_1 = I, v = (1, x).  Prop. 2 rows (alpha, i, j), i <= j, pairs row-major
+    then alpha in (1, x, x^2): b holds (P_0)_ii and 2 (P_0)_01 (both Y_01 and
+    Y_10 enter the same row); P = I + A_D A_D^T counts every packed Gram
+    entry of a row once, with weight 1 on the diagonal of Y and 2 off it."""
+    import ctypes as C
+
+    row_exps = (C.c_int32 * 3)(0, 1, 2)
+    # terms: (poly, exponent, coefficient, pair)
+    term_poly = (C.c_int32 * 6)(0, 0, 0, 0, 1, 1)
+    term_exps = (C.c_int32 * 6)(0, 2, 1, 0, 0, 0)
+    term_coef = (C.c_double * 6)(1.0, 1.0, 1.0, 2.0, 1.0, 1.0)
+    term_pair = (C.c_int32 * 12)(0, 0, 0, 0, 0, 1, 1, 1, 0, 0, 1, 1)
+    basis_exps = (C.c_int32 * 2)(0, 1)
+    blk = (capi.sos_block * 1)()
+    blk[0].N = 2
+    blk[0].basis_exps = C.cast(basis_exps, C.POINTER(C.c_int32))
+    blk[0].n_weight_terms = 0
+    con = (capi.sos_constraint * 1)()
+    con[0].n_rows = 3
+    con[0].row_exps = C.cast(row_exps, C.POINTER(C.c_int32))
+    con[0].n_terms = 6
+    con[0].term_poly = C.cast(term_poly, C.POINTER(C.c_int32))
+    con[0].term_exps = C.cast(term_exps, C.POINTER(C.c_int32))
+    con[0].term_coef = C.cast(term_coef, C.POINTER(C.c_double))
+    con[0].n_blocks = 1
+    con[0].blocks = blk
+    con[0].matrix_r = 2
+    con[0].term_pair = C.cast(term_pair, C.POINTER(C.c_int32))
+    w = (C.c_double * 1)(-1.0)
+    prog = (capi.sos_program * 1)()
+    prog[0].n_vars = 1
+    prog[0].t = 1
+    prog[0].w = C.cast(w, C.POINTER(C.c_double))
+    prog[0].n_constraints = 1
+    prog[0].constraints = con
+    lib = capi.lib()
+    dims = (C.c_int64 * 6)()
+    assert lib.sos_host_plan(prog, 1, dims, None, None, None, None) == capi.SOS_OK
+    assert (dims[0], dims[1]) == (1 + 10, 9)  # u, then the packed 4 x 4 Y; 3 pairs x 3 monomials
+    ent = np.zeros(dims[0], dtype=np.int32)
+    pd = np.zeros(dims[1])
+    b = np.zeros(dims[1])
+    zh = C.c_double(0)
+    assert lib.sos_host_plan(prog, 1, dims, ent.ctypes.data_as(C.POINTER(C.c_int32)),
+                             pd.ctypes.data_as(C.POINTER(C.c_double)), b.ctypes.data_as(C.POINTER(C.c_double)),
+                             C.byref(zh)) == capi.SOS_OK
+    #               (0,0): 1  x  x^2   (0,1): 1  x  x^2   (1,1): 1  x  x^2
+    assert b.tolist() == [1.0, 0.0, 1.0, 0.0, 2.0, 0.0, 2.0, 0.0, 0.0]
+    assert pd.tolist() == [2.0, 3.0, 2.0, 3.0, 5.0, 3.0, 2.0, 3.0, 2.0]
