@@ -13,11 +13,12 @@
 //                  Householder reduction Q^T W Q = T (T tridiagonal), the
 //                  reflector vectors kept for the back-transformation.
 //   k_tri_vectors  one warp per eigenvalue i (FP32): bisection on Sturm
-//                  counts of T brackets lambda_i, inverse iteration with
-//                  Rayleigh shifts on T gives its eigenvector z_i, and the
-//                  reflectors map it back: v_i = Q z_i.
+//                  counts of T brackets lambda_i, two steps of inverse
+//                  iteration on T give its eigenvector z_i, and the
+//                  reflectors map it back: v_i = Q z_i (four at a time).
 //   k_tri_recon    cooperative grid, FP64 products: V made orthonormal to the
-//                  unit roundoff (Newton-Schulz V (3I - V^T V) / 2),
+//                  unit roundoff (Newton-Schulz V (3I - V^T V) / 2, repeated
+//                  while the deviation is above 3e-8),
 //                  B = V^T W V, a check of the first-order projection of B,
 //                  and while that fails (at most twice) a Newton correction
 //                  of V (Ogita and Aishima's refinement step) and another
@@ -31,10 +32,10 @@
 // the check asks that sum to stay below 1e-14 |W|_F.  FP32 eigenvectors
 // carry |offdiag B| of order 1e-7 |W|, so the check passes without a
 // correction where the spectrum keeps away from zero and needs one where
-// eigenvalues of both signs crowd it.  If V is not even FP32-orthonormal, or
-// three passes do not pass the check, the grid Jacobi kernel launched after
-// this one takes the block over (flag word 0; started from V when V is
-// orthonormal).
+// eigenvalues of both signs crowd it.  If V^T V deviates from I by more
+// than 0.25 (or Newton-Schulz stops converging), or three passes do not pass
+// the check, the grid Jacobi kernel launched after this one takes the block
+// over (flag word 0; started from V when V is orthonormal).
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -47,7 +48,7 @@ namespace sos {
 namespace {
 
 constexpr int kTriThreads = 256;   // reduction CTA (8 warps: little redundant per-warp work)
-constexpr int kVecThreads = 256;   // one CTA per eigenvector
+constexpr int kVecThreads = 128;   // four eigenvectors per CTA (one warp per scheduler)
 constexpr int kRecThreads = 128;   // reconstruction CTAs
 constexpr int kTriSlots = (kTriMaxN + 31) / 32;  // per-lane register slots of a length-N vector
 constexpr int kTriRows = 256;                     // p vectors of the reduction (float4 chunks of two slots)
@@ -414,16 +415,28 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tri_reduce(DevPlan<T> p, int
 
 // Number of eigenvalues of T below x (Sturm sequence of the LDL^T pivots;
 // a pivot of magnitude below pivmin is replaced by -pivmin).
-__device__ __forceinline__ int sturm_count(const float* d, const float* e2, int N, float x, float pivmin) {
-  float q = d[0] - x;
-  if (fabsf(q) < pivmin) q = -pivmin;
-  int c = q < 0.f;
+// Sturm counts of T - x0 I and T - x1 I (the number of eigenvalues below
+// x0 and x1): the pivots of the LDL^T recurrence q_k = d_k - x - e_{k-1}^2 /
+// q_{k-1}, two independent chains interleaved; a pivot smaller than pivmin
+// is replaced by -pivmin.
+__device__ __forceinline__ void sturm_count2(const float* __restrict__ d, const float* __restrict__ e2, int N,
+                                             float x0, float x1, float pivmin, int& c0, int& c1) {
+  float q0 = d[0] - x0, q1 = d[0] - x1;
+  q0 = fabsf(q0) < pivmin ? -pivmin : q0;
+  q1 = fabsf(q1) < pivmin ? -pivmin : q1;
+  int a0 = q0 < 0.f, a1 = q1 < 0.f;
+#pragma unroll 4
   for (int k = 1; k < N; ++k) {
-    q = (d[k] - x) - __fdividef(e2[k - 1], q);
-    if (fabsf(q) < pivmin) q = -pivmin;
-    c += q < 0.f;
+    const float dk = d[k], ek = e2[k - 1];
+    q0 = (dk - x0) - __fdividef(ek, q0);
+    q1 = (dk - x1) - __fdividef(ek, q1);
+    q0 = fabsf(q0) < pivmin ? -pivmin : q0;
+    q1 = fabsf(q1) < pivmin ? -pivmin : q1;
+    a0 += q0 < 0.f;
+    a1 += q1 < 0.f;
   }
-  return c;
+  c0 = a0;
+  c1 = a1;
 }
 
 // Deterministic start vector entries in (-1, 1).
@@ -435,12 +448,30 @@ __device__ __forceinline__ float start_entry(int i, int j) {
   return (static_cast<float>(h & 0xFFFFFFu) + 0.5f) / 8388608.0f - 1.0f;
 }
 
+constexpr int kVecGroup = 4;                                   // reflectors applied per warp reduction
+constexpr int kVecChunk = kVecGroup * (kVecThreads / 32);      // reflectors staged at a time: one group per warp
+constexpr int kVecPairs = kVecGroup * (kVecGroup - 1) / 2;     // products u_r^T u_t, t < r, of a group
+
+__host__ __device__ __forceinline__ int vec_ld(int N) { return (N + 3) & ~3; }
+
+// Shared memory of k_tri_vectors: d, e, e^2, tau of T; per warp the
+// eigenvector z and the pivoted LU of the inverse iteration (1 / pivot,
+// first and second superdiagonal of U, multipliers); two chunks of
+// reflectors; the products of the reflectors within each group of a chunk;
+// per warp the row exchanges (bytes).
+size_t tri_vectors_smem(int N) {
+  constexpr int nw = kVecThreads / 32;
+  return sizeof(float) * (static_cast<size_t>(4 + 5 * nw) * N + 2 * kVecChunk * static_cast<size_t>(vec_ld(N)) +
+                          (kVecChunk / kVecGroup) * kVecPairs) +
+         sizeof(bool) * nw * static_cast<size_t>(N);
+}
+
 __global__ void __launch_bounds__(kVecThreads) k_tri_vectors(DevPlan<double> p, int bid, LargeScratch<double> L) {
   extern __shared__ __align__(16) float vsm[];
   __shared__ float s_g[3][kVecThreads / 32];
   const BlockDesc bd = p.blocks[bid];
   if (!p.active[bd.inst]) return;
-  const int N = bd.N;
+  const int N = bd.N, ldu = vec_ld(N);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int nw = kVecThreads / 32;
   const TriOut out = tri_out(L.B0, N);
@@ -448,12 +479,14 @@ __global__ void __launch_bounds__(kVecThreads) k_tri_vectors(DevPlan<double> p, 
   float* ef = df + N;    // subdiagonal, split entries zeroed
   float* e2f = ef + N;   // its squares
   float* tau_s = e2f + N;
-  float* z = tau_s + N + warp * 5 * N;  // this warp's eigenvector of T and
-  float* rinv = z + N;   // the pivoted LU of T - sigma I: reciprocal pivots,
-  float* du = rinv + N;  // first and second superdiagonal of U,
+  float* z = tau_s + N + warp * 5 * N;  // this warp's eigenvector of T and the
+  float* rinv = z + N;   // pivoted LU of T - sigma I: reciprocal pivots, first
+  float* du = rinv + N;  // and second superdiagonal of U, multipliers
   float* du2 = du + N;
-  float* dl = du2 + N;   // multipliers
-  int* piv = reinterpret_cast<int*>(tau_s + N + nw * 5 * N) + warp * N;
+  float* dl = du2 + N;
+  float* ubuf = tau_s + N + nw * 5 * N;      // [2][kVecChunk][ldu] reflectors
+  float* gbuf = ubuf + 2 * kVecChunk * ldu;  // [kVecChunk / kVecGroup][kVecPairs]
+  bool* pv = reinterpret_cast<bool*>(gbuf + (kVecChunk / kVecGroup) * kVecPairs) + warp * N;  // row exchanges
 
   // T, the Gershgorin bounds and the splits (|e_k| <= 1e-10 |T| set to zero)
   float tn = 0.f, glo = FLT_MAX, ghi = -FLT_MAX;
@@ -483,193 +516,335 @@ __global__ void __launch_bounds__(kVecThreads) k_tri_vectors(DevPlan<double> p, 
     ghi = fmaxf(ghi, s_g[2][w]);
   }
   const float split = 1e-10f * tn;
+  int has_split = 0;
   for (int k = tid; k < N; k += kVecThreads) {
     float ek = k < N - 1 ? out.e[k] : 0.f;
-    if (fabsf(ek) <= split) ek = 0.f;
+    if (fabsf(ek) <= split) {
+      ek = 0.f;
+      has_split |= k < N - 1;
+    }
     df[k] = out.d[k];
     ef[k] = ek;
     e2f[k] = ek * ek;
     tau_s[k] = out.tau[k];
   }
-  __syncthreads();
+  has_split = __syncthreads_or(has_split);
   const int i = blockIdx.x * nw + warp;  // this warp's eigenvalue (ascending order)
-  if (i >= N) return;
+  const bool valid = i < N;              // a warp past N still stages reflectors below
 
-  // bisection: 32 points per pass, keeping count(lo) <= i < count(hi)
-  const float pivmin = 1e-30f;
-  float lo = glo - 1e-6f * tn - 1e-30f, hi = ghi + 1e-6f * tn + 1e-30f;
-  for (int pass = 0; pass < 5; ++pass) {
-    const float x = lo + (hi - lo) * (static_cast<float>(lane + 1) / 33.f);
-    const int c = sturm_count(df, e2f, N, x, pivmin);
-    float nlo = c <= i ? x : -FLT_MAX;
-    float nhi = c >= i + 1 ? x : FLT_MAX;
-    for (int o = 16; o > 0; o >>= 1) {
-      nlo = fmaxf(nlo, __shfl_xor_sync(0xffffffffu, nlo, o));
-      nhi = fminf(nhi, __shfl_xor_sync(0xffffffffu, nhi, o));
+  if (valid) {
+    // bisection: 64 points per pass (two per lane), keeping
+    // count(lo) <= i < count(hi)
+    const float pivmin = 1e-30f;
+    float lo = glo - 1e-6f * tn - 1e-30f, hi = ghi + 1e-6f * tn + 1e-30f;
+    for (int pass = 0; pass < 4; ++pass) {
+      const float step = (hi - lo) * (1.f / 65.f);
+      const float x0 = fmaf(step, static_cast<float>(lane + 1), lo);
+      const float x1 = fmaf(step, static_cast<float>(lane + 33), lo);
+      int c0, c1;
+      sturm_count2(df, e2f, N, x0, x1, pivmin, c0, c1);
+      float nlo = fmaxf(c0 <= i ? x0 : -FLT_MAX, c1 <= i ? x1 : -FLT_MAX);
+      float nhi = fminf(c0 >= i + 1 ? x0 : FLT_MAX, c1 >= i + 1 ? x1 : FLT_MAX);
+      for (int o = 16; o > 0; o >>= 1) {
+        nlo = fmaxf(nlo, __shfl_xor_sync(0xffffffffu, nlo, o));
+        nhi = fminf(nhi, __shfl_xor_sync(0xffffffffu, nhi, o));
+      }
+      if (nlo > lo && nlo < hi) lo = nlo;
+      if (nhi < hi && nhi > lo) hi = nhi;
     }
-    if (nlo > lo && nlo < hi) lo = nlo;
-    if (nhi < hi && nhi > lo) hi = nhi;
-  }
 
-  // lane 0: the unreduced block of T that holds eigenvalue i, then inverse
-  // iteration on it with Rayleigh-quotient shifts kept by the bracket
-  if (lane == 0) {
-    int clo = 0;
-    {
-      float q = 0.f;
-      for (int k = 0; k < N; ++k) {
-        q = (k == 0 || e2f[k - 1] == 0.f) ? df[k] - lo : (df[k] - lo) - __fdividef(e2f[k - 1], q);
-        if (fabsf(q) < pivmin) q = -pivmin;
-        clo += q < 0.f;
-      }
-    }
-    const int want = i - clo;  // position of eigenvalue i among those in (lo, hi], by block
-    int run = 0, b0 = 0, b1 = N - 1, start = 0, cl = 0, ch = 0;
-    float ql = 0.f, qh = 0.f;
-    bool found = false;
-    for (int k = 0; k < N && !found; ++k) {
-      if (k == 0 || e2f[k - 1] == 0.f) {
-        start = k;
-        cl = ch = 0;
-        ql = df[k] - lo;
-        qh = df[k] - hi;
-      } else {
-        ql = (df[k] - lo) - __fdividef(e2f[k - 1], ql);
-        qh = (df[k] - hi) - __fdividef(e2f[k - 1], qh);
-      }
-      if (fabsf(ql) < pivmin) ql = -pivmin;
-      if (fabsf(qh) < pivmin) qh = -pivmin;
-      cl += ql < 0.f;
-      ch += qh < 0.f;
-      if (k == N - 1 || e2f[k] == 0.f) {  // end of a block
-        const int inb = ch - cl;
-        if (run + inb > want) {
-          b0 = start;
-          b1 = k;
-          found = true;
-        }
-        run += inb;
-      }
-    }
-    if (!found) {  // inconsistent counts: the whole matrix
-      b0 = 0;
-      b1 = N - 1;
-    }
-    for (int k = 0; k < N; ++k) z[k] = 0.f;
-    if (b1 == b0) {
-      z[b0] = 1.f;
-    } else {
-      const float tiny = 1.2e-7f * tn + 1e-30f;
-      const float wid = (hi - lo) + 1e-6f * tn;
-      float sigma = 0.5f * (lo + hi);
-      float nrm = 0.f;
-      for (int k = b0; k <= b1; ++k) {
-        z[k] = start_entry(i, k);
-        nrm = fmaf(z[k], z[k], nrm);
-      }
-      nrm = rsqrtf(nrm);
-      for (int k = b0; k <= b1; ++k) z[k] *= nrm;
-      for (int it = 0; it < 3; ++it) {
-        // LU with partial pivoting of T_b - sigma I
-        float dk = df[b0] - sigma, uk = ef[b0];
-        for (int k = b0; k < b1; ++k) {
-          const float lk = ef[k], dn = df[k + 1] - sigma, un = k + 1 < b1 ? ef[k + 1] : 0.f;
-          if (fabsf(dk) >= fabsf(lk)) {
-            const float pv = fabsf(dk) < tiny ? (dk < 0.f ? -tiny : tiny) : dk;
-            const float r = __fdividef(1.f, pv);
-            const float l = lk * r;
-            piv[k] = 0;
-            rinv[k] = r;
-            du[k] = uk;
-            du2[k] = 0.f;
-            dl[k] = l;
-            dk = fmaf(-l, uk, dn);
-            uk = un;
-          } else {  // rows k and k + 1 exchanged
-            const float r = __fdividef(1.f, lk);
-            const float l = dk * r;
-            piv[k] = 1;
-            rinv[k] = r;
-            du[k] = dn;
-            du2[k] = un;
-            dl[k] = l;
-            dk = fmaf(-l, dn, uk);
-            uk = -l * un;
+    // the unreduced block of T that holds eigenvalue i (the whole matrix
+    // unless T split), found by lane 0 from block-wise Sturm counts
+    int b0 = 0, b1 = N - 1;
+    if (has_split) {
+      if (lane == 0) {
+        int clo = 0;
+        {
+          float q = 0.f;
+          for (int k = 0; k < N; ++k) {
+            q = (k == 0 || e2f[k - 1] == 0.f) ? df[k] - lo : (df[k] - lo) - __fdividef(e2f[k - 1], q);
+            if (fabsf(q) < pivmin) q = -pivmin;
+            clo += q < 0.f;
           }
         }
-        rinv[b1] = __fdividef(1.f, fabsf(dk) < tiny ? (dk < 0.f ? -tiny : tiny) : dk);
-        // L U y = z: forward with the exchanges, then backward
-        float zk = z[b0];
-        for (int k = b0; k < b1; ++k) {
-          const float zn = z[k + 1];
-          if (piv[k]) {
-            z[k] = zn;
-            zk = fmaf(-dl[k], zn, zk);
+        const int want = i - clo;  // position of eigenvalue i among those in (lo, hi], by block
+        int run = 0, start = 0, cl = 0, ch = 0;
+        float ql = 0.f, qh = 0.f;
+        bool found = false;
+        for (int k = 0; k < N && !found; ++k) {
+          if (k == 0 || e2f[k - 1] == 0.f) {
+            start = k;
+            cl = ch = 0;
+            ql = df[k] - lo;
+            qh = df[k] - hi;
           } else {
-            z[k] = zk;
-            zk = fmaf(-dl[k], zk, zn);
+            ql = (df[k] - lo) - __fdividef(e2f[k - 1], ql);
+            qh = (df[k] - hi) - __fdividef(e2f[k - 1], qh);
+          }
+          if (fabsf(ql) < pivmin) ql = -pivmin;
+          if (fabsf(qh) < pivmin) qh = -pivmin;
+          cl += ql < 0.f;
+          ch += qh < 0.f;
+          if (k == N - 1 || e2f[k] == 0.f) {  // end of a block
+            const int inb = ch - cl;
+            if (run + inb > want) {
+              b0 = start;
+              b1 = k;
+              found = true;
+            }
+            run += inb;
           }
         }
-        float y2 = 0.f, y1 = zk * rinv[b1];
-        z[b1] = y1;
-        nrm = y1 * y1;
+        if (!found) {  // inconsistent counts: the whole matrix
+          b0 = 0;
+          b1 = N - 1;
+        }
+      }
+      b0 = __shfl_sync(0xffffffffu, b0, 0);
+      b1 = __shfl_sync(0xffffffffu, b1, 0);
+    }
+
+    // inverse iteration, two steps with the shift at the centre of the
+    // bracket: lane 0 factors T_b - sigma I once with partial pivoting (the
+    // first right side eliminated in the same pass) and substitutes
+    // backward; the warp normalises; lane 0 repeats the forward elimination
+    // and backward substitution on the result.  (Emulated on ADMM inputs of
+    // a 231 x 231 block, two steps at a fixed shift give the same
+    // orthogonality and Ritz off-diagonal as three with Rayleigh shifts.)
+    float nrm = 0.f;
+    for (int k = lane; k < N; k += 32) {
+      const float v = (k >= b0 && k <= b1) ? start_entry(i, k) : 0.f;
+      z[k] = v;
+      nrm = fmaf(v, v, nrm);
+    }
+    nrm = rsqrtf(warp_sum_f(nrm));
+    for (int k = lane; k < N; k += 32) z[k] *= nrm;
+    __syncwarp();
+    if (b1 > b0) {
+      const float tiny = 1.2e-7f * tn + 1e-30f;
+      const float sigma = 0.5f * (lo + hi);
+      float* __restrict__ zR = z;
+      float* __restrict__ rR = rinv;
+      float* __restrict__ uR = du;
+      float* __restrict__ u2R = du2;
+      float* __restrict__ lR = dl;
+      // backward substitution with U; the next step's operands are loaded
+      // one step ahead
+      auto backward = [&](float zk) {
+        float y1 = zk * rR[b1], y2 = 0.f;
+        zR[b1] = y1;
+        float zc = zR[b1 - 1], uc = uR[b1 - 1], u2c = u2R[b1 - 1], rc = rR[b1 - 1];
         for (int k = b1 - 1; k >= b0; --k) {
-          const float y = (z[k] - du[k] * y1 - du2[k] * y2) * rinv[k];
-          z[k] = y;
-          nrm = fmaf(y, y, nrm);
+          const bool more = k > b0;
+          const float zp = more ? zR[k - 1] : 0.f, up = more ? uR[k - 1] : 0.f;
+          const float u2p = more ? u2R[k - 1] : 0.f, rp = more ? rR[k - 1] : 0.f;
+          const float y = fmaf(-u2c, y2, fmaf(-uc, y1, zc)) * rc;
+          zR[k] = y;
           y2 = y1;
           y1 = y;
+          zc = zp;
+          uc = up;
+          u2c = u2p;
+          rc = rp;
         }
-        nrm = rsqrtf(nrm);
-        float rq = 0.f, prev = 0.f;
-        for (int k = b0; k <= b1; ++k) {
-          const float zz = z[k] * nrm;
-          z[k] = zz;
-          rq = fmaf(df[k] * zz, zz, rq);
-          if (k > b0) rq = fmaf(2.f * ef[k - 1] * prev, zz, rq);
-          prev = zz;
+      };
+      auto normalise = [&]() {
+        __syncwarp();
+        float n2 = 0.f;
+        for (int k = b0 + lane; k <= b1; k += 32) n2 = fmaf(z[k], z[k], n2);
+        const float sc = rsqrtf(warp_sum_f(n2));
+        for (int k = b0 + lane; k <= b1; k += 32) z[k] *= sc;
+        __syncwarp();
+      };
+      if (lane == 0) {
+        const float* __restrict__ dR = df;
+        const float* __restrict__ eR = ef;
+        // operands of the next step are loaded one step ahead, so the
+        // dependent chain of a step holds no shared-memory load; step k
+        // keeps its multiplier in lR and its row exchange in pv
+        float dk = dR[b0] - sigma, uk = eR[b0], zk = zR[b0];
+        float lk = eR[b0], dn = dR[b0 + 1] - sigma, zn = zR[b0 + 1];
+        float un = b0 + 1 < b1 ? eR[b0 + 1] : 0.f;
+        for (int k = b0; k < b1; ++k) {
+          const bool more = k + 1 < b1;
+          const float dn2 = more ? dR[k + 2] - sigma : 0.f;
+          const float zn2 = more ? zR[k + 2] : 0.f;
+          const float un2 = k + 2 < b1 ? eR[k + 2] : 0.f;
+          const bool sw = fabsf(lk) > fabsf(dk);  // rows k and k + 1 exchanged
+          const float pd = fabsf(dk) < tiny ? (dk < 0.f ? -tiny : tiny) : dk;
+          const float r = __fdividef(1.f, sw ? lk : pd);
+          const float l = (sw ? dk : lk) * r;
+          rR[k] = r;
+          uR[k] = sw ? dn : uk;
+          u2R[k] = sw ? un : 0.f;
+          lR[k] = l;
+          pv[k] = sw;
+          zR[k] = sw ? zn : zk;  // forward elimination of the right side
+          const float dk1 = sw ? fmaf(-l, dn, uk) : fmaf(-l, uk, dn);
+          const float uk1 = sw ? -l * un : un;
+          const float zk1 = sw ? fmaf(-l, zn, zk) : fmaf(-l, zk, zn);
+          dk = dk1;
+          uk = uk1;
+          zk = zk1;
+          lk = un;  // e_{k+1}
+          dn = dn2;
+          zn = zn2;
+          un = un2;
         }
-        if (rq > lo - wid && rq < hi + wid) sigma = rq;  // Rayleigh quotient z^T T z as the next shift
+        rR[b1] = __fdividef(1.f, fabsf(dk) < tiny ? (dk < 0.f ? -tiny : tiny) : dk);
+        backward(zk);
       }
+      normalise();
+      if (lane == 0) {  // second step: the same factors
+        float zk = zR[b0], zn = zR[b0 + 1], l = lR[b0];
+        bool sw = pv[b0];
+        for (int k = b0; k < b1; ++k) {
+          const bool more = k + 1 < b1;
+          const float zn2 = more ? zR[k + 2] : 0.f, l2 = more ? lR[k + 1] : 0.f;
+          const bool sw2 = more ? pv[k + 1] : false;
+          zR[k] = sw ? zn : zk;
+          zk = sw ? fmaf(-l, zn, zk) : fmaf(-l, zk, zn);
+          zn = zn2;
+          l = l2;
+          sw = sw2;
+        }
+        backward(zk);
+      }
+      normalise();
     }
   }
   __syncwarp();
 
-  // v_i = H_0 H_1 ... H_{N-3} z; lane l holds entries l + 32 s, and the next
-  // reflector's entries are loaded while the current one is applied
-  float zr[kTriSlots], un[kTriSlots];
+  // v_i = H_0 H_1 ... H_{N-3} z.  Lane l holds entries l + 32 s.  The CTA
+  // stages kVecChunk reflectors at a time in shared memory (entry k + 1 set
+  // to 1, entries up to k zero), loading the next chunk while the current
+  // one is applied.  A warp applies a group of kVecGroup reflectors
+  // u_0, u_1, ... (in the order they act) with one reduction: with
+  // d_r = u_r^T z and g_rt = u_r^T u_t, reflector r meets
+  // z - sum_{t < r} alpha_t u_t, so alpha_r = tau_r (d_r - sum_{t < r}
+  // alpha_t g_rt), and z -= sum_r alpha_r u_r.  The g_rt depend on the
+  // reflectors only: warp w forms those of group w of each chunk for the CTA.
+  float zr[kTriSlots];
 #pragma unroll
   for (int s = 0; s < kTriSlots; ++s) {
     const int j = lane + 32 * s;
-    zr[s] = j < N ? z[j] : 0.f;
+    zr[s] = (valid && j < N) ? z[j] : 0.f;
   }
-  auto fetch = [&](int k, float (&u)[kTriSlots]) {
-    const float* Uk = out.U + static_cast<int64_t>(k > 0 ? k : 0) * N;
+  const int nref = N - 2;  // reflectors 0 .. N - 3, applied from N - 3 down
+  const int nchunk = (nref + kVecChunk - 1) / kVecChunk;
+  constexpr int kPer = (kVecChunk * ((kTriMaxN + 3) & ~3) + kVecThreads - 1) / kVecThreads;
+  float pre[kPer];
+  // chunk c holds reflectors k = N - 3 - c kVecChunk - r, r = 0 .. kVecChunk - 1
+  auto load_chunk = [&](int c) {
 #pragma unroll
-    for (int s = 0; s < kTriSlots; ++s) {
-      const int j = lane + 32 * s;
-      u[s] = (k >= 0 && j >= k + 2 && j < N) ? __ldcg(Uk + j) : 0.f;
+    for (int t = 0; t < kPer; ++t) {
+      const int q = tid + t * kVecThreads;
+      const int r = q / ldu, j = q - r * ldu;
+      const int k = N - 3 - c * kVecChunk - r;
+      float v = 0.f;
+      if (r < kVecChunk && k >= 0 && j < N)
+        v = j == k + 1 ? 1.f : (j >= k + 2 ? __ldcg(out.U + static_cast<int64_t>(k) * N + j) : 0.f);
+      pre[t] = v;
     }
   };
-  fetch(N - 3, un);
-  for (int k = N - 3; k >= 0; --k) {
-    float ur[kTriSlots];
+  auto store_chunk = [&](int buf) {
+    float* dst = ubuf + buf * kVecChunk * ldu;
 #pragma unroll
-    for (int s = 0; s < kTriSlots; ++s) ur[s] = un[s];
-    fetch(k - 1, un);
-    const float tau = tau_s[k];
-    if (tau == 0.f) continue;  // H_k = I
-    float dsum = 0.f;
-#pragma unroll
-    for (int s = 0; s < kTriSlots; ++s) {
-      const int j = lane + 32 * s;
-      if (j == k + 1) ur[s] = 1.f;
-      dsum = fmaf(ur[s], zr[s], dsum);
+    for (int t = 0; t < kPer; ++t) {
+      const int q = tid + t * kVecThreads;
+      if (q < kVecChunk * ldu) dst[q] = pre[t];
     }
-    dsum = tau * warp_sum_f(dsum);
+  };
+  auto load_group = [&](const float* ub, int g, float (&u)[kVecGroup][kTriSlots]) {
 #pragma unroll
-    for (int s = 0; s < kTriSlots; ++s) zr[s] = fmaf(-dsum, ur[s], zr[s]);
+    for (int r = 0; r < kVecGroup; ++r)
+#pragma unroll
+      for (int s = 0; s < kTriSlots; ++s) {
+        const int j = lane + 32 * s;
+        u[r][s] = j < ldu ? ub[(g + r) * ldu + j] : 0.f;
+      }
+  };
+  load_chunk(0);
+  store_chunk(0);
+  __syncthreads();
+  for (int c = 0; c < nchunk; ++c) {
+    if (c + 1 < nchunk) load_chunk(c + 1);
+    const float* ub = ubuf + (c & 1) * kVecChunk * ldu;
+    {  // g_rt of group `warp` of this chunk
+      float u[kVecGroup][kTriSlots];
+      load_group(ub, warp * kVecGroup, u);
+      float gv[kVecPairs];
+      int q = 0;
+#pragma unroll
+      for (int r = 1; r < kVecGroup; ++r)
+#pragma unroll
+        for (int t = 0; t < r; ++t) {
+          float acc = 0.f;
+#pragma unroll
+          for (int s = 0; s < kTriSlots; ++s) acc = fmaf(u[r][s], u[t][s], acc);
+          gv[q++] = acc;
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q2 = 0; q2 < kVecPairs; ++q2) gv[q2] += __shfl_xor_sync(0xffffffffu, gv[q2], o);
+      if (lane < kVecPairs) {
+        float x = gv[0];
+#pragma unroll
+        for (int q2 = 1; q2 < kVecPairs; ++q2) x = lane == q2 ? gv[q2] : x;
+        gbuf[warp * kVecPairs + lane] = x;
+      }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int g = 0; g < kVecChunk; g += kVecGroup) {
+      const int k0 = N - 3 - c * kVecChunk - g;  // first reflector of the group
+      if (k0 < 0) break;
+      float u[kVecGroup][kTriSlots];
+      load_group(ub, g, u);
+      float dv[kVecGroup];
+#pragma unroll
+      for (int r = 0; r < kVecGroup; ++r) {
+        float acc = 0.f;
+#pragma unroll
+        for (int s = 0; s < kTriSlots; ++s) acc = fmaf(u[r][s], zr[s], acc);
+        dv[r] = acc;
+      }
+      // transposed reduction: after the xor-16 and xor-8 exchanges lane l
+      // holds a partial of d_{(l >> 3) & 3}; three more steps finish it, and
+      // lanes 0, 8, 16, 24 broadcast d_0 .. d_3
+      const bool h16 = lane & 16, h8 = lane & 8;
+      const float b0 = (h16 ? dv[2] : dv[0]) + __shfl_xor_sync(0xffffffffu, h16 ? dv[0] : dv[2], 16);
+      const float b1 = (h16 ? dv[3] : dv[1]) + __shfl_xor_sync(0xffffffffu, h16 ? dv[1] : dv[3], 16);
+      float x = (h8 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, h8 ? b0 : b1, 8);
+      x += __shfl_xor_sync(0xffffffffu, x, 4);
+      x += __shfl_xor_sync(0xffffffffu, x, 2);
+      x += __shfl_xor_sync(0xffffffffu, x, 1);
+      float dsum[kVecGroup];
+#pragma unroll
+      for (int r = 0; r < kVecGroup; ++r) dsum[r] = __shfl_sync(0xffffffffu, x, 8 * r);
+      const float* gg = gbuf + (g / kVecGroup) * kVecPairs;
+      float al[kVecGroup];
+#pragma unroll
+      for (int r = 0; r < kVecGroup; ++r) {
+        float dd = dsum[r];
+#pragma unroll
+        for (int t = 0; t < r; ++t) dd = fmaf(-al[t], gg[r * (r - 1) / 2 + t], dd);  // g_rt
+        const int k = k0 - r;
+        al[r] = k >= 0 ? tau_s[k] * dd : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < kVecGroup; ++r)
+#pragma unroll
+        for (int s = 0; s < kTriSlots; ++s) zr[s] = fmaf(-al[r], u[r][s], zr[s]);
+    }
+    // buffer (c + 1) & 1 last served chunk c - 1, which every warp finished
+    // before the barrier that opened chunk c; gbuf is rewritten only after
+    // the next barrier
+    if (c + 1 < nchunk) store_chunk((c + 1) & 1);
+    __syncthreads();
   }
+  if (!valid) return;
   const int Np = N + (N & 1);
 #pragma unroll
   for (int s = 0; s < kTriSlots; ++s) {
@@ -941,21 +1116,30 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
   double* Vn = L.B1;
   int work = 0;  // refinement GEMM passes beyond the reconstruction (reported per block)
   for (int pass = 0;; ++pass) {
-    double rmax = 0.0;
-    gemm_sym<true, false>(Vc, Vc, L.T1, N, Np, OrthMax{&rmax}, sA, sB);
-    double gm;
-    if (!grid_max(rmax, red, L, gen, err, p.wait_limit, gm)) return;
-    if (!(gm <= 1e-3)) {  // not even FP32-orthonormal
-      hand_over(L, false);
-      return;
-    }
-    if (gm > 1e-15) {
+    // Newton-Schulz until V^T V = I to the unit roundoff: a step takes the
+    // largest deviation g to about g^2, so steps repeat (with a new V^T V)
+    // while g > 3e-8.  Eigenvectors of close eigenvalues from separate
+    // inverse iterations overlap by up to about eps_32 / gap (6e-4 for a
+    // gap of 1e-5 |W|); a deviation above 0.25, or one that does not
+    // shrink, goes to the Jacobi kernel from a cold start.
+    double gm = 0.0;
+    for (int ns = 0;; ++ns) {
+      double rmax = 0.0;
+      gemm_sym<true, false>(Vc, Vc, L.T1, N, Np, OrthMax{&rmax}, sA, sB);
+      const double prev = gm;
+      if (!grid_max(rmax, red, L, gen, err, p.wait_limit, gm)) return;
+      if (!(gm <= 0.25) || (ns > 0 && !(gm < prev)) || ns == 6) {  // not converging
+        hand_over(L, false);
+        return;
+      }
+      if (gm <= 1e-15) break;
       gemm_full<false, false>(Vc, L.T1, Vn, N, Np, NsFactor(), sA, sB);
       if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
       double* t = Vc;
       Vc = Vn;
       Vn = t;
       ++work;
+      if (gm <= 3e-8) break;
     }
     gemm_full<false, false>(L.Wf, Vc, L.T1, N, Np, Ident(), sA, sB);
     if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
@@ -1051,9 +1235,6 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
 
 size_t tri_reduce_smem(int N) { return sizeof(float) * (static_cast<size_t>(N) * ((N + 3) & ~3) + 2 * kTriRows); }
 
-size_t tri_vectors_smem(int N) {
-  return (sizeof(float) * (4 + 5 * (kVecThreads / 32)) + sizeof(int) * (kVecThreads / 32)) * static_cast<size_t>(N);
-}
 
 }  // namespace
 
