@@ -17,8 +17,9 @@
 //                  iteration on T give its eigenvector z_i, and the
 //                  reflectors map it back: v_i = Q z_i (four at a time).
 //   k_tri_recon    cooperative grid, FP64 products: V made orthonormal to the
-//                  unit roundoff (Newton-Schulz V (3I - V^T V) / 2, repeated
-//                  while the deviation is above 3e-8),
+//                  unit roundoff (one second-order step of the inverse
+//                  square root of V^T V, or Newton-Schulz V (3I - V^T V) / 2
+//                  repeated for larger deviations),
 //                  B = V^T W V, a check of the first-order projection of B,
 //                  and while that fails (at most twice) a Newton correction
 //                  of V (Ogita and Aishima's refinement step) and another
@@ -967,6 +968,17 @@ struct NsFactor {
   }
 };
 
+// Second-order factor I + E/2 + 3 E^2 / 8 of the inverse square root of
+// V^T V = I - E, from the stored E^2 (staged) and V^T V (read).
+struct NsFactor2 {
+  const double* G;
+  int ld;
+  __device__ __forceinline__ double operator()(int k, int j, double e2) const {
+    const double g = __ldcg(G + static_cast<int64_t>(k) * ld + j);
+    return (k == j ? 1.0 + 0.5 * (1.0 - g) : -0.5 * g) + 0.375 * e2;
+  }
+};
+
 // First-order projection of B = V^T W V at its diagonal (see the file header).
 struct FirstOrder {
   const double* B;
@@ -1116,12 +1128,14 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
   double* Vn = L.B1;
   int work = 0;  // refinement GEMM passes beyond the reconstruction (reported per block)
   for (int pass = 0;; ++pass) {
-    // Newton-Schulz until V^T V = I to the unit roundoff: a step takes the
-    // largest deviation g to about g^2, so steps repeat (with a new V^T V)
-    // while g > 3e-8.  Eigenvectors of close eigenvalues from separate
-    // inverse iterations overlap by up to about eps_32 / gap (6e-4 for a
-    // gap of 1e-5 |W|); a deviation above 0.25, or one that does not
-    // shrink, goes to the Jacobi kernel from a cold start.
+    // V^T V = I to the unit roundoff: a Newton-Schulz step takes the
+    // largest deviation g to about (3/4) g^2 and ends it for g <= 3e-8; for
+    // g <= 1.5e-5 (FP32 eigenvectors of separated eigenvalues) one
+    // second-order step ends it; above that Newton-Schulz steps repeat with
+    // a new V^T V.  Eigenvectors of close eigenvalues from separate inverse
+    // iterations overlap by up to about eps_32 / gap (6e-4 for a gap of
+    // 1e-5 |W|); a deviation above 0.25, or one that does not shrink, goes
+    // to the Jacobi kernel from a cold start.
     double gm = 0.0;
     for (int ns = 0;; ++ns) {
       double rmax = 0.0;
@@ -1133,6 +1147,26 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
         return;
       }
       if (gm <= 1e-15) break;
+      if (gm > 3e-8 && gm <= 1.5e-5) {
+        // one second-order step V (I + E/2 + 3 E^2 / 8), E = I - V^T V
+        // exact in FP64 from the stored V^T V: it leaves about
+        // (5/16) g^3 <= 1e-15 where two first-order steps would take a
+        // second V^T V and a second full product
+        for (int64_t q = gt; q < static_cast<int64_t>(N) * Np; q += gs) {
+          const int k = static_cast<int>(q / Np), j = static_cast<int>(q - static_cast<int64_t>(k) * Np);
+          Vn[q] = j < N ? (k == j ? 1.0 : 0.0) - __ldcg(L.T1 + q) : 0.0;
+        }
+        if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
+        gemm_sym<true, false>(Vn, Vn, L.B0, N, Np, NoOp(), sA, sB);  // E^2 (E symmetric)
+        if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
+        gemm_full<false, false>(Vc, L.B0, Vn, N, Np, NsFactor2{L.T1, Np}, sA, sB);
+        if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
+        double* t = Vc;
+        Vc = Vn;
+        Vn = t;
+        work += 2;
+        break;
+      }
       gemm_full<false, false>(Vc, L.T1, Vn, N, Np, NsFactor(), sA, sB);
       if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
       double* t = Vc;
@@ -1213,7 +1247,16 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
   }
   // T1 = V M with M the first-order projection of B, then U = T1 V^T on the
   // lower triangle; u = svec(U), v = u - W
-  gemm_full<false, false>(Vc, L.B0, L.T1, N, Np, FirstOrder{L.B0, Np}, sA, sB);
+  {  // M once into the free V buffer (one division per entry, not one per
+     // staging of the entry by every tile row), then T1 = V M
+    const FirstOrder fo{L.B0, Np};
+    for (int64_t q = gt; q < static_cast<int64_t>(N) * Np; q += gs) {
+      const int k = static_cast<int>(q / Np), j = static_cast<int>(q - static_cast<int64_t>(k) * Np);
+      Vn[q] = j < N ? fo(k, j, __ldcg(L.B0 + q)) : 0.0;
+    }
+  }
+  if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
+  gemm_full<false, false>(Vc, Vn, L.T1, N, Np, Ident(), sA, sB);
   if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
   auto emit = [&](int ii, int jj, double x) {
     const int64_t kk = packed_index(ii, jj, N);
