@@ -52,7 +52,8 @@ constexpr int kTriThreads = 256;   // reduction CTA (8 warps: little redundant p
 constexpr int kVecThreads = 128;   // four eigenvectors per CTA (one warp per scheduler)
 constexpr int kRecThreads = 128;   // reconstruction CTAs
 constexpr int kTriSlots = (kTriMaxN + 31) / 32;  // per-lane register slots of a length-N vector
-constexpr int kTriRows = 256;                     // p vectors of the reduction (float4 chunks of two slots)
+constexpr int kTriRows = 256;                     // columns of a lane's two float4 slots
+constexpr int kTriPcol = (kTriThreads / 32) * kTriRows;  // per-warp column sums of one step
 
 // Output of the reduction inside LargeScratch::B0 (as floats):
 //   U[k * N + j]   entry j (>= k + 2) of reflector k; its entry k + 1 is 1
@@ -153,10 +154,12 @@ __device__ __forceinline__ void make_reflector(const float4 (&x)[2], int mk, int
   tau = 0.f;
   beta = alpha;
   float sc = 0.f;
-  if (s2 > 0.f) {
-    beta = -copysignf(sqrtf(fmaf(alpha, alpha, s2)), alpha);
-    tau = (beta - alpha) / beta;
-    sc = 1.f / (alpha - beta);
+  if (s2 > 0.f) {  // fast square root and reciprocals: the FP64 refinement
+                    // restores the accuracy these steps give away
+    const float a2 = fmaf(alpha, alpha, s2);
+    beta = -copysignf(a2 * rsqrtf(a2), alpha);
+    tau = (beta - alpha) * __fdividef(1.f, beta);
+    sc = __fdividef(1.f, alpha - beta);
   }
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
@@ -173,27 +176,34 @@ __device__ __forceinline__ void make_reflector(const float4 (&x)[2], int mk, int
 
 // One pass over the rows i < nrows owned by this warp (row chunks q = warp
 // + 8 t, rows 4 q .. 4 q + 3): a = a - v_i w - w_i v on the columns j < ncols,
-// then p_i = tau a v' (v' zero from nrows on), written to pn[i].  All eight
-// rows of two chunks are loaded before any is used; rows and columns past
-// the block are read at clamped addresses and neither written nor counted.
+// and this warp's share of the next product, sum over its rows i of
+// v'_i a_ij for every column j (A symmetric: the column sums are the row
+// products), written to pc[warp][j] -- no reduction across lanes.  All
+// eight rows of two chunks are loaded before any is used; rows past the
+// block are read at clamped addresses and not written (v' is zero there);
+// columns past ncols are not written and their sums are never used.
 // SL: float4 slots per lane (columns 4 lane + 128 s), 1 when ncols <= 128.
 template <int SL>
 __device__ __forceinline__ void fused_rows(float* B, int LD, int N, int nrows, int ncols, int warp, int lane,
                                            const float4 (&v)[2], const float4 (&w)[2], const float4 (&vn)[2],
-                                           float tau, float* pn) {
+                                           float* pc) {
+  float4 cs[SL];
+#pragma unroll
+  for (int s = 0; s < SL; ++s) cs[s] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
   for (int t0 = 0; t0 < 8; t0 += 2) {
     if (4 * (warp + 8 * t0) >= nrows) break;  // warp-uniform: later chunks are further out
-    float vi[8], wi[8];
+    float vi[8], wi[8], ni[8];
     int row[8];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int t = t0 + h, src = warp + 8 * (t & 3);
-      const float4 vq = t < 4 ? v[0] : v[1], wq = t < 4 ? w[0] : w[1];
+      const float4 vq = t < 4 ? v[0] : v[1], wq = t < 4 ? w[0] : w[1], nq = t < 4 ? vn[0] : vn[1];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         vi[4 * h + c] = __shfl_sync(0xffffffffu, f4get(vq, c), src);
         wi[4 * h + c] = __shfl_sync(0xffffffffu, f4get(wq, c), src);
+        ni[4 * h + c] = __shfl_sync(0xffffffffu, f4get(nq, c), src);
         row[4 * h + c] = 4 * (warp + 8 * t) + c;
       }
     }
@@ -205,10 +215,8 @@ __device__ __forceinline__ void fused_rows(float* B, int LD, int N, int nrows, i
         const int i = min(row[r], N - 1), j0 = min(128 * s + 4 * lane, LD - 4);
         a[r][s] = *reinterpret_cast<const float4*>(B + i * LD + j0);
       }
-    float acc[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      acc[r] = 0.f;
       const bool rok = row[r] < nrows;
 #pragma unroll
       for (int s = 0; s < SL; ++s) {
@@ -219,15 +227,15 @@ __device__ __forceinline__ void fused_rows(float* B, int LD, int N, int nrows, i
         t.z = fmaf(-vi[r], w[s].z, fmaf(-wi[r], v[s].z, t.z));
         t.w = fmaf(-vi[r], w[s].w, fmaf(-wi[r], v[s].w, t.w));
         if (rok && j0 < ncols) *reinterpret_cast<float4*>(B + row[r] * LD + j0) = t;
-        const float d4 = fmaf(t.x, vn[s].x, fmaf(t.y, vn[s].y, fmaf(t.z, vn[s].z, t.w * vn[s].w)));
-        acc[r] += (j0 < ncols) ? d4 : 0.f;
+        cs[s].x = fmaf(ni[r], t.x, cs[s].x);
+        cs[s].y = fmaf(ni[r], t.y, cs[s].y);
+        cs[s].z = fmaf(ni[r], t.z, cs[s].z);
+        cs[s].w = fmaf(ni[r], t.w, cs[s].w);
       }
     }
-    const float tot = warp_sum8(acc, lane);
-    const int idx = (lane >> 2) & 7;
-    const int i = 4 * (warp + 8 * (t0 + (idx >> 2))) + (idx & 3);
-    if ((lane & 3) == 0 && i < nrows) pn[i] = tau * tot;
   }
+#pragma unroll
+  for (int s = 0; s < SL; ++s) *reinterpret_cast<float4*>(pc + warp * kTriRows + 128 * s + 4 * lane) = cs[s];
 }
 
 constexpr int kGatherCtas = 64;
@@ -273,7 +281,10 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tri_reduce(DevPlan<T> p, int
   const int N = bd.N, LD = (N + 3) & ~3;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float* B = tsm;
-  float* pbuf = B + static_cast<size_t>(N) * LD;  // two alternating copies of p (kTriRows each)
+  // per-warp column sums [8][kTriRows] (read at the start of a step, before
+  // the barrier after which the step's fused pass rewrites them), and p
+  float* pcol = B + static_cast<size_t>(N) * LD;
+  float* pfin = pcol + kTriPcol;
   const TriOut out = tri_out(L.B0, N);
 
   // W (dense FP32 copy from k_tri_gather), scaled by 1 / |W|_F
@@ -293,7 +304,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tri_reduce(DevPlan<T> p, int
       a.w *= scale;
       dst[q] = a;
     }
-    for (int q = tid; q < 2 * kTriRows; q += kTriThreads) pbuf[q] = 0.f;
+    for (int q = tid; q < kTriPcol + kTriRows; q += kTriThreads) pcol[q] = 0.f;
   }
   __syncthreads();
 
@@ -317,14 +328,24 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tri_reduce(DevPlan<T> p, int
   // p = tau A22 v for step 0 (no update before it)
   {
     const float4 zero[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-    fused_rows<2>(B, LD, N, N - 1, N - 1, warp, lane, vk, zero, vk, tauk, pbuf);
+    fused_rows<2>(B, LD, N, N - 1, N - 1, warp, lane, vk, zero, vk, pcol);
   }
   __syncthreads();
 
   for (int k = 0; k < N - 2; ++k) {
     const int m = N - 1 - k;        // trailing block of step k: B[0..m-1][0..m-1]
-    const float* pc = pbuf + (k & 1) * kTriRows;
-    float* pn = pbuf + ((k + 1) & 1) * kTriRows;
+    const float* pc = pcol;
+    float* pn = pcol;
+    // p = tau A v: warp w sums the per-warp column sums of columns
+    // 32 w .. 32 w + 31 once, then every warp reads the whole p
+    {
+      const int j = 32 * warp + lane;
+      float q = 0.f;
+#pragma unroll
+      for (int w = 0; w < kTriThreads / 32; ++w) q += pc[w * kTriRows + j];
+      pfin[j] = j < m ? tauk * q : 0.f;  // sums past the block may be stale or non-finite
+    }
+    __syncthreads();
     // w_k = p - (tau / 2)(p^T v) v, every warp for itself
     {
       float dot = 0.f;
@@ -332,7 +353,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tri_reduce(DevPlan<T> p, int
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         const int j0 = 128 * s + 4 * lane;
-        pk[s] = j0 < kTriRows ? *reinterpret_cast<const float4*>(pc + j0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        pk[s] = *reinterpret_cast<const float4*>(pfin + j0);
         dot = fmaf(pk[s].x, vk[s].x, fmaf(pk[s].y, vk[s].y, fmaf(pk[s].z, vk[s].z, fmaf(pk[s].w, vk[s].w, dot))));
       }
       const float K = -0.5f * tauk * warp_sum_f(dot);
@@ -396,9 +417,9 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tri_reduce(DevPlan<T> p, int
     }
     // own rows i < m - 1: update with (v_k, w_k), then the product with v_{k+1}
     if (m > 129)
-      fused_rows<2>(B, LD, N, m - 1, m, warp, lane, vk, wk, vn, taun, pn);
+      fused_rows<2>(B, LD, N, m - 1, m, warp, lane, vk, wk, vn, pn);
     else
-      fused_rows<1>(B, LD, N, m - 1, m, warp, lane, vk, wk, vn, taun, pn);
+      fused_rows<1>(B, LD, N, m - 1, m, warp, lane, vk, wk, vn, pn);
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < 2; ++s) vk[s] = vn[s];
@@ -1276,7 +1297,9 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
   }
 }
 
-size_t tri_reduce_smem(int N) { return sizeof(float) * (static_cast<size_t>(N) * ((N + 3) & ~3) + 2 * kTriRows); }
+size_t tri_reduce_smem(int N) {
+  return sizeof(float) * (static_cast<size_t>(N) * ((N + 3) & ~3) + kTriPcol + kTriRows);
+}
 
 
 }  // namespace
