@@ -834,8 +834,8 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
       const size_t Np = static_cast<size_t>(ns_padded(nb.N));
       TRY(alloc(h, Np * Np, &nb.s.Wf));
       TRY(alloc(h, Np * Np, &nb.s.X));
-      TRY(alloc(h, Np * Np, &nb.s.Y));
       TRY(alloc(h, Np * Np, &nb.s.Xn));
+      TRY(alloc(h, 4 * ns_split_bytes(static_cast<int>(Np)), &nb.s.split));
       TRY(alloc(h, static_cast<size_t>(ns_grid(nb.N)), &nb.s.partial));
       TRY(alloc(h, 2, &nb.s.bar));
       TRY(alloc(h, 1, &nb.s.iters_out));
@@ -1382,7 +1382,8 @@ int psd_project_one(const double* in, double* out, int32_t N, void* stream, bool
       NsScratch S{};
       const size_t Np = static_cast<size_t>(ns_padded(N));
       if ((rc = alloc(h, Np * Np, &S.Wf)) != SOS_OK || (rc = alloc(h, Np * Np, &S.X)) != SOS_OK ||
-          (rc = alloc(h, Np * Np, &S.Y)) != SOS_OK || (rc = alloc(h, Np * Np, &S.Xn)) != SOS_OK ||
+          (rc = alloc(h, 4 * ns_split_bytes(static_cast<int>(Np)), &S.split)) != SOS_OK ||
+          (rc = alloc(h, Np * Np, &S.Xn)) != SOS_OK ||
           (rc = alloc(h, static_cast<size_t>(ns_grid(N)), &S.partial)) != SOS_OK || (rc = alloc(h, 2, &S.bar)) != SOS_OK ||
           (rc = alloc(h, 1, &S.iters_out)) != SOS_OK)
         break;

@@ -1132,21 +1132,25 @@ __global__ void __launch_bounds__(256, 1) k_psd_large(DevPlan<T> p, int bid, Lar
 // ---------------------------------------------------------------------------
 
 
-constexpr int kNsTM = 128, kNsTN = 64, kNsKC = 64;
+constexpr int kNsTM = 128, kNsTN = 64, kNsKC = 64, kNsStages = 3;
+constexpr uint32_t kNsABytes = kNsTM * kNsKC * 2;                  // one BF16 part of an A chunk
+constexpr uint32_t kNsBBytes = kNsTN * kNsKC * 2;                  // one BF16 part of a B chunk
+constexpr uint32_t kNsStageBytes = 3 * (kNsABytes + kNsBBytes);    // three parts of both chunks
+constexpr size_t kNsSmem = static_cast<size_t>(kNsStages) * kNsStageBytes;
 
-// Byte offset of element (r, k) of an R x kNsKC operand chunk in the core-matrix layout.
-__device__ __forceinline__ uint32_t ns_off(int r, int k) {
-  return static_cast<uint32_t>((r >> 3) * ((kNsKC / 8) * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+// The split operand layout of an Np x Np matrix (Np a multiple of 128),
+// three parts of BF16 (x = x_hi + x_mid + x_lo, each the rounding of what the
+// previous parts leave): part q, K chunk kc (64 columns), row group rg (8
+// rows) is one 1 KB strip in the no-swizzle K-major core-matrix layout (core
+// matrix (rg, k/8) at byte (k % 64 / 8) * 128, row r % 8 at + 16 (r % 8)),
+// strips ordered [q][kc][rg].  The A chunk of rows m0 .. m0 + 127 (or the B
+// chunk of rows n0 .. n0 + 63) of chunk kc is then one contiguous range, and
+// a stage of the product pipeline is six bulk copies.
+__device__ __forceinline__ size_t ns_strip(int Np, int q, int kc, int rg) {
+  return (static_cast<size_t>(q) * (Np / kNsKC) + kc) * (Np / 8) + rg;
 }
 
-// Stage rows [r0, r0 + R) x cols [k0, k0 + kNsKC) of the Np x Np FP32 matrix
-// M (Np is a multiple of 128, so the chunk is always inside) as three BF16
-// parts x = x_hi + x_mid + x_lo (each the rounding of what the previous parts
-// leave).  A thread converts 8 consecutive values (two 16-byte loads) into
-// one 16-byte core-matrix row of each part; the loads of a thread's groups
-// are issued before any is used.
-__device__ __forceinline__ void ns_split8(const float4& a, const float4& b, uint4& h, uint4& m, uint4& l) {
-  const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+__device__ __forceinline__ void ns_split8(const float (&x)[8], uint4& h, uint4& m, uint4& l) {
   __nv_bfloat16 hh[8], mm[8], ll[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -1160,99 +1164,148 @@ __device__ __forceinline__ void ns_split8(const float4& a, const float4& b, uint
   l = *reinterpret_cast<const uint4*>(ll);
 }
 
-template <int R>
-__device__ __forceinline__ void ns_stage(const float* M, int Np, int r0, int k0, unsigned char* p0, unsigned char* p1,
-                                         unsigned char* p2) {
-  constexpr int kGroups = R * (kNsKC / 8);  // 8-element groups in the chunk
-  constexpr int kPer = (kGroups + 255) / 256;
-  float4 va[kPer], vb[kPer];
-#pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    const int g = threadIdx.x + q * 256;
-    if (g < kGroups) {
-      const int r = g >> 3, c = g & 7;  // row, 8-column group
-      const float4* src = reinterpret_cast<const float4*>(M + static_cast<int64_t>(r0 + r) * Np + k0 + c * 8);
-      va[q] = __ldcg(src);
-      vb[q] = __ldcg(src + 1);
+// Entries (r, c0 .. c0 + 7) of a matrix into its split layout (c0 % 8 == 0):
+// one 16-byte core-matrix row per part.
+__device__ __forceinline__ void ns_put8(unsigned char* S, int Np, int r, int c0, const float (&x)[8]) {
+  uint4 h, m, l;
+  ns_split8(x, h, m, l);
+  const size_t o = ((c0 % kNsKC) >> 3) * 128 + (r & 7) * 16;
+  *reinterpret_cast<uint4*>(S + ns_strip(Np, 0, c0 / kNsKC, r >> 3) * 1024 + o) = h;
+  *reinterpret_cast<uint4*>(S + ns_strip(Np, 1, c0 / kNsKC, r >> 3) * 1024 + o) = m;
+  *reinterpret_cast<uint4*>(S + ns_strip(Np, 2, c0 / kNsKC, r >> 3) * 1024 + o) = l;
+}
+
+// Entries (r, c0 + j), j < 8, of a symmetric matrix computed by this thread:
+// those on or below the diagonal go to the split layout (and to the FP32
+// copy F when given), those strictly below also to their mirror (c0 + j, r).
+// Each entry of the lower triangle is computed by exactly one CTA, so the
+// stored matrix is exactly symmetric (the iteration doubles any
+// antisymmetric part once X^T X is near I).
+__device__ __forceinline__ void ns_put_sym(unsigned char* S, float* F, int Np, int r, int c0, const float (&x)[8]) {
+  if (c0 + 7 <= r) {  // the whole group on or below the diagonal
+    ns_put8(S, Np, r, c0, x);
+    if (F) {
+      float4* dst = reinterpret_cast<float4*>(F + static_cast<int64_t>(r) * Np + c0);
+      dst[0] = make_float4(x[0], x[1], x[2], x[3]);
+      dst[1] = make_float4(x[4], x[5], x[6], x[7]);
+    }
+  } else if (c0 <= r) {  // straddles the diagonal: entries c0 .. r only
+    uint4 h, m, l;
+    ns_split8(x, h, m, l);
+    const uint16_t* ph = reinterpret_cast<const uint16_t*>(&h);
+    const uint16_t* pm = reinterpret_cast<const uint16_t*>(&m);
+    const uint16_t* pl = reinterpret_cast<const uint16_t*>(&l);
+    const size_t o = ((c0 % kNsKC) >> 3) * 128 + (r & 7) * 16;
+    for (int j = 0; j <= r - c0; ++j) {
+      reinterpret_cast<uint16_t*>(S + ns_strip(Np, 0, c0 / kNsKC, r >> 3) * 1024 + o)[j] = ph[j];
+      reinterpret_cast<uint16_t*>(S + ns_strip(Np, 1, c0 / kNsKC, r >> 3) * 1024 + o)[j] = pm[j];
+      reinterpret_cast<uint16_t*>(S + ns_strip(Np, 2, c0 / kNsKC, r >> 3) * 1024 + o)[j] = pl[j];
+      if (F) F[static_cast<int64_t>(r) * Np + c0 + j] = x[j];
     }
   }
+  // mirrors (c, r) of the entries strictly below the diagonal
+  if (c0 < r) {
+    uint4 h, m, l;
+    ns_split8(x, h, m, l);
+    const uint16_t* pp[3] = {reinterpret_cast<const uint16_t*>(&h), reinterpret_cast<const uint16_t*>(&m),
+                             reinterpret_cast<const uint16_t*>(&l)};
+    const int jn = min(8, r - c0);
+    for (int j = 0; j < jn; ++j) {
+      const int c = c0 + j;
+      const size_t o = ((r % kNsKC) >> 3) * 128 + (c & 7) * 16 + (r & 7) * 2;
 #pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    const int g = threadIdx.x + q * 256;
-    if (g < kGroups) {
-      const int r = g >> 3, c = g & 7;
-      uint4 h, m, l;
-      ns_split8(va[q], vb[q], h, m, l);
-      const uint32_t o = ns_off(r, c * 8);
-      *reinterpret_cast<uint4*>(p0 + o) = h;
-      *reinterpret_cast<uint4*>(p1 + o) = m;
-      *reinterpret_cast<uint4*>(p2 + o) = l;
+      for (int q = 0; q < 3; ++q)
+        *reinterpret_cast<uint16_t*>(S + ns_strip(Np, q, r / kNsKC, c >> 3) * 1024 + o) = pp[q][j];
+      if (F) F[static_cast<int64_t>(c) * Np + r] = x[j];
     }
   }
 }
 
-struct NsState {
-  uint64_t* mbar;      // two barriers, one per operand buffer
+// Pipeline state of the products of one CTA (thread 0 drives the copies and
+// the MMAs; every thread waits on `done`).
+struct NsPipe {
+  uint64_t* full;   // [kNsStages] bulk copies of a stage landed
+  uint64_t* empty;  // [kNsStages] MMAs that read a stage completed
+  uint64_t* done;   // all MMAs of a product completed
+  uint32_t fph[kNsStages], eph[kNsStages], dph;  // phases awaited next
+  int epend[kNsStages];                           // a commit on empty[s] not yet waited for
+  int fpend[kNsStages];                           // bulk copies into stage s not yet waited for
   uint32_t tmem;
-  uint32_t phase[2];   // phase awaited next on each barrier
-  int pending[2];      // a commit on that barrier not yet waited for
+  long long limit;  // bound of each wait, clock cycles
   bool ok;
 };
 
-constexpr size_t kNsSmem = 3 * (kNsTM + kNsTN) * kNsKC * 2;  // three parts of both operand chunks (one buffer)
-
-// acc[128 x 64] (TMEM) = A[m0.., :] * B[n0.., :]^T over k in [0, Np), with the
-// six products of the three-part split whose exponent sum is at most 2^-16.
-// Two operand buffers: the chunk k + 1 is loaded, split and stored while the
-// MMAs of chunk k run; a buffer is rewritten only after the MMAs that read it
-// (two chunks earlier) have completed.
-__device__ void ns_gemm(const float* A, const float* B, int Np, int m0, int n0, unsigned char* smem, NsState& st) {
+// acc[128 x 64] (TMEM) = A[m0.., :] B[n0.., :]^T over k in [0, Np) from the
+// split layouts, with the six products of the three-part split whose
+// exponent sum is at most 2^-16.  Three stages: thread 0 refills the stage of
+// chunk kc - 1 with chunk kc + 2 once its MMAs have completed, while the
+// MMAs of chunk kc run.  On return (every thread) the accumulator is ready,
+// or P.ok is false after an expired wait.
+__device__ void ns_gemm(const unsigned char* As, const unsigned char* Bs, int Np, int m0, int n0,
+                        unsigned char* smem, NsPipe& P) {
   constexpr uint32_t LBO = 128, SBO = (kNsKC / 8) * 128;
   constexpr uint32_t idesc = tc::idesc_bf16(kNsTM, kNsTN);
   const int pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
-  auto wait_buf = [&](int b) {  // uniform: every thread waits for the commit on barrier b
-    if (!st.pending[b]) return;
-    const bool good = st.ok ? tc::wait(st.mbar + b, st.phase[b]) : false;
-    if (good) {
-      st.phase[b] ^= 1u;
-      st.pending[b] = 0;
-    } else {
-      st.ok = false;  // left pending: the kernel's cleanup waits for it once more
-    }
-    tc::fence_after();
-  };
   const int nk = Np / kNsKC;
-  for (int kc = 0; kc < nk; ++kc) {
-    const int b = kc & 1;
-    wait_buf(b);
-    unsigned char* base = smem + b * kNsSmem;
-    unsigned char* a[3];
-    unsigned char* bb[3];
-    for (int q = 0; q < 3; ++q) a[q] = base + q * kNsTM * kNsKC * 2;
-    for (int q = 0; q < 3; ++q) bb[q] = base + 3 * kNsTM * kNsKC * 2 + q * kNsTN * kNsKC * 2;
-    const int k0 = kc * kNsKC;
-    ns_stage<kNsTM>(A, Np, m0, k0, a[0], a[1], a[2]);
-    ns_stage<kNsTN>(B, Np, n0, k0, bb[0], bb[1], bb[2]);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    const bool issue = st.ok;
-    if (threadIdx.x == 0 && issue) {
-      for (int s = 0; s < kNsKC / 16; ++s) {
-        const uint32_t so = s * 2 * LBO;
+  if (threadIdx.x == 0) {
+    // the operands were written by generic stores of other CTAs before the
+    // grid barrier this thread acquired: order that view before the bulk
+    // copies (async proxy) that read them
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    auto load = [&](int kc) {
+      const int s = kc % kNsStages;
+      if (P.epend[s]) {  // the stage's previous chunk must be consumed
+        if (P.ok) P.ok = tc::wait(P.empty + s, P.eph[s], P.limit);
+        P.eph[s] ^= 1u;
+        P.epend[s] = 0;
+      }
+      if (!P.ok) return;
+      unsigned char* base = smem + s * kNsStageBytes;
+      tc::arrive_expect_tx(P.full + s, kNsStageBytes);
+      P.fpend[s] = 1;
+      for (int q = 0; q < 3; ++q) {
+        tc::bulk_g2s(base + q * kNsABytes, As + ns_strip(Np, q, kc, m0 / 8) * 1024, kNsABytes, P.full + s);
+        tc::bulk_g2s(base + 3 * kNsABytes + q * kNsBBytes, Bs + ns_strip(Np, q, kc, n0 / 8) * 1024, kNsBBytes,
+                     P.full + s);
+      }
+    };
+    for (int kc = 0; kc < nk && kc < kNsStages; ++kc) load(kc);
+    for (int kc = 0; kc < nk && P.ok; ++kc) {
+      const int s = kc % kNsStages;
+      P.ok = tc::wait(P.full + s, P.fph[s], P.limit);
+      if (!P.ok) break;  // left pending: the kernel's cleanup waits for these copies once more
+      P.fph[s] ^= 1u;
+      P.fpend[s] = 0;
+      tc::fence_after();
+      unsigned char* base = smem + s * kNsStageBytes;
+      for (int ks = 0; ks < kNsKC / 16; ++ks) {
+        const uint32_t so = ks * 2 * LBO;
         for (int q = 0; q < 6; ++q) {
-          const uint32_t acc = (k0 > 0 || s > 0 || q > 0) ? 1u : 0u;
-          tc::mma(st.tmem, tc::desc(tc::smem_u32(a[pa[q]]) + so, LBO, SBO), tc::desc(tc::smem_u32(bb[pb[q]]) + so, LBO, SBO),
-                  idesc, acc);
+          const uint32_t acc = (kc > 0 || ks > 0 || q > 0) ? 1u : 0u;
+          tc::mma(P.tmem, tc::desc(tc::smem_u32(base + pa[q] * kNsABytes) + so, LBO, SBO),
+                  tc::desc(tc::smem_u32(base + 3 * kNsABytes + pb[q] * kNsBBytes) + so, LBO, SBO), idesc, acc);
         }
       }
-      tc::commit(st.mbar + b);
+      tc::commit(P.empty + s);
+      P.epend[s] = 1;
+      if (kc >= 1 && kc - 1 + kNsStages < nk) load(kc - 1 + kNsStages);
     }
-    if (issue) st.pending[b] = 1;
+    tc::commit(P.done);  // arrives once every MMA issued so far has completed
   }
-  wait_buf(nk & 1);        // older of the last two commits first
-  wait_buf((nk + 1) & 1);
+  __syncthreads();
+  const bool good = tc::wait(P.done, P.dph, P.limit);
+  P.dph ^= 1u;
+  // every commit on empty[] precedes the one on done: their phases have
+  // completed too (thread 0's bookkeeping)
+  if (threadIdx.x == 0)
+    for (int s = 0; s < kNsStages; ++s)
+      if (P.epend[s]) {
+        P.eph[s] ^= 1u;
+        P.epend[s] = 0;
+      }
+  tc::fence_after();
+  const int bad = __syncthreads_or(!good || (threadIdx.x == 0 && !P.ok));
+  P.ok = !bad;
 }
 
 
@@ -1265,7 +1318,7 @@ __host__ __device__ __forceinline__ int ns_tiles(int N) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch S) {
   extern __shared__ __align__(1024) unsigned char nsm[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar[2 * kNsStages + 1];
   __shared__ uint32_t tmem_base;
   __shared__ double red[40];
   const BlockDesc bd = p.blocks[bid];
@@ -1277,22 +1330,33 @@ __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch
   int32_t* err = p.err;
   const int64_t gt = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t gs = static_cast<int64_t>(G) * blockDim.x;
-  // this CTA's lower tile: row tile ti holds column tiles 0 .. 2 ti + 1
+  // this CTA's lower tile: row tile ti holds column tiles 0 .. 2 ti + 1 (the
+  // products are symmetric; the epilogues write each lower entry and its mirror)
   int ti = 0, rem = blockIdx.x;
   while (rem >= (ti + 1) * (kNsTM / kNsTN)) {
     rem -= (ti + 1) * (kNsTM / kNsTN);
     ++ti;
   }
   const int m0 = ti * kNsTM, n0 = rem * kNsTN;
+  const size_t sb = ns_split_bytes(Np);
+  unsigned char* Wsp = S.split;
+  unsigned char* Xsp = S.split + sb;
+  unsigned char* Xnsp = S.split + 2 * sb;
+  unsigned char* Ysp = S.split + 3 * sb;
 
-  NsState st;
-  st.mbar = mbar;
-  st.phase[0] = st.phase[1] = 0;
-  st.pending[0] = st.pending[1] = 0;
-  st.ok = true;
+  NsPipe P;
+  P.full = mbar;
+  P.empty = mbar + kNsStages;
+  P.done = mbar + 2 * kNsStages;
+  for (int s = 0; s < kNsStages; ++s) {
+    P.fph[s] = P.eph[s] = 0;
+    P.epend[s] = P.fpend[s] = 0;
+  }
+  P.dph = 0;
+  P.limit = p.wait_limit;
+  P.ok = true;
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar[1])));
+    for (int s = 0; s < 2 * kNsStages + 1; ++s) tc::mbar_init(mbar + s, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (threadIdx.x < 32) {
@@ -1302,129 +1366,159 @@ __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch
   }
 
   bool alive = true;
-#define NS_SYNC()                                   \
-  do {                                              \
-    tc::fence_before();                             \
-    alive = grid_barrier(S.bar, (++gen) * G, err, p.wait_limit);  \
-    tc::fence_after();                              \
+  // the split layouts written by this CTA's threads become operands of bulk
+  // copies (async proxy) in other CTAs after the barrier
+#define NS_SYNC()                                                \
+  do {                                                           \
+    asm volatile("fence.proxy.async.global;" ::: "memory");     \
+    tc::fence_before();                                          \
+    alive = grid_barrier(S.bar, (++gen) * G, err, p.wait_limit); \
+    tc::fence_after();                                           \
   } while (0)
-  // load W (unscaled, FP32) and its Frobenius norm
+  // W (unscaled, FP32, and split) and its Frobenius norm; groups of eight
+  // consecutive columns
   double nrm = 0.0;
-  for (int64_t q = gt; q < static_cast<int64_t>(Np) * Np; q += gs) {
-    const int i = static_cast<int>(q / Np), j = static_cast<int>(q - static_cast<int64_t>(i) * Np);
-    float w = 0.f;
-    if (i < N && j < N) {
-      const int ii = i >= j ? i : j, jj = i >= j ? j : i;
-      const T wv = proj_input(p, bd, packed_index(ii, jj, N), ii != jj, s_sm);
-      if (i >= j) nrm += d(wv) * d(wv);
-      w = (i == j) ? static_cast<float>(wv) : static_cast<float>(d(wv) * 0.70710678118654752440);
+  const int gpr = Np / 8;  // groups per row
+  for (int64_t g = gt; g < static_cast<int64_t>(Np) * gpr; g += gs) {
+    const int i = static_cast<int>(g / gpr), c0 = static_cast<int>(g - static_cast<int64_t>(i) * gpr) * 8;
+    float w8[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int j = c0 + t;
+      float w = 0.f;
+      if (i < N && j < N) {
+        const int ii = i >= j ? i : j, jj = i >= j ? j : i;
+        const T wv = proj_input(p, bd, packed_index(ii, jj, N), ii != jj, s_sm);
+        if (i >= j) nrm += d(wv) * d(wv);
+        w = (i == j) ? static_cast<float>(wv) : static_cast<float>(d(wv) * 0.70710678118654752440);
+      }
+      w8[t] = w;
     }
-    S.Wf[q] = w;
+    float4* dst = reinterpret_cast<float4*>(S.Wf + static_cast<int64_t>(i) * Np + c0);
+    dst[0] = make_float4(w8[0], w8[1], w8[2], w8[3]);
+    dst[1] = make_float4(w8[4], w8[5], w8[6], w8[7]);
+    ns_put8(Wsp, Np, i, c0, w8);
   }
   const double part = block_sum(nrm, red);
   if (threadIdx.x == 0) S.partial[blockIdx.x] = part;
   NS_SYNC();
-  st.tmem = tmem_base;
+  P.tmem = tmem_base;
   const int wq = (threadIdx.x >> 5) & 3;  // TMEM lane quarter of this warp
   const int chalf = (threadIdx.x >> 7);   // warps 4..7 take the upper 32 columns
   const int row = m0 + wq * 32 + (threadIdx.x & 31);
   int it = 0;
   float* X = S.X;
-  if (alive) {
-  double tot = 0.0;
-  for (unsigned c = 0; c < G; ++c) tot += __ldcg(S.partial + c);
-  const float inv = tot > 0.0 ? static_cast<float>(1.0 / sqrt(tot)) : 0.f;
-  for (int64_t q = gt; q < static_cast<int64_t>(Np) * Np; q += gs) S.X[q] = __ldcg(S.Wf + q) * inv;
-  NS_SYNC();
-
   float* Xn = S.Xn;
-  // Plain Newton-Schulz, X <- (3 X - X^3) / 2: eigenvalues of X in (0, 1]
-  // converge to sign(lambda) quadratically near 1 and grow by 1.5x per step
-  // near 0.  The optimally scaled variant (step a-dependent, a > 1) sends
-  // eigenvalues near 1 down to the current floor ell before they return; in
-  // FP32 with split-BF16 products those lose their relative accuracy there and
-  // the outer ADMM iteration stalls near a 2e-4 dual residual, so it is not used.
-  for (it = 0; alive && it < S.max_iter; ++it) {
-    // Y = X X
-    ns_gemm(X, X, Np, m0, n0, nsm, st);
-    for (int c0 = chalf * 32; c0 < chalf * 32 + 32; c0 += 8) {
-      float v[8];
-      tc::ld8(st.tmem + (static_cast<uint32_t>(wq * 32) << 16) + c0, v);
-      for (int j = 0; j < 8; ++j) {
-        const int col = n0 + c0 + j;
-        if (row >= col) {
-          S.Y[static_cast<int64_t>(row) * Np + col] = v[j];
-          S.Y[static_cast<int64_t>(col) * Np + row] = v[j];
-        }
-      }
+  if (alive) {
+    double tot = 0.0;
+    for (unsigned c = 0; c < G; ++c) tot += __ldcg(S.partial + c);
+    const float inv = tot > 0.0 ? static_cast<float>(1.0 / sqrt(tot)) : 0.f;
+    for (int64_t g = gt; g < static_cast<int64_t>(Np) * gpr; g += gs) {
+      const int i = static_cast<int>(g / gpr), c0 = static_cast<int>(g - static_cast<int64_t>(i) * gpr) * 8;
+      const float4* src = reinterpret_cast<const float4*>(S.Wf + static_cast<int64_t>(i) * Np + c0);
+      const float4 a = __ldcg(src), b = __ldcg(src + 1);
+      float x8[8] = {a.x * inv, a.y * inv, a.z * inv, a.w * inv, b.x * inv, b.y * inv, b.z * inv, b.w * inv};
+      float4* dst = reinterpret_cast<float4*>(X + static_cast<int64_t>(i) * Np + c0);
+      dst[0] = make_float4(x8[0], x8[1], x8[2], x8[3]);
+      dst[1] = make_float4(x8[4], x8[5], x8[6], x8[7]);
+      ns_put8(Xsp, Np, i, c0, x8);
     }
     NS_SYNC();
-    if (!alive) break;
-    // X_next = 1.5 X - 0.5 Y X, and |X_next - X|^2
-    ns_gemm(S.Y, X, Np, m0, n0, nsm, st);
-    double dsq = 0.0;
-    for (int c0 = chalf * 32; c0 < chalf * 32 + 32; c0 += 8) {
-      float v[8];
-      tc::ld8(st.tmem + (static_cast<uint32_t>(wq * 32) << 16) + c0, v);
-      for (int j = 0; j < 8; ++j) {
-        const int col = n0 + c0 + j;
-        if (row >= col) {
-          const float x = __ldcg(X + static_cast<int64_t>(row) * Np + col);
-          const float xn = 1.5f * x - 0.5f * v[j];
-          Xn[static_cast<int64_t>(row) * Np + col] = xn;
-          Xn[static_cast<int64_t>(col) * Np + row] = xn;
-          const double df = static_cast<double>(xn) - x;
-          dsq += (row == col ? 1.0 : 2.0) * df * df;
+
+    // Plain Newton-Schulz, X <- (3 X - X^3) / 2: eigenvalues of X in (0, 1]
+    // converge to sign(lambda) quadratically near 1 and grow by 1.5x per step
+    // near 0.  The optimally scaled variant (step a-dependent, a > 1) sends
+    // eigenvalues near 1 down to the current floor ell before they return; in
+    // FP32 with split-BF16 products those lose their relative accuracy there and
+    // the outer ADMM iteration stalls near a 2e-4 dual residual, so it is not used.
+    for (it = 0; alive && it < S.max_iter; ++it) {
+      // Y = X X
+      ns_gemm(Xsp, Xsp, Np, m0, n0, nsm, P);
+      if (!P.ok) break;
+      for (int c0 = chalf * 32; c0 < chalf * 32 + 32; c0 += 8) {
+        float v[8];
+        tc::ld8(P.tmem + (static_cast<uint32_t>(wq * 32) << 16) + c0, v);
+        ns_put_sym(Ysp, nullptr, Np, row, n0 + c0, v);
+      }
+      NS_SYNC();
+      if (!alive) break;
+      // X_next = 1.5 X - 0.5 Y X, and |X_next - X|^2
+      ns_gemm(Ysp, Xsp, Np, m0, n0, nsm, P);
+      if (!P.ok) break;
+      double dsq = 0.0;
+      for (int c0 = chalf * 32; c0 < chalf * 32 + 32; c0 += 8) {
+        float v[8];
+        tc::ld8(P.tmem + (static_cast<uint32_t>(wq * 32) << 16) + c0, v);
+        const float4* xs = reinterpret_cast<const float4*>(X + static_cast<int64_t>(row) * Np + n0 + c0);
+        const float4 a = __ldcg(xs), b = __ldcg(xs + 1);
+        const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        float xn[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          xn[j] = 1.5f * x[j] - 0.5f * v[j];
+          const int col = n0 + c0 + j;
+          const double df = static_cast<double>(xn[j]) - x[j];
+          if (row >= col) dsq += (row == col ? 1.0 : 2.0) * df * df;
         }
+        ns_put_sym(Xnsp, Xn, Np, row, n0 + c0, xn);
+      }
+      const double pd = block_sum(dsq, red);
+      if (threadIdx.x == 0) S.partial[blockIdx.x] = pd;
+      NS_SYNC();
+      if (!alive) break;
+      double dtot = 0.0;
+      for (unsigned c = 0; c < G; ++c) dtot += __ldcg(S.partial + c);
+      float* tmp = X;
+      X = Xn;
+      Xn = tmp;
+      unsigned char* tsp = Xsp;
+      Xsp = Xnsp;
+      Xnsp = tsp;
+      if (dtot <= static_cast<double>(S.tol) * S.tol * Np) {  // same decision in every CTA
+        ++it;
+        break;
       }
     }
-    const double pd = block_sum(dsq, red);
-    if (threadIdx.x == 0) S.partial[blockIdx.x] = pd;
-    NS_SYNC();
-    if (!alive) break;
-    double dtot = 0.0;
-    for (unsigned c = 0; c < G; ++c) dtot += __ldcg(S.partial + c);
-    float* tmp = X;
-    X = Xn;
-    Xn = tmp;
-    if (dtot <= static_cast<double>(S.tol) * S.tol * Np) {  // same decision in every CTA
-      ++it;
-      break;
-    }
-  }
   }
   // U = (W + W S) / 2 with S = sign(W) ~ X; outputs u = svec(U), v = u - W
-  if (alive) ns_gemm(S.Wf, X, Np, m0, n0, nsm, st);
-  if (alive && st.ok) {
-  for (int c0 = chalf * 32; c0 < chalf * 32 + 32; c0 += 8) {
-    float v[8];
-    tc::ld8(st.tmem + (static_cast<uint32_t>(wq * 32) << 16) + c0, v);
-    for (int j = 0; j < 8; ++j) {
-      const int col = n0 + c0 + j;
-      if (row >= col && row < N && col < N) {
-        const float w = __ldcg(S.Wf + static_cast<int64_t>(row) * Np + col);
-        const float u = 0.5f * (w + v[j]);
-        const int64_t kk = packed_index(row, col, N);
-        const T wv = proj_input(p, bd, kk, row != col, s_sm);
-        const T uu = (row != col) ? static_cast<T>(static_cast<double>(u) * kSqrt2) : static_cast<T>(u);
-        p.ux[bd.x_off + kk] = uu;
-        const T vv = uu - wv;
-        p.vx[bd.x_off + kk] = vv;
-        if (bd.kind == kWeighted) p.wl[bd.lr_first + kk] = d(uu) + d(vv);  // w1_hat of the next iteration (c = 0)
+  // (lower triangle: the tile entries with row >= col)
+  if (alive && P.ok) ns_gemm(Wsp, Xsp, Np, m0, n0, nsm, P);
+  if (alive && P.ok) {
+    for (int c0 = chalf * 32; c0 < chalf * 32 + 32; c0 += 8) {
+      float v[8];
+      tc::ld8(P.tmem + (static_cast<uint32_t>(wq * 32) << 16) + c0, v);
+      for (int j = 0; j < 8; ++j) {
+        const int col = n0 + c0 + j;
+        if (row >= col && row < N && col < N) {
+          const float w = __ldcg(S.Wf + static_cast<int64_t>(row) * Np + col);
+          const float u = 0.5f * (w + v[j]);
+          const int64_t kk = packed_index(row, col, N);
+          const T wv = proj_input(p, bd, kk, row != col, s_sm);
+          const T uu = (row != col) ? static_cast<T>(static_cast<double>(u) * kSqrt2) : static_cast<T>(u);
+          p.ux[bd.x_off + kk] = uu;
+          const T vv = uu - wv;
+          p.vx[bd.x_off + kk] = vv;
+          if (bd.kind == kWeighted) p.wl[bd.lr_first + kk] = d(uu) + d(vv);  // w1_hat of the next iteration (c = 0)
+        }
       }
     }
   }
-  }
 #undef NS_SYNC
-  // cleanup on every path: MMAs still in flight after a failed wait get one
-  // more bounded wait, then the tensor memory is released
-  if (!st.ok)
-    for (int b = 0; b < 2; ++b)
-      if (st.pending[b]) tc::wait(st.mbar + b, st.phase[b]);
+  // cleanup on every path: after a failed wait, MMAs still in flight get one
+  // more bounded wait (on a fresh commit), then the tensor memory is released
+  if (!P.ok) {
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < kNsStages; ++s)
+        if (P.fpend[s]) tc::wait(P.full + s, P.fph[s], P.limit);  // bulk copies still in flight
+      tc::commit(P.done);
+    }
+    __syncthreads();
+    tc::wait(P.done, P.dph, P.limit);
+  }
   tc::fence_before();
   __syncthreads();
-  if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(st.tmem), "r"(kNsTN));
-  if (!st.ok && threadIdx.x == 0) atomicExch(err, 1);
+  if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(P.tmem), "r"(kNsTN));
+  if (!P.ok && threadIdx.x == 0) atomicExch(err, 1);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *S.iters_out = it;
     p.blk_sweeps[bid] = it;
@@ -1834,18 +1928,18 @@ cudaError_t launch_persistent(const DevPlan<T>& p, const PersistArgs<TC>& a, int
 
 int ns_grid(int N) { return ns_tiles(N); }
 int ns_padded(int N) { return ns_np(N); }
-size_t ns_smem_bytes() { return 2 * kNsSmem; }
+size_t ns_smem_bytes() { return kNsSmem; }
 
 template <typename T>
 cudaError_t launch_psd_ns(const DevPlan<T>& p, int bid, int N, const NsScratch& S, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_psd_ns<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(2 * kNsSmem));
+  cudaError_t e = cudaFuncSetAttribute(k_psd_ns<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kNsSmem));
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(S.bar, 0, 2 * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ns_tiles(N));
   cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = 2 * kNsSmem;
+  cfg.dynamicSmemBytes = kNsSmem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

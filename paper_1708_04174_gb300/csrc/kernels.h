@@ -114,8 +114,10 @@ cudaError_t launch_psd_tri_part(const DevPlan<double>& p, int bid, int N, const 
 struct NsScratch {
   float* Wf = nullptr;  // W, Np x Np (Np = N rounded up to 128)
   float* X = nullptr;
-  float* Y = nullptr;
   float* Xn = nullptr;
+  // W, X, Xn, Y as three BF16 parts each, in the operand layout of the
+  // tensor-core products (ns_split_bytes(Np) bytes per matrix)
+  unsigned char* split = nullptr;
   double* partial = nullptr;  // per CTA
   uint32_t* bar = nullptr;    // grid barrier [2], zeroed by the launcher
   int32_t* iters_out = nullptr;
@@ -196,6 +198,8 @@ template <typename T>
 cudaError_t launch_psd_ns(const DevPlan<T>& p, int bid, int N, const NsScratch& S, cudaStream_t s);
 int ns_grid(int N);
 int ns_padded(int N);
+// bytes of one matrix in the split operand layout (three BF16 parts)
+__host__ __device__ inline size_t ns_split_bytes(int Np) { return static_cast<size_t>(6) * Np * Np; }
 template <typename T, typename TC>
 int persistent_max_ctas_per_sm(int max_small_n, int max_teff);
 template <typename T, typename TC>

@@ -44,8 +44,9 @@ __device__ __forceinline__ void commit(uint64_t* mbar) {
                : "memory");
 }
 
-// Bounded wait for the given phase parity of an mbarrier; false on expiry.
-__device__ __forceinline__ bool wait(uint64_t* mbar, uint32_t parity) {
+// Bounded wait for the given phase parity of an mbarrier; false on expiry
+// (after `limit` clock cycles).
+__device__ __forceinline__ bool wait(uint64_t* mbar, uint32_t parity, long long limit = kTcSpinLimitCycles) {
   uint32_t done = 0;
   const long long t0 = clock64();
   while (!done) {
@@ -54,9 +55,27 @@ __device__ __forceinline__ bool wait(uint64_t* mbar, uint32_t parity) {
         : "=r"(done)
         : "r"(smem_u32(mbar)), "r"(parity)
         : "memory");
-    if (!done && clock64() - t0 > kTcSpinLimitCycles) return false;
+    if (!done && clock64() - t0 > limit) return false;
   }
   return true;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
+}
+
+// This thread's arrival on an mbarrier that also expects `bytes` of bulk copies.
+__device__ __forceinline__ void arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to this CTA's shared memory, completing on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
