@@ -1133,6 +1133,7 @@ __global__ void __launch_bounds__(256, 1) k_psd_large(DevPlan<T> p, int bid, Lar
 
 
 constexpr int kNsTM = 128, kNsTN = 64, kNsKC = 64, kNsStages = 3;
+constexpr uint32_t kNsStrip = 8 * kNsKC * 2;                      // bytes of an 8-row strip of a K chunk
 constexpr uint32_t kNsABytes = kNsTM * kNsKC * 2;                  // one BF16 part of an A chunk
 constexpr uint32_t kNsBBytes = kNsTN * kNsKC * 2;                  // one BF16 part of a B chunk
 constexpr uint32_t kNsStageBytes = 3 * (kNsABytes + kNsBBytes);    // three parts of both chunks
@@ -1140,10 +1141,10 @@ constexpr size_t kNsSmem = static_cast<size_t>(kNsStages) * kNsStageBytes;
 
 // The split operand layout of an Np x Np matrix (Np a multiple of 128),
 // three parts of BF16 (x = x_hi + x_mid + x_lo, each the rounding of what the
-// previous parts leave): part q, K chunk kc (64 columns), row group rg (8
-// rows) is one 1 KB strip in the no-swizzle K-major core-matrix layout (core
-// matrix (rg, k/8) at byte (k % 64 / 8) * 128, row r % 8 at + 16 (r % 8)),
-// strips ordered [q][kc][rg].  The A chunk of rows m0 .. m0 + 127 (or the B
+// previous parts leave): part q, K chunk kc (kNsKC columns), row group rg (8
+// rows) is one strip of kNsStrip bytes in the no-swizzle K-major
+// core-matrix layout (core matrix (rg, k/8) at byte (k % kNsKC / 8) * 128,
+// row r % 8 at + 16 (r % 8)), strips ordered [q][kc][rg].  The A chunk of rows m0 .. m0 + 127 (or the B
 // chunk of rows n0 .. n0 + 63) of chunk kc is then one contiguous range, and
 // a stage of the product pipeline is six bulk copies.
 __device__ __forceinline__ size_t ns_strip(int Np, int q, int kc, int rg) {
@@ -1170,18 +1171,15 @@ __device__ __forceinline__ void ns_put8(unsigned char* S, int Np, int r, int c0,
   uint4 h, m, l;
   ns_split8(x, h, m, l);
   const size_t o = ((c0 % kNsKC) >> 3) * 128 + (r & 7) * 16;
-  *reinterpret_cast<uint4*>(S + ns_strip(Np, 0, c0 / kNsKC, r >> 3) * 1024 + o) = h;
-  *reinterpret_cast<uint4*>(S + ns_strip(Np, 1, c0 / kNsKC, r >> 3) * 1024 + o) = m;
-  *reinterpret_cast<uint4*>(S + ns_strip(Np, 2, c0 / kNsKC, r >> 3) * 1024 + o) = l;
+  *reinterpret_cast<uint4*>(S + ns_strip(Np, 0, c0 / kNsKC, r >> 3) * kNsStrip + o) = h;
+  *reinterpret_cast<uint4*>(S + ns_strip(Np, 1, c0 / kNsKC, r >> 3) * kNsStrip + o) = m;
+  *reinterpret_cast<uint4*>(S + ns_strip(Np, 2, c0 / kNsKC, r >> 3) * kNsStrip + o) = l;
 }
 
-// Entries (r, c0 + j), j < 8, of a symmetric matrix computed by this thread:
-// those on or below the diagonal go to the split layout (and to the FP32
-// copy F when given), those strictly below also to their mirror (c0 + j, r).
-// Each entry of the lower triangle is computed by exactly one CTA, so the
-// stored matrix is exactly symmetric (the iteration doubles any
-// antisymmetric part once X^T X is near I).
-__device__ __forceinline__ void ns_put_sym(unsigned char* S, float* F, int Np, int r, int c0, const float (&x)[8]) {
+// Entries (r, c0 + j), j < 8, of a symmetric matrix computed by this thread,
+// those on or below the diagonal, to the split layout (and to the FP32 copy
+// F when given).  Their mirrors are written by ns_put_mirror.
+__device__ __forceinline__ void ns_put_lower(unsigned char* S, float* F, int Np, int r, int c0, const float (&x)[8]) {
   if (c0 + 7 <= r) {  // the whole group on or below the diagonal
     ns_put8(S, Np, r, c0, x);
     if (F) {
@@ -1197,26 +1195,50 @@ __device__ __forceinline__ void ns_put_sym(unsigned char* S, float* F, int Np, i
     const uint16_t* pl = reinterpret_cast<const uint16_t*>(&l);
     const size_t o = ((c0 % kNsKC) >> 3) * 128 + (r & 7) * 16;
     for (int j = 0; j <= r - c0; ++j) {
-      reinterpret_cast<uint16_t*>(S + ns_strip(Np, 0, c0 / kNsKC, r >> 3) * 1024 + o)[j] = ph[j];
-      reinterpret_cast<uint16_t*>(S + ns_strip(Np, 1, c0 / kNsKC, r >> 3) * 1024 + o)[j] = pm[j];
-      reinterpret_cast<uint16_t*>(S + ns_strip(Np, 2, c0 / kNsKC, r >> 3) * 1024 + o)[j] = pl[j];
+      reinterpret_cast<uint16_t*>(S + ns_strip(Np, 0, c0 / kNsKC, r >> 3) * kNsStrip + o)[j] = ph[j];
+      reinterpret_cast<uint16_t*>(S + ns_strip(Np, 1, c0 / kNsKC, r >> 3) * kNsStrip + o)[j] = pm[j];
+      reinterpret_cast<uint16_t*>(S + ns_strip(Np, 2, c0 / kNsKC, r >> 3) * kNsStrip + o)[j] = pl[j];
       if (F) F[static_cast<int64_t>(r) * Np + c0 + j] = x[j];
     }
   }
-  // mirrors (c, r) of the entries strictly below the diagonal
-  if (c0 < r) {
-    uint4 h, m, l;
-    ns_split8(x, h, m, l);
-    const uint16_t* pp[3] = {reinterpret_cast<const uint16_t*>(&h), reinterpret_cast<const uint16_t*>(&m),
-                             reinterpret_cast<const uint16_t*>(&l)};
-    const int jn = min(8, r - c0);
-    for (int j = 0; j < jn; ++j) {
-      const int c = c0 + j;
-      const size_t o = ((r % kNsKC) >> 3) * 128 + (c & 7) * 16 + (r & 7) * 2;
+}
+
+// Mirrors of the strictly-lower entries of this CTA's 128 x 64 tile (rows
+// m0.., columns n0..), staged in shared memory T[128][65] by the epilogue:
+// entry (c, r) = T[r - m0][c - n0] for r > c, written as rows c of the
+// split layout (eight consecutive r per 16-byte store) and of F.  Each entry
+// of the lower triangle is computed by exactly one CTA, so the stored matrix
+// is exactly symmetric (the iteration doubles any antisymmetric part once
+// X^T X is near I).  Call with the whole CTA after a barrier that made T
+// visible.
+__device__ __forceinline__ void ns_put_mirror(unsigned char* S, float* F, int Np, int m0, int n0, const float* T) {
+  for (int g = threadIdx.x; g < kNsTN * (kNsTM / 8); g += blockDim.x) {
+    const int cl = g % kNsTN, rg = g / kNsTN;  // consecutive threads: consecutive columns (no bank conflicts)
+    const int c = n0 + cl, r0 = m0 + 8 * rg;
+    if (r0 + 7 <= c) continue;  // no entry of the group below the diagonal
+    float x[8];
 #pragma unroll
-      for (int q = 0; q < 3; ++q)
-        *reinterpret_cast<uint16_t*>(S + ns_strip(Np, q, r / kNsKC, c >> 3) * 1024 + o) = pp[q][j];
-      if (F) F[static_cast<int64_t>(c) * Np + r] = x[j];
+    for (int t = 0; t < 8; ++t) x[t] = T[(8 * rg + t) * (kNsTN + 1) + cl];
+    if (r0 > c) {  // all eight strictly below
+      ns_put8(S, Np, c, r0, x);
+      if (F) {
+        float4* dst = reinterpret_cast<float4*>(F + static_cast<int64_t>(c) * Np + r0);
+        dst[0] = make_float4(x[0], x[1], x[2], x[3]);
+        dst[1] = make_float4(x[4], x[5], x[6], x[7]);
+      }
+    } else {
+      uint4 h, m, l;
+      ns_split8(x, h, m, l);
+      const uint16_t* pp[3] = {reinterpret_cast<const uint16_t*>(&h), reinterpret_cast<const uint16_t*>(&m),
+                               reinterpret_cast<const uint16_t*>(&l)};
+      const size_t o = ((r0 % kNsKC) >> 3) * 128 + (c & 7) * 16;
+      for (int t = 0; t < 8; ++t) {
+        if (r0 + t <= c) continue;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          reinterpret_cast<uint16_t*>(S + ns_strip(Np, q, r0 / kNsKC, c >> 3) * kNsStrip + o)[t] = pp[q][t];
+        if (F) F[static_cast<int64_t>(c) * Np + r0 + t] = x[t];
+      }
     }
   }
 }
@@ -1237,9 +1259,9 @@ struct NsPipe {
 
 // acc[128 x 64] (TMEM) = A[m0.., :] B[n0.., :]^T over k in [0, Np) from the
 // split layouts, with the six products of the three-part split whose
-// exponent sum is at most 2^-16.  Three stages: thread 0 refills the stage of
-// chunk kc - 1 with chunk kc + 2 once its MMAs have completed, while the
-// MMAs of chunk kc run.  On return (every thread) the accumulator is ready,
+// exponent sum is at most 2^-16.  kNsStages stages: thread 0 refills the
+// stage of chunk kc - 1 with chunk kc - 1 + kNsStages once its MMAs have
+// completed, while the MMAs of chunk kc run.  On return (every thread) the accumulator is ready,
 // or P.ok is false after an expired wait.
 __device__ void ns_gemm(const unsigned char* As, const unsigned char* Bs, int Np, int m0, int n0,
                         unsigned char* smem, NsPipe& P) {
@@ -1264,8 +1286,8 @@ __device__ void ns_gemm(const unsigned char* As, const unsigned char* Bs, int Np
       tc::arrive_expect_tx(P.full + s, kNsStageBytes);
       P.fpend[s] = 1;
       for (int q = 0; q < 3; ++q) {
-        tc::bulk_g2s(base + q * kNsABytes, As + ns_strip(Np, q, kc, m0 / 8) * 1024, kNsABytes, P.full + s);
-        tc::bulk_g2s(base + 3 * kNsABytes + q * kNsBBytes, Bs + ns_strip(Np, q, kc, n0 / 8) * 1024, kNsBBytes,
+        tc::bulk_g2s(base + q * kNsABytes, As + ns_strip(Np, q, kc, m0 / 8) * kNsStrip, kNsABytes, P.full + s);
+        tc::bulk_g2s(base + 3 * kNsABytes + q * kNsBBytes, Bs + ns_strip(Np, q, kc, n0 / 8) * kNsStrip, kNsBBytes,
                      P.full + s);
       }
     };
@@ -1406,6 +1428,9 @@ __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch
   const int wq = (threadIdx.x >> 5) & 3;  // TMEM lane quarter of this warp
   const int chalf = (threadIdx.x >> 7);   // warps 4..7 take the upper 32 columns
   const int row = m0 + wq * 32 + (threadIdx.x & 31);
+  // an epilogue stages its tile for the mirror writes in the product
+  // pipeline's shared memory, which no copy targets between products
+  float* tile = reinterpret_cast<float*>(nsm);
   int it = 0;
   float* X = S.X;
   float* Xn = S.Xn;
@@ -1438,31 +1463,43 @@ __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch
       for (int c0 = chalf * 32; c0 < chalf * 32 + 32; c0 += 8) {
         float v[8];
         tc::ld8(P.tmem + (static_cast<uint32_t>(wq * 32) << 16) + c0, v);
-        ns_put_sym(Ysp, nullptr, Np, row, n0 + c0, v);
+        ns_put_lower(Ysp, nullptr, Np, row, n0 + c0, v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) tile[(row - m0) * (kNsTN + 1) + c0 + j] = v[j];
       }
+      __syncthreads();
+      ns_put_mirror(Ysp, nullptr, Np, m0, n0, tile);
       NS_SYNC();
       if (!alive) break;
       // X_next = 1.5 X - 0.5 Y X, and |X_next - X|^2
       ns_gemm(Ysp, Xsp, Np, m0, n0, nsm, P);
       if (!P.ok) break;
-      double dsq = 0.0;
+      float dsq = 0.f;  // FP32: the FP64 pipe is 1/64 of the FP32 one here
+      float4 xq[8];     // this thread's 32 entries of X, loaded together
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        xq[q] = __ldcg(reinterpret_cast<const float4*>(X + static_cast<int64_t>(row) * Np + n0 + chalf * 32) + q);
+#pragma unroll
       for (int c0 = chalf * 32; c0 < chalf * 32 + 32; c0 += 8) {
         float v[8];
         tc::ld8(P.tmem + (static_cast<uint32_t>(wq * 32) << 16) + c0, v);
-        const float4* xs = reinterpret_cast<const float4*>(X + static_cast<int64_t>(row) * Np + n0 + c0);
-        const float4 a = __ldcg(xs), b = __ldcg(xs + 1);
+        const float4 a = xq[(c0 - chalf * 32) / 4], b = xq[(c0 - chalf * 32) / 4 + 1];
         const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
         float xn[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           xn[j] = 1.5f * x[j] - 0.5f * v[j];
           const int col = n0 + c0 + j;
-          const double df = static_cast<double>(xn[j]) - x[j];
-          if (row >= col) dsq += (row == col ? 1.0 : 2.0) * df * df;
+          const float df = xn[j] - x[j];
+          if (row >= col) dsq = fmaf((row == col ? 1.f : 2.f) * df, df, dsq);
         }
-        ns_put_sym(Xnsp, Xn, Np, row, n0 + c0, xn);
+        ns_put_lower(Xnsp, Xn, Np, row, n0 + c0, xn);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) tile[(row - m0) * (kNsTN + 1) + c0 + j] = xn[j];
       }
-      const double pd = block_sum(dsq, red);
+      __syncthreads();
+      ns_put_mirror(Xnsp, Xn, Np, m0, n0, tile);
+      const double pd = block_sum(static_cast<double>(dsq), red);
       if (threadIdx.x == 0) S.partial[blockIdx.x] = pd;
       NS_SYNC();
       if (!alive) break;
