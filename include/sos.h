@@ -392,12 +392,16 @@ int sos_launches_per_iteration(const sos_handle* h);
  * z = L^-T L^-1 y (eq. (28)), 7 = sigma_2 = x - P^-1 A_L z, 8 = per-instance
  * scalars (eq. (24b), (25)) and free variables, 9 = u_y, v_y and u_hat_2
  * rows; and single kernels of the large-block projection (stage 2 is
- * 10..14 in order): 10 = gather of W into a dense FP32 copy, 11 = Householder
- * reduction to tridiagonal form, 12 = eigenvectors of the tridiagonal matrix
- * mapped back, 13 = FP64 refinement and reconstruction (10..13 do nothing
+ * 15, 10..14 in that order): 15 = warm attempt, the FP64 refinement and
+ * reconstruction started from the previous iteration's eigenvectors (it
+ * does nothing unless the last iteration left them and no cool-down after
+ * a failed attempt is running; when it succeeds, 10..14 do nothing),
+ * 10 = gather of W into a dense FP32 copy, 11 = Householder reduction to
+ * tridiagonal form, 12 = eigenvectors of the tridiagonal matrix mapped
+ * back, 13 = FP64 refinement and reconstruction (10..13 and 15 do nothing
  * for blocks that the FP64 tridiagonal path does not take), 14 = grid
  * Jacobi kernel (the whole projection of those blocks; after a successful
- * tridiagonal path it does nothing).  Stages 4..14 run out of order leave
+ * tridiagonal path it does nothing).  Stages 4..15 run out of order leave
  * the iterate meaningless; they exist to time one kernel.
  * sos_stage_bytes gives the algorithmic bytes of one launch of a stage:
  * every array element the stage has to read or write, counted once (the

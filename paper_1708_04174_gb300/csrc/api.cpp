@@ -71,7 +71,7 @@ struct sos_handle {
   int64_t iter_count = 0;
   int32_t* blk_sweeps = nullptr;  // device
   int32_t large_grid_best = 0;    // grid chosen for the cooperative Jacobi kernel
-  int64_t stage_bytes[15] = {0};  // algorithmic bytes of each profiling stage
+  int64_t stage_bytes[16] = {0};  // algorithmic bytes of each profiling stage
   std::vector<int32_t> row_perm;  // device row q holds the constraint row row_perm[q]
   int64_t* cat_map = nullptr;     // device iterate exchange: source of each concatenated position (lazy)
   int64_t cat_total = 0;
@@ -253,7 +253,7 @@ cudaError_t enqueue_stage(sos_handle* h, const DevPlan<T>& p, std::vector<LargeB
                           const SmallWarm<TC>& wm, int stage) {
   cudaError_t e = cudaSuccess;
   if (stage >= 4 && stage <= 9) return launch_affine_part<T>(p, h->shape, stage - 4, h->stream);
-  if (stage >= 10 && stage <= 14) {
+  if (stage >= 10 && stage <= 15) {
     for (auto& lb : large) {
       e = launch_psd_large_part<T, TC>(p, lb.bid, lb.N, lb.scratch, lb.grid, stage - 10, h->stream);
       if (e != cudaSuccess) return e;
@@ -818,6 +818,9 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
   if (h->precision == SOS_PREC_FP64) {
     TRY(make_devplan(h, c, max_teff, h->d64));
     TRY(make_large(h, h->large64, large));
+    // the iterations of a solve first try each tridiagonal-path block's
+    // refinement from the previous iteration's eigenvectors
+    for (auto& lb : h->large64) lb.scratch.tri_warm = 1;
     CK((prepare_kernels<double, double>(max_small, max_teff)));
   } else {
     // FP32 projections: large blocks by Newton-Schulz on the tensor cores
@@ -1475,7 +1478,7 @@ int sos_launches_per_iteration(const sos_handle* h) {
   int affine = h->TL > 0 ? 6 : 4;
   if (h->TL > 0 && woodbury_wide(h->n_inst, teff)) affine += 1;
   int large = 0;
-  for (const auto& lb : h->large64) large += tri_path(lb.N) ? 5 : 1;  // gather, reduce, vectors, recon, Jacobi
+  for (const auto& lb : h->large64) large += tri_path(lb.N) ? (lb.scratch.tri_warm ? 6 : 5) : 1;  // warm attempt, gather, reduce, vectors, recon, Jacobi
   return affine + static_cast<int>(h->small.size()) + large +
          static_cast<int>(h->large32.size() + h->ns_large.size());
 }
@@ -1483,13 +1486,13 @@ int sos_launches_per_iteration(const sos_handle* h) {
 void* sos_stream(sos_handle* h) { return h ? static_cast<void*>(h->stream) : nullptr; }
 
 int sos_stage_bytes(const sos_handle* h, int32_t stage, int64_t* bytes) {
-  if (!h || !bytes || stage < 0 || stage > 14) return SOS_ERR_INVALID_ARG;
+  if (!h || !bytes || stage < 0 || stage > 15) return SOS_ERR_INVALID_ARG;
   *bytes = h->stage_bytes[stage];
   return SOS_OK;
 }
 
 int sos_run_stage(sos_handle* h, int32_t stage) {
-  if (!h || stage < 0 || stage > 14) return SOS_ERR_INVALID_ARG;
+  if (!h || stage < 0 || stage > 15) return SOS_ERR_INVALID_ARG;
   cudaError_t e = enqueue_any(h, stage);
   if (e != cudaSuccess) return set_err(h, SOS_ERR_CUDA, std::string("stage launch: ") + cudaGetErrorString(e));
   return SOS_OK;

@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(256) k_tri_gather(DevPlan<T> p, int bid, Large
   __shared__ double red[40];
   const BlockDesc bd = p.blocks[bid];
   if (!p.active[bd.inst]) return;
+  if (L.tri_warm && __ldcg(L.flags) == 1) return;  // the warm attempt projected the block
   const int N = bd.N, LD = (N + 3) & ~3;
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), nwg = gridDim.x * (blockDim.x / 32);
@@ -278,6 +279,7 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_tri_reduce(DevPlan<T> p, int
   __shared__ double redd[40];
   const BlockDesc bd = p.blocks[bid];
   if (!p.active[bd.inst]) return;
+  if (L.tri_warm && __ldcg(L.flags) == 1) return;  // the warm attempt projected the block
   const int N = bd.N, LD = (N + 3) & ~3;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float* B = tsm;
@@ -493,6 +495,7 @@ __global__ void __launch_bounds__(kVecThreads) k_tri_vectors(DevPlan<double> p, 
   __shared__ float s_g[3][kVecThreads / 32];
   const BlockDesc bd = p.blocks[bid];
   if (!p.active[bd.inst]) return;
+  if (L.tri_warm && __ldcg(L.flags) == 1) return;  // the warm attempt projected the block
   const int N = bd.N, ldu = vec_ld(N);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int nw = kVecThreads / 32;
@@ -1114,16 +1117,41 @@ __device__ bool grid_max(double v, double* red, LargeScratch<double>& L, unsigne
 __device__ void hand_over(LargeScratch<double>& L, bool warm) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     L.flags[0] = 0;
+    L.flags[3] = 0;
     *L.warm = warm ? 1 : 0;
   }
 }
 
+// A warm attempt that gave up: the cold path (gather, reduction,
+// eigenvectors, refinement) projects the block, and the next attempt waits
+// twice as many iterations as this one did (16 the first time, at most 1024).
+__device__ void warm_abort(LargeScratch<double>& L) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    L.flags[0] = 0;
+    const int wait = min(max(2 * L.flags[4], 16), 1024);
+    L.flags[4] = wait;
+    L.flags[1] = wait;
+  }
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid, LargeScratch<double> L) {
+__global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid, LargeScratch<double> L,
+                                                           int warm_mode) {
   __shared__ double sA[16 * (kKC + 1)], sB[kKC * (24 + 1)];
   __shared__ double red[40];
   const BlockDesc bd = p.blocks[bid];
   if (!p.active[bd.inst]) return;
+  if (warm_mode) {
+    // start from the previous iteration's eigenvectors (kept in L.V) when
+    // they are there and no cool-down is running; otherwise leave the block
+    // to the cold path launched after this kernel
+    if (!(__ldcg(L.flags + 3) == 1 && __ldcg(L.flags + 1) == 0)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) L.flags[0] = 0;
+      return;
+    }
+  } else if (L.tri_warm && __ldcg(L.flags) == 1) {
+    return;  // the warm attempt of this iteration projected the block
+  }
   const int N = bd.N, Np = N + (N & 1);
   const unsigned G = gridDim.x;
   unsigned gen = 0;
@@ -1164,7 +1192,10 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
       const double prev = gm;
       if (!grid_max(rmax, red, L, gen, err, p.wait_limit, gm)) return;
       if (!(gm <= 0.25) || (ns > 0 && !(gm < prev)) || ns == 6) {  // not converging
-        hand_over(L, false);
+        if (warm_mode)
+          warm_abort(L);
+        else
+          hand_over(L, false);
         return;
       }
       if (gm <= 1e-15) break;
@@ -1251,7 +1282,12 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
     f2 = block_sum(f2, red);
     const double wn = sqrt(f2);
     if (a <= 1e-3 && rk <= 1e-13 * wn && sc <= 1e-14 * wn) break;
-    if (pass == 2) {  // still not accurate: the Jacobi kernel finishes from these eigenvectors
+    if (warm_mode && ((pass == 0 && (a > 1e-2 || sc > 1e-8 * wn)) || pass == 3)) {
+      // the previous eigenvectors are too far for a few Newton passes
+      warm_abort(L);
+      return;
+    }
+    if (!warm_mode && pass == 2) {  // still not accurate: the Jacobi kernel finishes from these eigenvectors
       if (Vc != L.V)
         for (int64_t q = gt; q < static_cast<int64_t>(N) * Np; q += gs) L.V[q] = __ldcg(Vc + q);
       hand_over(L, true);
@@ -1289,8 +1325,21 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
     if (bd.kind == kWeighted) p.wl[bd.lr_first + kk] = d(u) + d(vv);  // w1_hat of the next iteration (c = 0)
   };
   gemm_sym<false, true>(L.T1, Vc, static_cast<double*>(nullptr), N, Np, emit, sA, sB);
+  // keep V for the next iteration's warm attempt (L.V last held M, which the
+  // product above has consumed)
+  if (L.tri_warm && Vc != L.V)
+    for (int64_t q = gt; q < static_cast<int64_t>(N) * Np; q += gs) L.V[q] = __ldcg(Vc + q);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     L.flags[0] = 1;
+    L.flags[3] = 1;
+    if (warm_mode) {
+      L.flags[1] = 0;  // stay warm
+    } else if (L.flags[4] == 0) {
+      L.flags[4] = 16;  // first cold projection: the first attempt waits 16 iterations
+      L.flags[1] = 16;
+    } else if (L.flags[1] > 0) {
+      --L.flags[1];
+    }
     *L.sweeps_out = 0;
     p.blk_sweeps[bid] = work;
     *L.warm = 0;
@@ -1325,7 +1374,9 @@ cudaError_t launch_psd_tri_part(const DevPlan<double>& p, int bid, int N, const 
       k_tri_vectors<<<(N + kVecThreads / 32 - 1) / (kVecThreads / 32), kVecThreads, sm2, s>>>(p, bid, L);
       return cudaGetLastError();
     }
-    case 3: {
+    case 3:
+    case 4: {  // 3: refinement after the cold path; 4: warm attempt from the previous eigenvectors
+      const int warm_mode = part == 4 ? 1 : 0;
       e = cudaMemsetAsync(L.bar, 0, 2 * sizeof(uint32_t), s);
       if (e != cudaSuccess) return e;
       cudaLaunchConfig_t cfg = {};
@@ -1338,7 +1389,7 @@ cudaError_t launch_psd_tri_part(const DevPlan<double>& p, int bid, int N, const 
       attr[0].val.cooperative = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      return cudaLaunchKernelEx(&cfg, k_tri_recon<double>, p, bid, L);
+      return cudaLaunchKernelEx(&cfg, k_tri_recon<double>, p, bid, L, warm_mode);
     }
     default:
       return cudaErrorInvalidValue;
@@ -1347,6 +1398,10 @@ cudaError_t launch_psd_tri_part(const DevPlan<double>& p, int bid, int N, const 
 
 cudaError_t launch_psd_tri(const DevPlan<double>& p, int bid, int N, const LargeScratch<double>& L, int grid,
                            cudaStream_t s) {
+  if (L.tri_warm) {
+    const cudaError_t e = launch_psd_tri_part(p, bid, N, L, grid, 4, s);
+    if (e != cudaSuccess) return e;
+  }
   for (int part = 0; part < 4; ++part) {
     const cudaError_t e = launch_psd_tri_part(p, bid, N, L, grid, part, s);
     if (e != cudaSuccess) return e;

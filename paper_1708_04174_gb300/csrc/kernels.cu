@@ -1872,12 +1872,13 @@ size_t large_smem_bytes(int N, size_t es) {
 template <typename T, typename TC>
 cudaError_t launch_psd_large_part(const DevPlan<T>& p, int bid, int N, const LargeScratch<TC>& ls, int grid,
                                   int part, cudaStream_t s) {
-  if (part < 4) {
+  if (part < 4 || part == 5) {  // 5: the warm attempt of the tridiagonal path
     if constexpr (sizeof(T) == 8 && sizeof(TC) == 8) {
-      if (tri_path(N)) return launch_psd_tri_part(p, bid, N, ls, grid, part, s);
+      if (tri_path(N) && (part < 4 || ls.tri_warm)) return launch_psd_tri_part(p, bid, N, ls, grid, part == 5 ? 4 : part, s);
     }
     return cudaSuccess;
   }
+  if (part != 4) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(ls.bar, 0, 2 * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -1896,7 +1897,7 @@ cudaError_t launch_psd_large_part(const DevPlan<T>& p, int bid, int N, const Lar
 template <typename T, typename TC>
 cudaError_t launch_psd_large(const DevPlan<T>& p, int bid, int N, const LargeScratch<TC>& ls, int grid,
                              cudaStream_t s) {
-  for (int part = 0; part < 5; ++part) {
+  for (int part : {5, 0, 1, 2, 3, 4}) {
     const cudaError_t e = launch_psd_large_part<T, TC>(p, bid, N, ls, grid, part, s);
     if (e != cudaSuccess) return e;
   }

@@ -82,11 +82,15 @@ struct LargeScratch {
   T* V = nullptr;    // eigenvectors, kept across iterations (warm start)
   T* T1 = nullptr;   // GEMM temporary
   double* partial = nullptr;   // large_partials_size(grid, N) doubles
-  int32_t* flags = nullptr;    // [0]: 1 if the tridiagonal path projected the block in this iteration
+  // [0]: 1 if the tridiagonal path projected the block in this iteration;
+  // with tri_warm, [1]: iterations before the next warm attempt, [3]: 1 if V
+  // holds the last iteration's eigenvectors, [4]: the last wait
+  int32_t* flags = nullptr;
   uint32_t* bar = nullptr;     // grid barrier: [arrivals, released generation], zeroed before each launch
   int32_t* sweeps_out = nullptr;  // number of sweeps of the last launch
   int32_t* warm = nullptr;     // 1 if V holds the previous eigenvectors
   int32_t warm_limit = 1024;   // cold restart after this many warm iterations
+  int32_t tri_warm = 0;        // 1: each iteration first tries the refinement from the last eigenvectors
 };
 
 constexpr int kMaxSweeps = 40;
@@ -106,7 +110,8 @@ __host__ __device__ constexpr bool tri_path(int N) { return N >= kTriMinN && N <
 cudaError_t launch_psd_tri(const DevPlan<double>& p, int bid, int N, const LargeScratch<double>& L, int grid,
                            cudaStream_t s);
 // one kernel of that path (profiling): 0 gather, 1 reduction, 2 eigenvectors,
-// 3 FP64 refinement and reconstruction
+// 3 FP64 refinement and reconstruction, 4 the warm attempt (refinement from
+// the last iteration's eigenvectors, launched first when tri_warm is set)
 cudaError_t launch_psd_tri_part(const DevPlan<double>& p, int bid, int N, const LargeScratch<double>& L, int grid,
                                 int part, cudaStream_t s);
 
@@ -185,7 +190,8 @@ cudaError_t launch_psd_large(const DevPlan<T>& p, int bid, int N, const LargeScr
                              cudaStream_t s);
 // one kernel of the large-block projection (profiling): parts 0..3 the
 // tridiagonal path (FP64 form, kTriMinN <= N <= kTriMaxN), part 4 the grid
-// Jacobi kernel (which does nothing after a successful tridiagonal path)
+// Jacobi kernel (which does nothing after a successful tridiagonal path),
+// part 5 the warm attempt of the tridiagonal path (launched first)
 template <typename T, typename TC>
 cudaError_t launch_psd_large_part(const DevPlan<T>& p, int bid, int N, const LargeScratch<TC>& ls, int grid,
                                   int part, cudaStream_t s);

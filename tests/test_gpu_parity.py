@@ -112,6 +112,23 @@ def test_fp64_large_block_config1(capi):
     assert rel(vg, vo) < 1e-9, rel(vg, vo)
 
 
+def test_fp64_config1_warm_attempts_keep_parity(capi):
+    """Config 1 over 240 iterations: from about iteration 17 on, each
+    iteration first refines the previous iteration's eigenvectors (the cold
+    tridiagonal path runs only when that attempt gives up); the FP64 iterates
+    stay within 1e-9 of the oracle."""
+    prog = W.ball_pop(20, 0)
+    iters = 240
+    uo, vo = oracle_packed(prog, iters)
+    s = capi.Solver(prog, precision=capi.PREC_FP64)
+    s.iterate(iters)
+    s.sync()
+    ug, vg = s.get_iterate()
+    s.close()
+    assert rel(ug, uo) < 1e-9, rel(ug, uo)
+    assert rel(vg, vo) < 1e-9, rel(vg, vo)
+
+
 def test_fp64_config1_solve_to_1e6(capi):
     """Constrained quartic POP n = 20 (Gram 231 + weighted 21) solved to a
     1e-6 residual: the same number of iterations as the oracle (same checks

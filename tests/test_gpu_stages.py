@@ -38,7 +38,7 @@ def test_stage_bytes_consistent(capi):
         s.run_stage(k)
     s.sync()
     with pytest.raises(RuntimeError):
-        s.stage_bytes(15)
+        s.stage_bytes(16)
     s.close()
 
 
