@@ -242,6 +242,7 @@ int make_large(sos_handle* h, std::vector<LargeBlock<T>>& out, const std::vector
     TRY(alloc(h, 2, &lb.scratch.bar));
     TRY(alloc(h, 1, &lb.scratch.sweeps_out));
     TRY(alloc(h, 1, &lb.scratch.warm));
+    if (sizeof(T) == 8 && tri_path(lb.N)) TRY(alloc(h, 5 * Np * Np, &lb.scratch.F32));
     lb.scratch.warm_limit = h->warm64.limit;  // same restart period as the small blocks
     out.push_back(lb);
   }

@@ -888,14 +888,14 @@ constexpr int kKC = 16;
 // t / TM + 8 q.  op(X) = X^T where the flag is set.  xb(k, j, x) maps an
 // element of op(B) as it is staged.  The next K chunk is loaded into
 // registers while the current one is multiplied.
-template <int TM, int TN, bool TA, bool TB, class XB>
-__device__ __forceinline__ void gemm_tile(const double* A, const double* B, int ld, int n, int i0, int j0, XB xb,
-                                          double (&acc)[TM * TN / kRecThreads], double* sA, double* sB) {
+template <typename F, int TM, int TN, bool TA, bool TB, class XB>
+__device__ __forceinline__ void gemm_tile(const F* A, const F* B, int ld, int n, int i0, int j0, XB xb,
+                                          F (&acc)[TM * TN / kRecThreads], F* sA, F* sB) {
   constexpr int PT = TM * TN / kRecThreads;
   constexpr int LA = TM * kKC / kRecThreads, LB = kKC * TN / kRecThreads;
   static_assert(LA * kRecThreads == TM * kKC && LB * kRecThreads == kKC * TN, "tile shape");
   const int t = threadIdx.x, r = t % TM, g = t / TM;
-  double ra[LA], rb[LB];
+  F ra[LA], rb[LB];
   auto load = [&](int k0) {
 #pragma unroll
     for (int u = 0; u < LA; ++u) {
@@ -911,7 +911,7 @@ __device__ __forceinline__ void gemm_tile(const double* A, const double* B, int 
       const int gi = i0 + ii, gk = k0 + kk;
       ra[u] = (gi < n && gk < n)
                   ? __ldcg(TA ? A + static_cast<int64_t>(gk) * ld + gi : A + static_cast<int64_t>(gi) * ld + gk)
-                  : 0.0;
+                  : F(0);
     }
 #pragma unroll
     for (int u = 0; u < LB; ++u) {
@@ -927,7 +927,7 @@ __device__ __forceinline__ void gemm_tile(const double* A, const double* B, int 
       const int gj = j0 + jj, gk = k0 + kk;
       rb[u] = (gj < n && gk < n)
                   ? __ldcg(TB ? B + static_cast<int64_t>(gj) * ld + gk : B + static_cast<int64_t>(gk) * ld + gj)
-                  : 0.0;
+                  : F(0);
     }
   };
   auto store = [&](int k0) {
@@ -956,11 +956,11 @@ __device__ __forceinline__ void gemm_tile(const double* A, const double* B, int 
         jj = e - kk * TN;
       }
       const int gj = j0 + jj, gk = k0 + kk;
-      sB[kk * (TN + 1) + jj] = (gj < n && gk < n) ? xb(gk, gj, rb[u]) : 0.0;
+      sB[kk * (TN + 1) + jj] = (gj < n && gk < n) ? static_cast<F>(xb(gk, gj, rb[u])) : F(0);
     }
   };
 #pragma unroll
-  for (int q = 0; q < PT; ++q) acc[q] = 0.0;
+  for (int q = 0; q < PT; ++q) acc[q] = F(0);
   load(0);
   for (int k0 = 0; k0 < n; k0 += kKC) {
     store(k0);
@@ -968,7 +968,7 @@ __device__ __forceinline__ void gemm_tile(const double* A, const double* B, int 
     if (k0 + kKC < n) load(k0 + kKC);
 #pragma unroll
     for (int kk = 0; kk < kKC; ++kk) {
-      const double a = sA[r * (kKC + 1) + kk];
+      const F a = sA[r * (kKC + 1) + kk];
 #pragma unroll
       for (int q = 0; q < PT; ++q) acc[q] = fma(a, sB[kk * (TN + 1) + g + 8 * q], acc[q]);
     }
@@ -977,7 +977,8 @@ __device__ __forceinline__ void gemm_tile(const double* A, const double* B, int 
 }
 
 struct Ident {
-  __device__ __forceinline__ double operator()(int, int, double x) const { return x; }
+  template <typename X>
+  __device__ __forceinline__ X operator()(int, int, X x) const { return x; }
 };
 
 // I + X for a stored correction X (X = E of the refinement step).
@@ -1025,13 +1026,13 @@ __device__ __forceinline__ void lower_tile(int t, int& ti, int& tj) {
 }
 
 // C = op(A) op(B) over all 16 x 24 tiles (full) into C.
-template <bool TA, bool TB, class XB>
-__device__ void gemm_full(const double* A, const double* B, double* C, int N, int ld, XB xb, double* sA, double* sB) {
+template <bool TA, bool TB, class XB, typename F>
+__device__ void gemm_full(const F* A, const F* B, F* C, int N, int ld, XB xb, F* sA, F* sB) {
   const int ntn = (N + 23) / 24, nfull = ((N + 15) / 16) * ntn;
   for (int t = blockIdx.x; t < nfull; t += gridDim.x) {
     const int ti = t / ntn, tj = t - ti * ntn;
-    double acc[3];
-    gemm_tile<16, 24, TA, TB>(A, B, ld, N, ti * 16, tj * 24, xb, acc, sA, sB);
+    F acc[3];
+    gemm_tile<F, 16, 24, TA, TB>(A, B, ld, N, ti * 16, tj * 24, xb, acc, sA, sB);
     const int r = threadIdx.x % 16, g = threadIdx.x / 16;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -1050,7 +1051,7 @@ __device__ void gemm_sym(const double* A, const double* B, double* C, int N, int
     int ti, tj;
     lower_tile(t, ti, tj);
     double acc[2];
-    gemm_tile<16, 16, TA, TB>(A, B, ld, N, ti * 16, tj * 16, Ident(), acc, sA, sB);
+    gemm_tile<double, 16, 16, TA, TB>(A, B, ld, N, ti * 16, tj * 16, Ident(), acc, sA, sB);
     const int r = threadIdx.x % 16, g = threadIdx.x / 16;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -1084,21 +1085,42 @@ struct OrthMax {
 // S = V^T W V: V' = V (I + E), e_ij = s_ij / (s_jj - s_ii) where that is a
 // small rotation (|e_ij| <= 0.1), else 0 (the pair is left as a cluster).
 // E is written over S's storage companion C (N x N, leading dimension ld).
-__device__ void newton_correction(const double* S, double* C, int N, int ld) {
+// With F32 (the Rayleigh-quotient update below), also FP32 copies of E and
+// of the off-diagonal of S, the diagonal of S in dsave, and this thread's
+// largest |e| and largest off-diagonal |s_ij| in emax and omax.
+__device__ void newton_correction(const double* S, double* C, int N, int ld, float* Ef, float* Of, double* dsave,
+                                  double& emax, double& omax) {
   const int64_t gt = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t gs = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t q = gt; q < static_cast<int64_t>(N) * N; q += gs) {
     const int i = static_cast<int>(q / N), j = static_cast<int>(q - static_cast<int64_t>(i) * N);
     const int64_t o = static_cast<int64_t>(i) * ld + j;
     double e = 0.0;
+    const double sij = __ldcg(S + o);
     if (i != j) {
       const double den = __ldcg(S + static_cast<int64_t>(j) * ld + j) - __ldcg(S + static_cast<int64_t>(i) * ld + i);
-      const double sij = __ldcg(S + o);
       if (den != 0.0 && fabs(sij) <= 0.1 * fabs(den)) e = sij / den;
     }
     C[o] = e;
+    emax = fmax(emax, fabs(e));
+    if (i != j) omax = fmax(omax, fabs(sij));
+    if (Ef) {
+      Ef[o] = static_cast<float>(e);
+      Of[o] = i != j ? static_cast<float>(sij) : 0.f;
+      if (i == j) dsave[i] = sij;
+    }
   }
 }
+
+// V (I + E + E^2 / 2) from the stored E (staged) and FP32 E^2 (read): the
+// exponential of the antisymmetric E to second order, orthogonal to O(E^4).
+struct ExpE {
+  const float* E2;
+  int ld;
+  __device__ __forceinline__ double operator()(int k, int j, double e) const {
+    return (k == j ? 1.0 : 0.0) + e + 0.5 * static_cast<double>(__ldcg(E2 + static_cast<int64_t>(k) * ld + j));
+  }
+};
 
 // Grid-wide maximum of one value per CTA (same result in every CTA).
 __device__ bool grid_max(double v, double* red, LargeScratch<double>& L, unsigned& gen, int32_t* err, long long limit,
@@ -1123,13 +1145,15 @@ __device__ void hand_over(LargeScratch<double>& L, bool warm) {
 }
 
 // A warm attempt that gave up: the cold path (gather, reduction,
-// eigenvectors, refinement) projects the block, and the next attempt waits
-// twice as many iterations as this one did (16 the first time, at most 1024).
-__device__ void warm_abort(LargeScratch<double>& L) {
+// eigenvectors, refinement) projects the block.  After an attempt whose
+// start was far from converged the next one waits twice as long as the
+// last wait (16 iterations the first time, at most 64); after a near miss
+// (it got past the first check) only 4.
+__device__ void warm_abort(LargeScratch<double>& L, bool near) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     L.flags[0] = 0;
-    const int wait = min(max(2 * L.flags[4], 16), 1024);
-    L.flags[4] = wait;
+    const int wait = near ? 4 : min(max(2 * L.flags[4], 16), 64);
+    if (!near) L.flags[4] = wait;
     L.flags[1] = wait;
   }
 }
@@ -1176,7 +1200,9 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
   double* Vc = L.V;
   double* Vn = L.B1;
   int work = 0;  // refinement GEMM passes beyond the reconstruction (reported per block)
+  bool fresh = false;  // B = V^T W V already updated for the current V (Rayleigh-quotient update)
   for (int pass = 0;; ++pass) {
+   if (!fresh) {
     // V^T V = I to the unit roundoff: a Newton-Schulz step takes the
     // largest deviation g to about (3/4) g^2 and ends it for g <= 3e-8; for
     // g <= 1.5e-5 (FP32 eigenvectors of separated eigenvalues) one
@@ -1193,7 +1219,7 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
       if (!grid_max(rmax, red, L, gen, err, p.wait_limit, gm)) return;
       if (!(gm <= 0.25) || (ns > 0 && !(gm < prev)) || ns == 6) {  // not converging
         if (warm_mode)
-          warm_abort(L);
+          warm_abort(L, pass > 0);
         else
           hand_over(L, false);
         return;
@@ -1231,6 +1257,8 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
     if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
     gemm_sym<true, false>(Vc, L.T1, L.B0, N, Np, NoOp(), sA, sB);
     if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
+   }
+   fresh = false;
 
     // check of the first-order projection of B: a pair of diagonal entries
     // of opposite signs adds |b_lk|^2 / (|b_ll| + |b_kk|) at second order
@@ -1282,9 +1310,10 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
     f2 = block_sum(f2, red);
     const double wn = sqrt(f2);
     if (a <= 1e-3 && rk <= 1e-13 * wn && sc <= 1e-14 * wn) break;
-    if (warm_mode && ((pass == 0 && (a > 1e-2 || sc > 1e-8 * wn)) || pass == 3)) {
-      // the previous eigenvectors are too far for a few Newton passes
-      warm_abort(L);
+    if (warm_mode && ((pass == 0 && (a > 0.05 || sc > 1e-3 * wn)) || pass == 2)) {
+      // the previous eigenvectors are too far for a few Newton passes (an
+      // angle beyond 0.05 meets the step's 0.1 clip), or two did not do
+      warm_abort(L, pass > 0);
       return;
     }
     if (!warm_mode && pass == 2) {  // still not accurate: the Jacobi kernel finishes from these eigenvectors
@@ -1293,10 +1322,62 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
       hand_over(L, true);
       return;
     }
-    newton_correction(L.B0, L.T1, N, Np);
-    if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
-    gemm_full<false, false>(Vc, L.T1, Vn, N, Np, PlusIdent(), sA, sB);
-    if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
+    const size_t fs = static_cast<size_t>(N) * Np;  // one FP32 slot of L.F32
+    float* F0 = L.F32;
+    double* dsv = L.partial + 4 * G;
+    double emax = 0.0, omax = 0.0;
+    newton_correction(L.B0, L.T1, N, Np, F0, F0 ? F0 + fs : nullptr, dsv, emax, omax);
+    // the update needs |E| <= 1e-5 and |O| <= 1e-4 |B|_F (so the FP32 terms
+    // stay below 1e-15 |B|_F); one grid maximum decides both
+    double eg;
+    const double ratio = fmax(emax / 1e-5, omax / (1e-4 * wn));
+    if (!grid_max(ratio == ratio ? ratio : 1e300, red, L, gen, err, p.wait_limit, eg)) return;
+    if (F0 && eg <= 1.0) {
+      // Rayleigh-quotient update for small E: V' = V M, M = I + C,
+      // C = E + E^2/2 (orthogonal to O(E^4), so V' needs no new V^T V), and
+      // B' = M^T B M = B + D C + (D C)^T + O C + (O C)^T + C^T (S C) with
+      // B = D + O (diagonal, off-diagonal), S C = D C + O C.  The terms
+      // O C and C^T S C (of order |O| |E| and |E|^2) go through FP32
+      // products, the others stay FP64; W V and V^T W V are not formed again.
+      float* Ef = F0;            // E (slot 0; later S C)
+      float* Of = F0 + fs;       // O (slot 1; later C^T S C)
+      float* E2 = F0 + 2 * fs;   // E^2
+      float* Cf = F0 + 3 * fs;   // C
+      float* OC = F0 + 4 * fs;   // O C
+      float* sAf = reinterpret_cast<float*>(sA);
+      float* sBf = reinterpret_cast<float*>(sB);
+      gemm_full<false, false>(Ef, Ef, E2, N, Np, Ident(), sAf, sBf);
+      if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
+      gemm_full<false, false>(Vc, L.T1, Vn, N, Np, ExpE{E2, Np}, sA, sB);
+      for (int64_t q = gt; q < fs; q += gs) Cf[q] = __ldcg(Ef + q) + 0.5f * __ldcg(E2 + q);
+      if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
+      gemm_full<false, false>(Of, Cf, OC, N, Np, Ident(), sAf, sBf);
+      if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
+      float* SC = Ef;
+      for (int64_t q = gt; q < static_cast<int64_t>(N) * N; q += gs) {
+        const int i = static_cast<int>(q / N), j = static_cast<int>(q - static_cast<int64_t>(i) * N);
+        const int64_t o = static_cast<int64_t>(i) * Np + j;
+        SC[o] = static_cast<float>(__ldcg(dsv + i)) * __ldcg(Cf + o) + __ldcg(OC + o);
+      }
+      if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
+      float* CSC = Of;
+      gemm_full<true, false>(Cf, SC, CSC, N, Np, Ident(), sAf, sBf);
+      if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
+      for (int64_t q = gt; q < static_cast<int64_t>(N) * N; q += gs) {
+        const int i = static_cast<int>(q / N), j = static_cast<int>(q - static_cast<int64_t>(i) * N);
+        const int64_t o = static_cast<int64_t>(i) * Np + j, ot = static_cast<int64_t>(j) * Np + i;
+        const double cij = __ldcg(L.T1 + o) + 0.5 * static_cast<double>(__ldcg(E2 + o));
+        const double cji = __ldcg(L.T1 + ot) + 0.5 * static_cast<double>(__ldcg(E2 + ot));
+        const double small = static_cast<double>(__ldcg(OC + o)) + static_cast<double>(__ldcg(OC + ot)) +
+                             static_cast<double>(__ldcg(CSC + o));
+        L.B0[o] = __ldcg(L.B0 + o) + __ldcg(dsv + i) * cij + __ldcg(dsv + j) * cji + small;
+      }
+      if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
+      fresh = true;
+    } else {
+      gemm_full<false, false>(Vc, L.T1, Vn, N, Np, PlusIdent(), sA, sB);
+      if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
+    }
     double* t = Vc;
     Vc = Vn;
     Vn = t;

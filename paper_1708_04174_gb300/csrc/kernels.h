@@ -91,6 +91,7 @@ struct LargeScratch {
   int32_t* warm = nullptr;     // 1 if V holds the previous eigenvectors
   int32_t warm_limit = 1024;   // cold restart after this many warm iterations
   int32_t tri_warm = 0;        // 1: each iteration first tries the refinement from the last eigenvectors
+  float* F32 = nullptr;        // five N x Np FP32 work matrices of the refinement's Rayleigh-quotient update, or none
 };
 
 constexpr int kMaxSweeps = 40;
