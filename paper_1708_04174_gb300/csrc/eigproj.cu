@@ -1145,16 +1145,14 @@ __device__ void hand_over(LargeScratch<double>& L, bool warm) {
 }
 
 // A warm attempt that gave up: the cold path (gather, reduction,
-// eigenvectors, refinement) projects the block.  After an attempt whose
-// start was far from converged the next one waits twice as long as the
-// last wait (16 iterations the first time, at most 64); after a near miss
-// (it got past the first check) only 4.
+// eigenvectors, refinement) projects the block.  The next attempt waits 16
+// iterations after a start far from converged (given up at the first check,
+// which costs about one W V product) and 4 after a near miss (given up after
+// one or two Newton passes).
 __device__ void warm_abort(LargeScratch<double>& L, bool near) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     L.flags[0] = 0;
-    const int wait = near ? 4 : min(max(2 * L.flags[4], 16), 64);
-    if (!near) L.flags[4] = wait;
-    L.flags[1] = wait;
+    L.flags[1] = near ? 4 : 16;
   }
 }
 
@@ -1201,6 +1199,7 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
   double* Vn = L.B1;
   int work = 0;  // refinement GEMM passes beyond the reconstruction (reported per block)
   bool fresh = false;  // B = V^T W V already updated for the current V (Rayleigh-quotient update)
+  double rk0 = 0.0;     // the first check's largest same-sign coupling (warm attempts)
   for (int pass = 0;; ++pass) {
    if (!fresh) {
     // V^T V = I to the unit roundoff: a Newton-Schulz step takes the
@@ -1310,11 +1309,20 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
     f2 = block_sum(f2, red);
     const double wn = sqrt(f2);
     if (a <= 1e-3 && rk <= 1e-13 * wn && sc <= 1e-14 * wn) break;
-    if (warm_mode && ((pass == 0 && (a > 0.05 || sc > 1e-3 * wn)) || pass == 2)) {
-      // the previous eigenvectors are too far for a few Newton passes (an
-      // angle beyond 0.05 meets the step's 0.1 clip), or two did not do
-      warm_abort(L, pass > 0);
-      return;
+    if (pass == 0) rk0 = rk;
+    if (warm_mode) {
+      // Two Newton passes take a second-order sum s to about s^4 / |B|^3,
+      // so a start above 1e-6 |B|_F cannot reach the check; an angle
+      // beyond 0.05 meets the step's 0.1 clip; same-sign couplings of
+      // close eigenvalues (a cluster the step leaves alone) stay where they
+      // are, so a start above 1e-4 |B|_F, or a first pass that does not
+      // halve them, does not converge either.
+      const bool far = pass == 0 && (a > 0.05 || sc > 1e-6 * wn || rk > 1e-4 * wn);
+      const bool stuck = pass == 1 && rk > 1e-13 * wn && rk > 0.5 * rk0;
+      if (far || stuck || pass == 2) {
+        warm_abort(L, !far);
+        return;
+      }
     }
     if (!warm_mode && pass == 2) {  // still not accurate: the Jacobi kernel finishes from these eigenvectors
       if (Vc != L.V)
@@ -1416,7 +1424,7 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
     if (warm_mode) {
       L.flags[1] = 0;  // stay warm
     } else if (L.flags[4] == 0) {
-      L.flags[4] = 16;  // first cold projection: the first attempt waits 16 iterations
+      L.flags[4] = 1;  // first cold projection: the first attempt waits 16 iterations
       L.flags[1] = 16;
     } else if (L.flags[1] > 0) {
       --L.flags[1];

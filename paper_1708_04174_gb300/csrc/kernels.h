@@ -84,7 +84,8 @@ struct LargeScratch {
   double* partial = nullptr;   // large_partials_size(grid, N) doubles
   // [0]: 1 if the tridiagonal path projected the block in this iteration;
   // with tri_warm, [1]: iterations before the next warm attempt, [3]: 1 if V
-  // holds the last iteration's eigenvectors, [4]: the last wait
+  // holds the last iteration's eigenvectors, [4]: 1 once a cold projection
+  // has set the first wait
   int32_t* flags = nullptr;
   uint32_t* bar = nullptr;     // grid barrier: [arrivals, released generation], zeroed before each launch
   int32_t* sweeps_out = nullptr;  // number of sweeps of the last launch
