@@ -887,15 +887,16 @@ constexpr int kKC = 16;
 // dimension ld, 128 threads; thread t computes row t % TM and the columns
 // t / TM + 8 q.  op(X) = X^T where the flag is set.  xb(k, j, x) maps an
 // element of op(B) as it is staged.  The next K chunk is loaded into
-// registers while the current one is multiplied.
-template <typename F, int TM, int TN, bool TA, bool TB, class XB>
-__device__ __forceinline__ void gemm_tile(const F* A, const F* B, int ld, int n, int i0, int j0, XB xb,
+// registers while the current one is multiplied.  A and B are stored as G
+// and multiplied as F (rounded as they are staged).
+template <typename F, int TM, int TN, bool TA, bool TB, class XB, typename G = F>
+__device__ __forceinline__ void gemm_tile(const G* A, const G* B, int ld, int n, int i0, int j0, XB xb,
                                           F (&acc)[TM * TN / kRecThreads], F* sA, F* sB) {
   constexpr int PT = TM * TN / kRecThreads;
   constexpr int LA = TM * kKC / kRecThreads, LB = kKC * TN / kRecThreads;
   static_assert(LA * kRecThreads == TM * kKC && LB * kRecThreads == kKC * TN, "tile shape");
   const int t = threadIdx.x, r = t % TM, g = t / TM;
-  F ra[LA], rb[LB];
+  G ra[LA], rb[LB];
   auto load = [&](int k0) {
 #pragma unroll
     for (int u = 0; u < LA; ++u) {
@@ -911,7 +912,7 @@ __device__ __forceinline__ void gemm_tile(const F* A, const F* B, int ld, int n,
       const int gi = i0 + ii, gk = k0 + kk;
       ra[u] = (gi < n && gk < n)
                   ? __ldcg(TA ? A + static_cast<int64_t>(gk) * ld + gi : A + static_cast<int64_t>(gi) * ld + gk)
-                  : F(0);
+                  : G(0);
     }
 #pragma unroll
     for (int u = 0; u < LB; ++u) {
@@ -927,7 +928,7 @@ __device__ __forceinline__ void gemm_tile(const F* A, const F* B, int ld, int n,
       const int gj = j0 + jj, gk = k0 + kk;
       rb[u] = (gj < n && gk < n)
                   ? __ldcg(TB ? B + static_cast<int64_t>(gj) * ld + gk : B + static_cast<int64_t>(gk) * ld + gj)
-                  : F(0);
+                  : G(0);
     }
   };
   auto store = [&](int k0) {
@@ -942,7 +943,7 @@ __device__ __forceinline__ void gemm_tile(const F* A, const F* B, int ld, int n,
         ii = e / kKC;
         kk = e - ii * kKC;
       }
-      sA[ii * (kKC + 1) + kk] = ra[u];
+      sA[ii * (kKC + 1) + kk] = static_cast<F>(ra[u]);
     }
 #pragma unroll
     for (int u = 0; u < LB; ++u) {
@@ -981,9 +982,12 @@ struct Ident {
   __device__ __forceinline__ X operator()(int, int, X x) const { return x; }
 };
 
-// I + X for a stored correction X (X = E of the refinement step).
-struct PlusIdent {
-  __device__ __forceinline__ double operator()(int k, int j, double x) const { return (k == j ? 1.0 : 0.0) + x; }
+// Correction part (I - V^T V) / 2 of the Newton-Schulz factor, from the
+// stored V^T V.
+struct NsCorr {
+  __device__ __forceinline__ double operator()(int k, int j, double x) const {
+    return 0.5 * ((k == j ? 1.0 : 0.0) - x);
+  }
 };
 
 // Newton-Schulz factor (3 I - V^T V) / 2 from the stored V^T V.
@@ -1016,6 +1020,29 @@ struct FirstOrder {
     return (fmax(bk, 0.0) - fmax(bj, 0.0)) / (bk - bj) * x;  // |bk - bj| > 0 here
   }
 };
+
+// C = A + A X for FP64 A and a small correction X = xb(stored), the
+// product A X in FP32 (relative error about 1e-6 of |X|): for steps whose
+// result the next check measures again in FP64 (a Newton rotation, a
+// Newton-Schulz step far from orthonormal), never for the last one.
+template <class XB>
+__device__ void gemm_corr(const double* A, const double* X, double* C, int N, int ld, XB xb, float* sA, float* sB) {
+  const int ntn = (N + 23) / 24, nfull = ((N + 15) / 16) * ntn;
+  for (int t = blockIdx.x; t < nfull; t += gridDim.x) {
+    const int ti = t / ntn, tj = t - ti * ntn;
+    float acc[3];
+    gemm_tile<float, 16, 24, false, false, XB, double>(A, X, ld, N, ti * 16, tj * 24, xb, acc, sA, sB);
+    const int r = threadIdx.x % 16, g = threadIdx.x / 16;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int ii = ti * 16 + r, jj = tj * 24 + g + 8 * q;
+      if (ii < N && jj < N) {
+        const int64_t o = static_cast<int64_t>(ii) * ld + jj;
+        C[o] = __ldcg(A + o) + static_cast<double>(acc[q]);
+      }
+    }
+  }
+}
 
 // Lower-triangle tile index -> (ti, tj), ti >= tj.
 __device__ __forceinline__ void lower_tile(int t, int& ti, int& tj) {
@@ -1122,16 +1149,153 @@ struct ExpE {
   }
 };
 
-// Grid-wide maximum of one value per CTA (same result in every CTA).
+// Grid-wide maximum of one value per CTA (same result in every CTA).  The
+// per-CTA values go to slots of their own, alternating between two sets by
+// the barrier count: a CTA that runs ahead cannot overwrite values another
+// CTA is still reading, neither those of the check (slots 0..4G) nor those of
+// the previous maximum when no barrier lies between the two.
 __device__ bool grid_max(double v, double* red, LargeScratch<double>& L, unsigned& gen, int32_t* err, long long limit,
                          double& out) {
+  const unsigned G = gridDim.x;
+  double* slot = L.partial + (4 + (gen & 1)) * static_cast<size_t>(G);
   v = block_max(v, red);
-  if (threadIdx.x == 0) L.partial[blockIdx.x] = v;
-  if (!grid_barrier(L.bar, (++gen) * gridDim.x, err, limit)) return false;
+  if (threadIdx.x == 0) slot[blockIdx.x] = v;
+  if (!grid_barrier(L.bar, (++gen) * G, err, limit)) return false;
   double m = 0.0;
-  for (unsigned c = threadIdx.x; c < gridDim.x; c += blockDim.x) m = fmax(m, __ldcg(L.partial + c));
+  for (unsigned c = threadIdx.x; c < G; c += blockDim.x) m = fmax(m, __ldcg(slot + c));
   out = block_max(m, red);
   return true;
+}
+
+// Exact plane rotations for the pairs the Newton step leaves alone
+// (|b_lk| > 0.1 |b_ll - b_kk|: eigenvalues close enough that the change of
+// W mixes their eigenvectors by a large angle).  Each row l proposes its
+// largest such coupling b_lk, k < l (one warp per row); a proposal is taken
+// when it is the largest of all proposals that share an index with it (ties
+// to the smaller row), so the taken pairs are disjoint and their rotations
+// commute.  Each rotation is the Jacobi rotation that zeroes b_lk (angle at
+// most pi/4); V <- V Q and B <- Q^T B Q in place.  Pairs left out wait for
+// the next pass.  `gb` holds 5 N doubles: proposals (value, column), then
+// per index the rotation's cosine, partner coefficient and partner.
+// Returns false if a grid wait expired.
+__device__ bool pair_rotations(double* B, double* V, int N, int ld, double* gb, double* red, LargeScratch<double>& L,
+                               unsigned& gen, int32_t* err, long long limit) {
+  double* pv = gb;
+  double* pk = gb + N;
+  double* qc = gb + 2 * N;
+  double* qs = gb + 3 * N;
+  double* qp = gb + 4 * N;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  double found = 0.0;
+  for (int64_t l = warp; l < N; l += nwarps) {
+    const double bll = __ldcg(B + l * ld + l);
+    double best = 0.0;
+    int bk = -1;
+    for (int k = lane; k < l; k += 32) {
+      const double x = fabs(__ldcg(B + l * ld + k));
+      const double den = fabs(__ldcg(B + static_cast<int64_t>(k) * ld + k) - bll);
+      if (x > 0.1 * den && x > best) {  // NaN never qualifies
+        best = x;
+        bk = k;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      if (ob > best || (ob == best && ok >= 0 && (bk < 0 || ok < bk))) {
+        best = ob;
+        bk = ok;
+      }
+    }
+    if (lane == 0) {
+      pv[l] = best;
+      pk[l] = bk;
+      qc[l] = 1.0;
+      qs[l] = 0.0;
+      qp[l] = static_cast<double>(l);
+    }
+    found = fmax(found, best);
+  }
+  double any = 0.0;
+  if (!grid_max(found, red, L, gen, err, limit, any)) return false;
+  if (!(any > 0.0)) return true;
+  // a proposal (l, k) is taken when no other proposal touching l or k is larger
+  for (int64_t l = warp; l < N; l += nwarps) {
+    const int k = static_cast<int>(__ldcg(pk + l));
+    if (k < 0) continue;  // warp-uniform
+    const double v = __ldcg(pv + l);
+    bool beaten = false;
+    for (int m = lane; m < N; m += 32) {
+      if (m == l) continue;
+      const int km = static_cast<int>(__ldcg(pk + m));
+      if (km < 0) continue;
+      if (m == k || km == l || km == k) {
+        const double vm = __ldcg(pv + m);
+        if (vm > v || (vm == v && m < l)) beaten = true;
+      }
+    }
+    if (__any_sync(0xffffffffu, beaten)) continue;
+    if (lane == 0) {
+      // Jacobi rotation of the 2 x 2 block (k, l): tau = (b_ll - b_kk) / (2 b_kl),
+      // t = tan(theta) = sign(tau) / (|tau| + sqrt(1 + tau^2)), |t| <= 1
+      const double bkk = __ldcg(B + static_cast<int64_t>(k) * ld + k), bll = __ldcg(B + l * ld + l);
+      const double bkl = __ldcg(B + l * ld + k);
+      const double tau = (bll - bkk) / (2.0 * bkl);
+      const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+      const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+      // column k of V Q is c v_k - s v_l, column l is c v_l + s v_k
+      qc[k] = c;
+      qs[k] = -sn;
+      qp[k] = static_cast<double>(l);
+      qc[l] = c;
+      qs[l] = sn;
+      qp[l] = static_cast<double>(k);
+    }
+  }
+  if (!grid_barrier(L.bar, (++gen) * gridDim.x, err, limit)) return false;
+  const int64_t gt = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t gs = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  // V Q: each pair of columns once per row (j the smaller index)
+  for (int64_t q = gt; q < static_cast<int64_t>(N) * N; q += gs) {
+    const int r = static_cast<int>(q / N), j = static_cast<int>(q - static_cast<int64_t>(r) * N);
+    const int pj = static_cast<int>(__ldcg(qp + j));
+    if (pj <= j) continue;
+    double* row = V + static_cast<int64_t>(r) * ld;
+    const double x = __ldcg(row + j), y = __ldcg(row + pj);
+    row[j] = __ldcg(qc + j) * x + __ldcg(qs + j) * y;
+    row[pj] = __ldcg(qc + pj) * y + __ldcg(qs + pj) * x;
+  }
+  // Q^T B Q: the entries {i, p(i)} x {j, p(j)} together, by the thread of
+  // the smaller index of each side; (Q^T B Q)_xy = sum_ab Q_ax B_ab Q_by with
+  // Q_xx = qc[x] and Q_p(x)x = qs[x]
+  for (int64_t q = gt; q < static_cast<int64_t>(N) * N; q += gs) {
+    const int i = static_cast<int>(q / N), j = static_cast<int>(q - static_cast<int64_t>(i) * N);
+    const int pi = static_cast<int>(__ldcg(qp + i)), pj = static_cast<int>(__ldcg(qp + j));
+    if (pi < i || pj < j || (pi == i && pj == j)) continue;
+    const int xs[2] = {i, pi}, ys[2] = {j, pj};
+    const int nx = pi != i ? 2 : 1, ny = pj != j ? 2 : 1;
+    double o[2][2], nv[2][2];
+    for (int a = 0; a < nx; ++a)
+      for (int b = 0; b < ny; ++b) o[a][b] = __ldcg(B + static_cast<int64_t>(xs[a]) * ld + ys[b]);
+    for (int x = 0; x < nx; ++x)
+      for (int y = 0; y < ny; ++y) {
+        double acc = 0.0;
+        for (int a = 0; a < nx; ++a) {
+          const double qa = a == x ? __ldcg(qc + xs[x]) : __ldcg(qs + xs[x]);
+          for (int b = 0; b < ny; ++b) {
+            const double qb = b == y ? __ldcg(qc + ys[y]) : __ldcg(qs + ys[y]);
+            acc += qa * o[a][b] * qb;
+          }
+        }
+        nv[x][y] = acc;
+      }
+    for (int x = 0; x < nx; ++x)
+      for (int y = 0; y < ny; ++y) B[static_cast<int64_t>(xs[x]) * ld + ys[y]] = nv[x][y];
+  }
+  return grid_barrier(L.bar, (++gen) * gridDim.x, err, limit);
 }
 
 // Leaves the block to the Jacobi kernel launched after this one: cold, or
@@ -1244,7 +1408,12 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
         work += 2;
         break;
       }
-      gemm_full<false, false>(Vc, L.T1, Vn, N, Np, NsFactor(), sA, sB);
+      // far from orthonormal the step's product may be FP32 (the next
+      // V^T V measures the result again); the last step is FP64
+      if (gm > 1.5e-5)
+        gemm_corr(Vc, L.T1, Vn, N, Np, NsCorr(), reinterpret_cast<float*>(sA), reinterpret_cast<float*>(sB));
+      else
+        gemm_full<false, false>(Vc, L.T1, Vn, N, Np, NsFactor(), sA, sB);
       if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
       double* t = Vc;
       Vc = Vn;
@@ -1332,7 +1501,8 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
     }
     const size_t fs = static_cast<size_t>(N) * Np;  // one FP32 slot of L.F32
     float* F0 = L.F32;
-    double* dsv = L.partial + 4 * G;
+    double* dsv = L.partial + 6 * G;
+    if (!pair_rotations(L.B0, Vc, N, Np, dsv + N, red, L, gen, err, p.wait_limit)) return;
     double emax = 0.0, omax = 0.0;
     newton_correction(L.B0, L.T1, N, Np, F0, F0 ? F0 + fs : nullptr, dsv, emax, omax);
     // the update needs |E| <= 1e-5 and |O| <= 1e-4 |B|_F (so the FP32 terms
@@ -1383,7 +1553,9 @@ __global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid
       if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
       fresh = true;
     } else {
-      gemm_full<false, false>(Vc, L.T1, Vn, N, Np, PlusIdent(), sA, sB);
+      // V (I + E), E in FP32: the next pass orthonormalises the result and
+      // measures V^T W V again in FP64
+      gemm_corr(Vc, L.T1, Vn, N, Np, Ident(), reinterpret_cast<float*>(sA), reinterpret_cast<float*>(sB));
       if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
     }
     double* t = Vc;

@@ -97,11 +97,13 @@ struct LargeScratch {
 
 constexpr int kMaxSweeps = 40;
 // LargeScratch::partial: kLargePartials doubles per CTA (the Jacobi kernel
-// uses three: norm and two alternating sweep checks; the tridiagonal path
-// four), then N doubles of the tridiagonal path's eigenvalue estimates
-constexpr int kLargePartials = 4;
-inline size_t large_partials_size(int grid, int N) {
-  return static_cast<size_t>(kLargePartials) * static_cast<size_t>(grid) + static_cast<size_t>(N) + 1;
+// uses three: norm and two alternating sweep checks; the tridiagonal path's
+// refinement four for its check and two sets for grid maxima), then 6 N + 1
+// doubles of the refinement (diagonal of B, pair-rotation proposals and
+// rotations)
+constexpr int kLargePartials = 6;
+__host__ __device__ constexpr size_t large_partials_size(int grid, int N) {
+  return static_cast<size_t>(kLargePartials) * static_cast<size_t>(grid) + 6 * static_cast<size_t>(N) + 1;
 }
 
 // FP64 large blocks of kTriMinN <= N <= kTriMaxN are projected through a

@@ -33,7 +33,7 @@ constexpr size_t kPacked = align256(sizeof(double) * kNoAllocMaxN * (kNoAllocMax
 constexpr size_t kOffV = 0;                       // v = u - W output (packed)
 constexpr size_t kOffMats = kOffV + kPacked;      // Wf, B0, B1, V, T1
 constexpr size_t kOffPartial = kOffMats + 5 * kMat;
-constexpr size_t kOffSmall = kOffPartial + align256(sizeof(double) * (kLargePartials * kMaxGrid + kNoAllocMaxN + 1));
+constexpr size_t kOffSmall = kOffPartial + align256(sizeof(double) * large_partials_size(kMaxGrid, kNoAllocMaxN));
 // small words: block descriptor, instance state, ids/flags
 constexpr size_t kOffDesc = kOffSmall;
 constexpr size_t kOffState = kOffDesc + align256(sizeof(BlockDesc));
