@@ -840,7 +840,7 @@ int build(sos_handle* h, const sos_program* progs, int32_t n_progs) {
       TRY(alloc(h, Np * Np, &nb.s.X));
       TRY(alloc(h, Np * Np, &nb.s.Xn));
       TRY(alloc(h, 4 * ns_split_bytes(static_cast<int>(Np)), &nb.s.split));
-      TRY(alloc(h, static_cast<size_t>(ns_grid(nb.N)), &nb.s.partial));
+      TRY(alloc(h, 2 * static_cast<size_t>(ns_grid(nb.N)), &nb.s.partial));
       TRY(alloc(h, 2, &nb.s.bar));
       TRY(alloc(h, 1, &nb.s.iters_out));
       h->ns_large.push_back(nb);
@@ -1388,7 +1388,7 @@ int psd_project_one(const double* in, double* out, int32_t N, void* stream, bool
       if ((rc = alloc(h, Np * Np, &S.Wf)) != SOS_OK || (rc = alloc(h, Np * Np, &S.X)) != SOS_OK ||
           (rc = alloc(h, 4 * ns_split_bytes(static_cast<int>(Np)), &S.split)) != SOS_OK ||
           (rc = alloc(h, Np * Np, &S.Xn)) != SOS_OK ||
-          (rc = alloc(h, static_cast<size_t>(ns_grid(N)), &S.partial)) != SOS_OK || (rc = alloc(h, 2, &S.bar)) != SOS_OK ||
+          (rc = alloc(h, 2 * static_cast<size_t>(ns_grid(N)), &S.partial)) != SOS_OK || (rc = alloc(h, 2, &S.bar)) != SOS_OK ||
           (rc = alloc(h, 1, &S.iters_out)) != SOS_OK)
         break;
       e = launch_psd_ns<double>(p, 0, N, S, s);

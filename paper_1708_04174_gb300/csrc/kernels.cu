@@ -1456,21 +1456,47 @@ __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch
     // eigenvalues near 1 down to the current floor ell before they return; in
     // FP32 with split-BF16 products those lose their relative accuracy there and
     // the outer ADMM iteration stalls near a 2e-4 dual residual, so it is not used.
+    // The first step alone is rescaled: |X|_2 <= c = |X^2|_F^(1/2) <= |X|_F = 1,
+    // so X / c still has its eigenvalues in [-1, 1] and every one of them
+    // starts a factor 1/c higher (c is about r^(-1/4) for r eigenvalues of
+    // comparable size), which saves log_1.5(1/c) steps.
+    float alpha = 1.5f, beta = 0.5f;
     for (it = 0; alive && it < S.max_iter; ++it) {
       // Y = X X
       ns_gemm(Xsp, Xsp, Np, m0, n0, nsm, P);
       if (!P.ok) break;
+      float ysq = 0.f;
       for (int c0 = chalf * 32; c0 < chalf * 32 + 32; c0 += 8) {
         float v[8];
         tc::ld8(P.tmem + (static_cast<uint32_t>(wq * 32) << 16) + c0, v);
         ns_put_lower(Ysp, nullptr, Np, row, n0 + c0, v);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) tile[(row - m0) * (kNsTN + 1) + c0 + j] = v[j];
+        for (int j = 0; j < 8; ++j) {
+          tile[(row - m0) * (kNsTN + 1) + c0 + j] = v[j];
+          const int col = n0 + c0 + j;
+          if (row >= col) ysq = fmaf((row == col ? 1.f : 2.f) * v[j], v[j], ysq);
+        }
       }
       __syncthreads();
       ns_put_mirror(Ysp, nullptr, Np, m0, n0, tile);
+      if (it == 0) {
+        const double py = block_sum(static_cast<double>(ysq), red);
+        if (threadIdx.x == 0) S.partial[G + blockIdx.x] = py;
+      }
       NS_SYNC();
       if (!alive) break;
+      if (it == 0) {
+        double ytot = 0.0;
+        for (unsigned c = 0; c < G; ++c) ytot += __ldcg(S.partial + G + c);  // same order in every CTA
+        const double c = sqrt(sqrt(ytot));
+        if (c > 0.0 && c < 1.0) {
+          alpha = static_cast<float>(1.5 / c);
+          beta = static_cast<float>(0.5 / (c * c * c));
+        }
+      } else {
+        alpha = 1.5f;
+        beta = 0.5f;
+      }
       // X_next = 1.5 X - 0.5 Y X, and |X_next - X|^2
       ns_gemm(Ysp, Xsp, Np, m0, n0, nsm, P);
       if (!P.ok) break;
@@ -1488,7 +1514,7 @@ __global__ void __launch_bounds__(256) k_psd_ns(DevPlan<T> p, int bid, NsScratch
         float xn[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          xn[j] = 1.5f * x[j] - 0.5f * v[j];
+          xn[j] = alpha * x[j] - beta * v[j];
           const int col = n0 + c0 + j;
           const float df = xn[j] - x[j];
           if (row >= col) dsq = fmaf((row == col ? 1.f : 2.f) * df, df, dsq);

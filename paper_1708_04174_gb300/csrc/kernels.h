@@ -127,7 +127,7 @@ struct NsScratch {
   // W, X, Xn, Y as three BF16 parts each, in the operand layout of the
   // tensor-core products (ns_split_bytes(Np) bytes per matrix)
   unsigned char* split = nullptr;
-  double* partial = nullptr;  // per CTA
+  double* partial = nullptr;  // two per CTA
   uint32_t* bar = nullptr;    // grid barrier [2], zeroed by the launcher
   int32_t* iters_out = nullptr;
   int32_t max_iter = 60;
