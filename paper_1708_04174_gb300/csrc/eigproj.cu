@@ -50,7 +50,8 @@ namespace {
 
 constexpr int kTriThreads = 256;   // reduction CTA (8 warps: little redundant per-warp work)
 constexpr int kVecThreads = 128;   // four eigenvectors per CTA (one warp per scheduler)
-constexpr int kRecThreads = 128;   // reconstruction CTAs
+constexpr int kRecThreads = 128;   // one warpgroup: the threads of a product tile
+constexpr int kRecBlock = 2 * kRecThreads;  // refinement CTAs: two warpgroups split each product's K
 constexpr int kTriSlots = (kTriMaxN + 31) / 32;  // per-lane register slots of a length-N vector
 constexpr int kTriRows = 256;                     // columns of a lane's two float4 slots
 constexpr int kTriPcol = (kTriThreads / 32) * kTriRows;  // per-warp column sums of one step
@@ -884,18 +885,27 @@ __global__ void __launch_bounds__(kVecThreads) k_tri_vectors(DevPlan<double> p, 
 constexpr int kKC = 16;
 
 // Tile (TM x TN) of C = op(A) op(B), op(A) n x n, op(B) n x n, leading
-// dimension ld, 128 threads; thread t computes row t % TM and the columns
-// t / TM + 8 q.  op(X) = X^T where the flag is set.  xb(k, j, x) maps an
-// element of op(B) as it is staged.  The next K chunk is loaded into
-// registers while the current one is multiplied.  A and B are stored as G
-// and multiplied as F (rounded as they are staged).
+// dimension ld, on the CTA's two warpgroups: warpgroup w multiplies the K
+// chunks w, w + 2, ... with its own shared-memory buffers and its own named
+// barrier, and the partial sums meet at the end.  Thread t of a warpgroup
+// computes row t % TM and the columns t / TM + 8 q; the result is valid in
+// warpgroup 0 (threads 0..127).  op(X) = X^T where the flag is set.
+// xb(k, j, x) maps an element of op(B) as it is staged.  The next chunk is
+// loaded into registers while the current one is multiplied.  A and B are
+// stored as G and multiplied as F (rounded as they are staged).  sA and sB
+// hold two buffers each (2 TM (kKC + 1) and 2 kKC (TN + 1) elements of F).
 template <typename F, int TM, int TN, bool TA, bool TB, class XB, typename G = F>
 __device__ __forceinline__ void gemm_tile(const G* A, const G* B, int ld, int n, int i0, int j0, XB xb,
                                           F (&acc)[TM * TN / kRecThreads], F* sA, F* sB) {
   constexpr int PT = TM * TN / kRecThreads;
   constexpr int LA = TM * kKC / kRecThreads, LB = kKC * TN / kRecThreads;
   static_assert(LA * kRecThreads == TM * kKC && LB * kRecThreads == kKC * TN, "tile shape");
-  const int t = threadIdx.x, r = t % TM, g = t / TM;
+  static_assert(TM * TN <= kKC * (TN + 1), "partial sums fit the B buffer");
+  const int wg = threadIdx.x / kRecThreads;
+  const int t = threadIdx.x - wg * kRecThreads, r = t % TM, g = t / TM;
+  F* mA = sA + wg * TM * (kKC + 1);
+  F* mB = sB + wg * kKC * (TN + 1);
+  auto wg_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(1 + wg), "n"(kRecThreads) : "memory"); };
   G ra[LA], rb[LB];
   auto load = [&](int k0) {
 #pragma unroll
@@ -943,7 +953,7 @@ __device__ __forceinline__ void gemm_tile(const G* A, const G* B, int ld, int n,
         ii = e / kKC;
         kk = e - ii * kKC;
       }
-      sA[ii * (kKC + 1) + kk] = static_cast<F>(ra[u]);
+      mA[ii * (kKC + 1) + kk] = static_cast<F>(ra[u]);
     }
 #pragma unroll
     for (int u = 0; u < LB; ++u) {
@@ -957,24 +967,50 @@ __device__ __forceinline__ void gemm_tile(const G* A, const G* B, int ld, int n,
         jj = e - kk * TN;
       }
       const int gj = j0 + jj, gk = k0 + kk;
-      sB[kk * (TN + 1) + jj] = (gj < n && gk < n) ? static_cast<F>(xb(gk, gj, rb[u])) : F(0);
+      mB[kk * (TN + 1) + jj] = (gj < n && gk < n) ? static_cast<F>(xb(gk, gj, rb[u])) : F(0);
     }
   };
+  // KS independent partial sums per output (interleaved k): four warps per
+  // SM leave the dependent multiply-add latency exposed with one chain per
+  // output
+  constexpr int KS = 2;
+  F part[KS][PT];
 #pragma unroll
-  for (int q = 0; q < PT; ++q) acc[q] = F(0);
-  load(0);
-  for (int k0 = 0; k0 < n; k0 += kKC) {
+  for (int h = 0; h < KS; ++h)
+#pragma unroll
+    for (int q = 0; q < PT; ++q) part[h][q] = F(0);
+  load(wg * kKC);
+  for (int k0 = wg * kKC; k0 < n; k0 += 2 * kKC) {
     store(k0);
-    __syncthreads();
-    if (k0 + kKC < n) load(k0 + kKC);
+    wg_sync();
+    if (k0 + 2 * kKC < n) load(k0 + 2 * kKC);
 #pragma unroll
-    for (int kk = 0; kk < kKC; ++kk) {
-      const F a = sA[r * (kKC + 1) + kk];
+    for (int kk = 0; kk < kKC; kk += KS) {
 #pragma unroll
-      for (int q = 0; q < PT; ++q) acc[q] = fma(a, sB[kk * (TN + 1) + g + 8 * q], acc[q]);
+      for (int h = 0; h < KS; ++h) {
+        const F a = mA[r * (kKC + 1) + kk + h];
+#pragma unroll
+        for (int q = 0; q < PT; ++q) part[h][q] = fma(a, mB[(kk + h) * (TN + 1) + g + 8 * q], part[h][q]);
+      }
     }
-    __syncthreads();
+    wg_sync();
   }
+#pragma unroll
+  for (int q = 0; q < PT; ++q) {
+#pragma unroll
+    for (int h = 1; h < KS; ++h) part[0][q] += part[h][q];
+  }
+  // warpgroup 1 hands its sums to warpgroup 0 through the first B buffer
+  // (warpgroup 1's next stores go to its own buffers; warpgroup 0 reads
+  // these before its own next store)
+  __syncthreads();
+  if (wg == 1)
+#pragma unroll
+    for (int q = 0; q < PT; ++q) sB[t * PT + q] = part[0][q];
+  __syncthreads();
+  if (wg == 0)
+#pragma unroll
+    for (int q = 0; q < PT; ++q) acc[q] = part[0][q] + sB[t * PT + q];
 }
 
 struct Ident {
@@ -1032,6 +1068,7 @@ __device__ void gemm_corr(const double* A, const double* X, double* C, int N, in
     const int ti = t / ntn, tj = t - ti * ntn;
     float acc[3];
     gemm_tile<float, 16, 24, false, false, XB, double>(A, X, ld, N, ti * 16, tj * 24, xb, acc, sA, sB);
+    if (threadIdx.x >= kRecThreads) continue;
     const int r = threadIdx.x % 16, g = threadIdx.x / 16;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -1060,6 +1097,7 @@ __device__ void gemm_full(const F* A, const F* B, F* C, int N, int ld, XB xb, F*
     const int ti = t / ntn, tj = t - ti * ntn;
     F acc[3];
     gemm_tile<F, 16, 24, TA, TB>(A, B, ld, N, ti * 16, tj * 24, xb, acc, sA, sB);
+    if (threadIdx.x >= kRecThreads) continue;
     const int r = threadIdx.x % 16, g = threadIdx.x / 16;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -1079,6 +1117,7 @@ __device__ void gemm_sym(const double* A, const double* B, double* C, int N, int
     lower_tile(t, ti, tj);
     double acc[2];
     gemm_tile<double, 16, 16, TA, TB>(A, B, ld, N, ti * 16, tj * 16, Ident(), acc, sA, sB);
+    if (threadIdx.x >= kRecThreads) continue;
     const int r = threadIdx.x % 16, g = threadIdx.x / 16;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -1320,10 +1359,14 @@ __device__ void warm_abort(LargeScratch<double>& L, bool near) {
   }
 }
 
+// 256 threads at most 128 registers each (32 K of the SM's 64 K): the
+// cooperative grid needs a CTA on every SM, and the small-block projections
+// running beside it on another stream keep room for theirs (at 255
+// registers each CTA filled its SM and waited for those to finish).
 template <typename T>
-__global__ void __launch_bounds__(kRecThreads) k_tri_recon(DevPlan<T> p, int bid, LargeScratch<double> L,
-                                                           int warm_mode) {
-  __shared__ double sA[16 * (kKC + 1)], sB[kKC * (24 + 1)];
+__global__ void __maxnreg__(128) k_tri_recon(DevPlan<T> p, int bid, LargeScratch<double> L,
+                                                         int warm_mode) {
+  __shared__ double sA[2 * 16 * (kKC + 1)], sB[2 * kKC * (24 + 1)];
   __shared__ double red[40];
   const BlockDesc bd = p.blocks[bid];
   if (!p.active[bd.inst]) return;
@@ -1642,7 +1685,7 @@ cudaError_t launch_psd_tri_part(const DevPlan<double>& p, int bid, int N, const 
       if (e != cudaSuccess) return e;
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(grid);
-      cfg.blockDim = dim3(kRecThreads);
+      cfg.blockDim = dim3(kRecBlock);
       cfg.dynamicSmemBytes = 0;
       cfg.stream = s;
       cudaLaunchAttribute attr[1];
