@@ -1108,15 +1108,18 @@ __device__ void gemm_full(const F* A, const F* B, F* C, int N, int ld, XB xb, F*
 }
 
 // Symmetric C = op(A) op(B) over the lower 16 x 16 tiles, mirrored; f(i, j,
-// c) sees each lower entry (i >= j) once.
-template <bool TA, bool TB, class F>
+// c) sees each lower entry (i >= j) once.  CT: the type the products are
+// computed in (FP32 only where the result's rounding is far below what it
+// is used for).
+template <bool TA, bool TB, class F, typename CT = double>
 __device__ void gemm_sym(const double* A, const double* B, double* C, int N, int ld, F f, double* sA, double* sB) {
   const int nt = (N + 15) / 16, nlow = nt * (nt + 1) / 2;
   for (int t = blockIdx.x; t < nlow; t += gridDim.x) {
     int ti, tj;
     lower_tile(t, ti, tj);
-    double acc[2];
-    gemm_tile<double, 16, 16, TA, TB>(A, B, ld, N, ti * 16, tj * 16, Ident(), acc, sA, sB);
+    CT acc[2];
+    gemm_tile<CT, 16, 16, TA, TB, Ident, double>(A, B, ld, N, ti * 16, tj * 16, Ident(), acc,
+                                                 reinterpret_cast<CT*>(sA), reinterpret_cast<CT*>(sB));
     if (threadIdx.x >= kRecThreads) continue;
     const int r = threadIdx.x % 16, g = threadIdx.x / 16;
 #pragma unroll
@@ -1441,7 +1444,9 @@ __global__ void __maxnreg__(128) k_tri_recon(DevPlan<T> p, int bid, LargeScratch
           Vn[q] = j < N ? (k == j ? 1.0 : 0.0) - __ldcg(L.T1 + q) : 0.0;
         }
         if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
-        gemm_sym<true, false>(Vn, Vn, L.B0, N, Np, NoOp(), sA, sB);  // E^2 (E symmetric)
+        // E^2 (E symmetric) in FP32: its entries are at most g^2 <= 2.3e-10,
+        // so its rounding (about 1e-6 relative) stays below 1e-15
+        gemm_sym<true, false, NoOp, float>(Vn, Vn, L.B0, N, Np, NoOp(), sA, sB);
         if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
         gemm_full<false, false>(Vc, L.B0, Vn, N, Np, NsFactor2{L.T1, Np}, sA, sB);
         if (!grid_barrier(L.bar, (++gen) * G, err, p.wait_limit)) return;
