@@ -670,13 +670,21 @@ def main():
     # region.  In the timed steps the small-block projections run on a side
     # stream beside the large-block ones, so a step is affine + max(small,
     # large); the replay is trusted only if that sum is within 10% of it.
-    stage_names = ((0, "affine"), (1, "psd_small"), (15, "tri_warm"), (10, "tri_gather"), (11, "tri_reduce"),
-                   (12, "tri_vectors"), (13, "tri_recon"), (14, "psd_large_jacobi"))
+    blocks = [blk.size(prog.n) for con in prog.constraints for blk in con.blocks]
+    # Gram blocks above 112 go to the tensor-core Newton-Schulz kernel in the
+    # FP32-projection forms; stage 2 (every large-block projection) times it
+    ns_blocks = [N for N in blocks if N > 112] if prec != capi.PREC_FP64 else []
+    if ns_blocks:
+        stage_names = ((0, "affine"), (1, "psd_small"), (2, "psd_large_ns"))
+    else:
+        stage_names = ((0, "affine"), (1, "psd_small"), (15, "tri_warm"), (10, "tri_gather"), (11, "tri_reduce"),
+                       (12, "tri_vectors"), (13, "tri_recon"), (14, "psd_large_jacobi"))
     sk = capi.Solver(prog, precision=prec, k_check=10)
     sk.iterate(args.warmup)
     sk.sync()
     stk = torch.cuda.ExternalStream(sk.stream)
     evs = {name: [] for _, name in stage_names}
+    ns_steps = []  # Newton-Schulz steps of each replayed iteration (largest over the blocks)
     for _ in range(args.steps):
         with torch.cuda.stream(stk):
             flush()
@@ -688,6 +696,8 @@ def main():
             with torch.cuda.stream(stk):
                 b.record(stk)
             evs[name].append((a, b))
+        if ns_blocks:
+            ns_steps.append(sk.stats()["max_sweeps"])
     sk.sync()
     sk.close()
     stage_all = {name: [a.elapsed_time(b) for a, b in evs[name]] for _, name in stage_names}
@@ -696,13 +706,12 @@ def main():
     # cold kernels after it return at once (a few microseconds)
     worked = {name: [x for x in v if x > 0.02] for name, v in stage_all.items()}
     large_ms = sum(stage_ms[k] for k in ("tri_warm", "tri_gather", "tri_reduce", "tri_vectors", "tri_recon",
-                                         "psd_large_jacobi"))
+                                         "psd_large_jacobi", "psd_large_ns") if k in stage_ms)
     replay_ms = stage_ms["affine"] + max(stage_ms["psd_small"], large_ms)
     step_ms = total_ms / args.steps
     consistent = abs(replay_ms - step_ms) <= 0.1 * step_ms
 
     d = solver.dims[0]
-    blocks = [blk.size(prog.n) for con in prog.constraints for blk in con.blocks]
     clk_sum = clk.summary(local)
     sm_mhz = (clk_sum or {}).get("sm_max_mhz") or 2070.0
     alu = alu_peaks(sm_mhz)
@@ -761,6 +770,28 @@ def main():
                            "work is counted as 9 N^3 in every iteration"
                            if len(worked['tri_reduce']) < len(stage_all['tri_reduce']) else ""),
                 "stage_ms": stage_ms}
+    elif ns_blocks:
+        # The dominant unit is the tensor-core Newton-Schulz projection of the
+        # large blocks: per step two products of the padded Np x Np iterate
+        # (Np = N rounded up to 128), each as six BF16 products of the
+        # three-part split (2 Np^3 flops each), plus the final product W S;
+        # bound by the BF16 tensor rate (the sustained measured peak: the
+        # kernel runs inside a long step).
+        pk, pk_kind = peaks()
+        peak_tf = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
+        steps_mean = float(np.mean(ns_steps)) if ns_steps else 0.0
+        tflop = sum(6 * 2.0 * (-(-N // 128) * 128) ** 3 * (2 * steps_mean + 1) for N in ns_blocks) / 1e12
+        fp32_equiv = sum(2.0 * N ** 3 * (2 * steps_mean + 1) for N in ns_blocks) / 1e12
+        ns_ms = stage_ms["psd_large_ns"]
+        achieved = tflop / (ns_ms / 1e3)
+        roof = {"kernel": "k_psd_ns (tensor-core Newton-Schulz projection)", "bound": "tensor",
+                "achieved": achieved if consistent else None, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved / peak_tf if consistent else None, "traffic": None,
+                "ns_steps_mean": steps_mean, "ms_per_launch": ns_ms,
+                "note": f"BF16 tensor flops of the three-part split products ({tflop * 1e3:.2f} GFLOP per launch; "
+                        f"{fp32_equiv * 1e3:.2f} GFLOP as FP32-equivalent products of the N x N iterate) over "
+                        f"the sustained BF16 peak ({pk_kind})" + note_tail,
+                "stage_ms": stage_ms}
     else:
         flops = sum(9.0 * N ** 3 for N in blocks)
         dom_ms = stage_ms["psd_small"] if stage_ms["psd_small"] >= large_ms else large_ms
@@ -804,7 +835,8 @@ def main():
            "wall_s": t_wall, "e2e": e2e, "roofline": roof,
            "gpu_launches": None}
     out["gpu_launches"] = int(solver.launches_per_iteration() * args.steps)
-    out["roofline"]["peak_source"] = "unit counts x SM clock (derivation in the design notes)"
+    out["roofline"]["peak_source"] = ("MEASURED_PEAKS.json bf16_tflops_sustained" if ns_blocks else
+                                      "unit counts x SM clock (derivation in the design notes)")
     out["clocks"] = clk_sum
 
     # the FP32-projection form (tensor-core Newton-Schulz for the large block)
