@@ -810,13 +810,15 @@ def main():
     se = capi.Solver(prog, precision=prec, k_check=10)
     se.iterate(args.warmup)
     se.sync()
-    u0, v0 = se.get_iterate()
+    # the step's input and result live in pinned host memory
+    pin = [torch.empty(se.total, dtype=torch.float64).pin_memory() for _ in range(2)]
+    u0, v0 = se.get_iterate(out=(pin[0].numpy(), pin[1].numpy()))
     e2e_steps = args.steps
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         se.set_iterate(u0, v0)
         se.iterate(1)
-        u0, v0 = se.get_iterate()
+        se.get_iterate(out=(u0, v0))
     e2e_dt = time.perf_counter() - t0
     se.close()
     esz = 8 if prec == capi.PREC_FP64 else 4

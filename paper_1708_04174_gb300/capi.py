@@ -373,9 +373,17 @@ class Solver:
         """Bound of the grid-wide device waits, microseconds (0: about 2 s)."""
         _check(lib().sos_set_wait_limit(self.h, us), self.h)
 
-    def get_iterate(self):
-        u = np.zeros(self.total)
-        v = np.zeros(self.total)
+    def get_iterate(self, out=None):
+        """sos_get_iterate into new arrays, or into ``out = (u, v)``
+        (contiguous float64 host arrays of ``self.total``, e.g. views of
+        pinned memory)."""
+        if out is None:
+            u = np.zeros(self.total)
+            v = np.zeros(self.total)
+        else:
+            u, v = out
+            assert all(a.dtype == np.float64 and a.flags["C_CONTIGUOUS"] and a.shape == (self.total,)
+                       for a in (u, v))
         _check(lib().sos_get_iterate(self.h, _ptr(u, C.c_double), _ptr(v, C.c_double)), self.h)
         return u, v
 

@@ -75,6 +75,7 @@ struct sos_handle {
   std::vector<int32_t> row_perm;  // device row q holds the constraint row row_perm[q]
   int64_t* cat_map = nullptr;     // device iterate exchange: source of each concatenated position (lazy)
   int64_t cat_total = 0;
+  double* cat_stage = nullptr;    // 2 x cat_total doubles: device staging of the host iterate exchange (lazy)
   // persistent batched path
   bool persistent = false;
   int32_t solve_mode = 0;
@@ -925,42 +926,6 @@ int get_all(sos_handle* h, std::vector<double>& ux, std::vector<double>& vx, std
   return copy_iterate_out(h, h->d32, ux, vx, uy, vy, tau, kappa);
 }
 
-template <typename T>
-int copy_iterate_in(sos_handle* h, const DevPlan<T>& p, const double* u, const double* v) {
-  std::vector<T> a(h->NX), b(h->NX), c(h->M), dd(h->M);
-  std::vector<double> tau(h->n_inst), kappa(h->n_inst);
-  int64_t pos = 0;
-  for (int i = 0; i < h->n_inst; ++i) {
-    const InstInfo& in = h->inst[i];
-    for (int k = 0; k < in.nx; ++k) {
-      a[in.x_off + k] = static_cast<T>(u[pos + k]);
-      b[in.x_off + k] = static_cast<T>(v[pos + k]);
-    }
-    pos += in.nx;
-    for (int k = 0; k < in.m; ++k) {
-      c[in.y_off + k] = static_cast<T>(u[pos + k]);
-      dd[in.y_off + k] = static_cast<T>(v[pos + k]);
-    }
-    pos += in.m;
-    tau[i] = u[pos];
-    kappa[i] = v[pos];
-    pos += 1;
-  }
-  std::vector<T> cq(h->M), dq(h->M);
-  for (int64_t q = 0; q < h->M; ++q) {  // device rows are ordered by length
-    cq[q] = c[h->row_perm[q]];
-    dq[q] = dd[h->row_perm[q]];
-  }
-  CK(cudaMemcpyAsync(p.ux, a.data(), sizeof(T) * h->NX, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(p.vx, b.data(), sizeof(T) * h->NX, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(p.uy, cq.data(), sizeof(T) * h->M, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(p.vy, dq.data(), sizeof(T) * h->M, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(h->d64.tau, tau.data(), sizeof(double) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(h->d64.kappa, kappa.data(), sizeof(double) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  return SOS_OK;
-}
-
 }  // namespace
 
 extern "C" {
@@ -1215,26 +1180,6 @@ int sos_solve(sos_handle* h, double tol, int32_t max_iter, sos_result* results) 
   return SOS_OK;
 }
 
-int sos_get_iterate(sos_handle* h, double* u, double* v) {
-  if (!h || !u || !v) return SOS_ERR_INVALID_ARG;
-  std::vector<double> ux, vx, uy, vy, tau, kappa;
-  TRY(get_all(h, ux, vx, uy, vy, tau, kappa));
-  int64_t pos = 0;
-  for (int i = 0; i < h->n_inst; ++i) {
-    const InstInfo& in = h->inst[i];
-    std::memcpy(u + pos, ux.data() + in.x_off, sizeof(double) * in.nx);
-    std::memcpy(v + pos, vx.data() + in.x_off, sizeof(double) * in.nx);
-    pos += in.nx;
-    std::memcpy(u + pos, uy.data() + in.y_off, sizeof(double) * in.m);
-    std::memcpy(v + pos, vy.data() + in.y_off, sizeof(double) * in.m);
-    pos += in.m;
-    u[pos] = tau[i];
-    v[pos] = kappa[i];
-    pos += 1;
-  }
-  return SOS_OK;
-}
-
 static int ensure_cat_map(sos_handle* h) {
   if (h->cat_map) return SOS_OK;
   std::vector<int32_t> inv(h->M);
@@ -1270,15 +1215,44 @@ int sos_set_iterate_device(sos_handle* h, const double* u, const double* v) {
   return SOS_OK;
 }
 
+// Host iterate exchange: one contiguous copy each way through a device
+// staging buffer, the reordering done by the device gather / scatter kernels
+// (no host-side loops; pinned caller buffers copy at full link speed).
+static int ensure_cat_stage(sos_handle* h) {
+  TRY(ensure_cat_map(h));
+  if (!h->cat_stage) TRY(alloc(h, 2 * static_cast<size_t>(h->cat_total), &h->cat_stage));
+  return SOS_OK;
+}
+
+int sos_get_iterate(sos_handle* h, double* u, double* v) {
+  if (!h || !u || !v) return SOS_ERR_INVALID_ARG;
+  TRY(ensure_cat_stage(h));
+  double* su = h->cat_stage;
+  double* sv = h->cat_stage + h->cat_total;
+  const size_t bytes = sizeof(double) * static_cast<size_t>(h->cat_total);
+  CK(iter64(h) ? launch_gather_iterate<double>(h->d64, h->cat_map, h->cat_total, su, sv, h->stream)
+               : launch_gather_iterate<float>(h->d32, h->cat_map, h->cat_total, su, sv, h->stream));
+  CK(cudaMemcpyAsync(u, su, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(v, sv, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SOS_OK;
+}
+
 int sos_set_iterate(sos_handle* h, const double* u, const double* v) {
   if (!h || !u || !v) return SOS_ERR_INVALID_ARG;
-  int rc = iter64(h) ? copy_iterate_in(h, h->d64, u, v) : copy_iterate_in(h, h->d32, u, v);
-  if (rc != SOS_OK) return rc;
+  TRY(ensure_cat_stage(h));
+  double* su = h->cat_stage;
+  double* sv = h->cat_stage + h->cat_total;
+  const size_t bytes = sizeof(double) * static_cast<size_t>(h->cat_total);
+  CK(cudaMemcpyAsync(su, u, bytes, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(sv, v, bytes, cudaMemcpyHostToDevice, h->stream));
+  // the scatter also marks every instance active
+  CK(iter64(h) ? launch_scatter_iterate<double>(h->d64, h->cat_map, h->cat_total, su, sv, h->active, h->stream)
+               : launch_scatter_iterate<float>(h->d32, h->cat_map, h->cat_total, su, sv, h->active, h->stream));
   TRY(init_wl(h));
   std::fill(h->active_h.begin(), h->active_h.end(), 1);
   std::fill(h->iters_h.begin(), h->iters_h.end(), 0);
   std::fill(h->status_h.begin(), h->status_h.end(), SOS_RUNNING);
-  CK(cudaMemcpyAsync(h->active, h->active_h.data(), sizeof(int32_t) * h->n_inst, cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return SOS_OK;
 }
