@@ -244,7 +244,12 @@ int sos_sync(sos_handle* h);
 
 /* Copies the HSDE iterates of all instances (concatenated in instance order,
  * each [n_x + m + 1]) to / from HOST buffers.  set_iterate also marks every
- * instance as running (warm start, resume from a checkpoint). */
+ * instance as running (warm start, resume from a checkpoint).  Both calls
+ * synchronise the handle's stream before returning.  One contiguous copy
+ * each way goes through a device staging buffer (2 x the concatenated length
+ * in doubles, allocated by the first call and owned by the handle); pinned
+ * host buffers copy at full link speed, pageable ones through the driver's
+ * staging.  Errors: SOS_ERR_INVALID_ARG (NULL), SOS_ERR_CUDA. */
 int sos_get_iterate(sos_handle* h, double* u, double* v);
 int sos_set_iterate(sos_handle* h, const double* u, const double* v);
 
