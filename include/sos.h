@@ -248,7 +248,7 @@ int sos_sync(sos_handle* h);
  * synchronise the handle's stream before returning.  One contiguous copy
  * each way goes through a device staging buffer (2 x the concatenated length
  * in doubles, allocated by the first call and owned by the handle); pinned
- * host buffers copy at full link speed, pageable ones through the driver's
+ * host buffers copy at full link speed, pageable ones through the CUDA driver's
  * staging.  Errors: SOS_ERR_INVALID_ARG (NULL), SOS_ERR_CUDA. */
 int sos_get_iterate(sos_handle* h, double* u, double* v);
 int sos_set_iterate(sos_handle* h, const double* u, const double* v);
